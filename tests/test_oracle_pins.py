@@ -1,0 +1,412 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics (no GPU).
+
+Each test checks one oracle function against something other than itself: a naive DFT,
+Parseval, the adjoint identity, the exact Gaussian posterior, a dense scan, a brute-force
+ICD, the closed-form limits of the q-GGMRF potential, a dense-matrix MAP objective, or a value
+printed in the paper (tests/golden/paper_values.txt).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ddh_oracle as o
+from synth import ddh_synth as sy
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+
+
+def _rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+def _crandn(rng, *shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2)
+
+
+def _dft_matrix_2d(n):
+    """Dense unitary 2D DFT on row-major n x n images, written from the definition."""
+    k = np.arange(n)
+    f1 = np.exp(-2j * math.pi * np.outer(k, k) / n) / math.sqrt(n)
+    return np.kron(f1, f1)
+
+
+def _golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, *vals = line.split()
+        out[key] = [float(v) for v in vals]
+    return out
+
+
+# ---------------------------------------------------------------------------- transforms
+@pytest.mark.parametrize("n", [8, 16])
+def test_fft_matches_naive_dft(n):
+    rng = _rng(n)
+    x = _crandn(rng, n, n)
+    X = np.zeros((n, n), complex)
+    for ky in range(n):
+        for kx in range(n):
+            acc = 0j
+            for yy in range(n):
+                for xx in range(n):
+                    acc += x[yy, xx] * np.exp(-2j * math.pi * (ky * yy + kx * xx) / n)
+            X[ky, kx] = acc / n
+    assert np.allclose(o.fft2u(x), X, atol=1e-12)
+    assert np.allclose(o.ifft2u(X), x, atol=1e-12)
+
+
+def test_parseval_and_inverse():
+    rng = _rng(1)
+    x = _crandn(rng, 32, 32)
+    assert math.isclose(np.linalg.norm(o.fft2u(x)), np.linalg.norm(x), rel_tol=1e-13)
+    assert np.allclose(o.ifft2u(o.fft2u(x)), x, atol=1e-13)
+
+
+def test_adjoint_identity():
+    rng = _rng(2)
+    n = 16
+    a = o.aperture(n, 8.0)
+    x, y = _crandn(rng, n, n), _crandn(rng, n, n)
+    phi = rng.uniform(-math.pi, math.pi, (n, n))
+    lhs = np.vdot(y, o.forward_op(x, phi, a))
+    rhs = np.vdot(o.adjoint_op(y, phi, a), x)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_operator_matches_dense_matrix():
+    """A_phi = D_a D(exp(j phi)) F as an explicit matrix (Sec. 2)."""
+    rng = _rng(3)
+    n = 8
+    a = o.aperture(n, 4.0)
+    phi = rng.uniform(-math.pi, math.pi, (n, n))
+    A = np.diag(a.ravel().astype(float)) @ np.diag(np.exp(1j * phi.ravel())) @ _dft_matrix_2d(n)
+    g = _crandn(rng, n, n)
+    assert np.allclose(o.forward_op(g, phi, a).ravel(), A @ g.ravel(), atol=1e-12)
+    y = _crandn(rng, n, n)
+    assert np.allclose(o.adjoint_op(y, phi, a).ravel(), A.conj().T @ y.ravel(), atol=1e-12)
+
+
+def test_aperture_geometry():
+    a = o.aperture(256, 128.0)
+    # disc of radius 64 about (127.5, 127.5): pi r^2 to within the pixelation
+    assert abs(a.sum() - math.pi * 64 ** 2) < 2 * math.pi * 64
+    assert a[127, 127] and a[128, 128] and not a[0, 0]
+    assert np.array_equal(a, a[::-1, :]) and np.array_equal(a, a.T)
+
+
+# ---------------------------------------------------------------------------- Normalize
+def test_normalize_eq4():
+    rng = _rng(4)
+    y = _crandn(rng, 32, 32) * 3.0 + (1.5 - 2j)
+    yt, st = o.normalize(y)
+    assert abs(yt.mean()) < 1e-13
+    assert math.isclose(np.sum(np.abs(yt) ** 2), y.size, rel_tol=1e-13)
+    # invariant to affine rescaling up to the phase of the scale
+    c = 3.0 * np.exp(0.7j)
+    yt2, _ = o.normalize(c * y + (2.0 + 1.0j))
+    assert np.allclose(yt2, np.exp(0.7j) * yt, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------- RemoveTipTilt
+def test_tip_tilt_removes_wrapped_plane():
+    n, d = 32, 16.0
+    a = o.aperture(n, d)
+    c = (n - 1) / 2
+    yy, xx = np.mgrid[0:n, 0:n]
+    tx, ty, piston = 0.9, -1.3, 2.5
+    phi = o.wrap(tx * (xx - c) + ty * (yy - c) + piston)
+    ex, ey = o.tip_tilt(phi, a)
+    assert math.isclose(ex, tx, rel_tol=1e-12) and math.isclose(ey, ty, rel_tol=1e-12)
+    out, _ = o.remove_tip_tilt(phi, a)
+    assert np.allclose(o.wrap(out[a] - piston), 0.0, atol=1e-12)
+    assert np.all(out[~a] == 0.0)
+
+
+def test_tip_tilt_zero_phase():
+    a = o.aperture(16, 8.0)
+    assert o.tip_tilt(np.zeros((16, 16)), a) == (0.0, 0.0)
+
+
+# ---------------------------------------------------------------------------- E-step
+def test_estep_equals_exact_posterior_for_constant_r():
+    """For constant r the A^H A ~ I posterior mean is exact: F^H D_a F is a projection and
+    A^H y lies in its range.  Compare with D(r) A^H (A D(r) A^H + s2 I)^-1 y."""
+    rng = _rng(5)
+    n = 8
+    a = o.aperture(n, 4.0)
+    phi = rng.uniform(-math.pi, math.pi, (n, n))
+    A = np.diag(a.ravel().astype(float)) @ np.diag(np.exp(1j * phi.ravel())) @ _dft_matrix_2d(n)
+    y = _crandn(rng, n, n)
+    r0, s2 = 0.7, 0.3
+    prm = o.Params(n=n, aperture_diam=4.0, noise_var=s2)
+    R = r0 * np.eye(n * n)
+    mu_exact = R @ A.conj().T @ np.linalg.solve(A @ R @ A.conj().T + s2 * np.eye(n * n), y.ravel())
+    b = o.adjoint_op(y, phi, a)
+    mu, s, w = o.estep(np.full((n, n), r0), b, prm)
+    assert np.allclose(mu.ravel(), mu_exact, atol=1e-12)
+    # the variance term is the exact one when a == 1 everywhere (A unitary)
+    Au = np.diag(np.exp(1j * phi.ravel())) @ _dft_matrix_2d(n)
+    cov = np.linalg.inv(np.eye(n * n) / r0 + Au.conj().T @ Au / s2)
+    assert np.allclose(np.real(np.diag(cov)), (s - np.abs(mu) ** 2).ravel(), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------- prior
+def test_qggmrf_closed_forms():
+    prm = o.Params(n=4, aperture_diam=2, prior_p=1.1, prior_q=2.0, prior_T=1.0, prior_sigma=0.3)
+    # p = q = 2: u = 1 and rho = D^2 / (4 sigma^2)
+    prm22 = o.Params(n=4, aperture_diam=2, prior_p=2.0, prior_q=2.0, prior_T=1.0, prior_sigma=0.3)
+    d = np.linspace(-2, 2, 41)
+    assert np.allclose(o.qggmrf_rho(d, prm22), d ** 2 / (4 * 0.3 ** 2), rtol=1e-13)
+    # small |D|: rho ~ D^2 / (p sigma^2 T^(2-p)); large |D|: rho ~ |D|^p/(p sigma^p)
+    small = 1e-7
+    assert math.isclose(float(o.qggmrf_rho(small, prm)), small ** 2 / (1.1 * 0.3 ** 2), rel_tol=1e-5)
+    big = 1e7
+    assert math.isclose(float(o.qggmrf_rho(big, prm)), big ** 1.1 / (1.1 * 0.3 ** 1.1), rel_tol=1e-5)
+
+
+def test_qggmrf_weight_is_derivative_over_delta():
+    prm = o.Params(n=4, aperture_diam=2, prior_p=1.1, prior_q=2.0, prior_T=1.3, prior_sigma=0.2)
+    d = np.concatenate([np.linspace(-3, -1e-3, 50), np.linspace(1e-3, 3, 50)])
+    h = 1e-6
+    deriv = (o.qggmrf_rho(d + h, prm) - o.qggmrf_rho(d - h, prm)) / (2 * h)
+    assert np.allclose(o.qggmrf_weight(d, prm), deriv / d, rtol=1e-6)
+    # the value at zero is the limit
+    lim = float(o.qggmrf_weight(np.array([0.0]), prm)[0])
+    assert math.isclose(lim, float(o.qggmrf_weight(np.array([1e-9]), prm)[0]), rel_tol=1e-6)
+
+
+def test_symmetric_bound_majorises():
+    prm = o.Params(n=4, aperture_diam=2, prior_p=1.1, prior_q=2.0, prior_T=1.0, prior_sigma=0.1)
+    dp = np.linspace(-2, 2, 81)
+    dd = np.linspace(-3, 3, 241)
+    for x0 in dp:
+        bound = o.qggmrf_rho(x0, prm) + 0.5 * o.qggmrf_weight(np.array([x0]), prm)[0] * (dd ** 2 - x0 ** 2)
+        assert np.all(o.qggmrf_rho(dd, prm) <= bound + 1e-12)
+
+
+def test_prior_energy_bruteforce():
+    rng = _rng(6)
+    n = 5
+    prm = o.Params(n=n, aperture_diam=2, prior_sigma=0.2)
+    r = rng.uniform(0, 1, (n, n))
+    e = 0.0
+    pix = [(y, x) for y in range(n) for x in range(n)]
+    for i, (y0, x0) in enumerate(pix):
+        for (y1, x1) in pix[i + 1:]:
+            dy, dx = abs(y1 - y0), abs(x1 - x0)
+            if max(dy, dx) != 1:
+                continue
+            bij = 1 / (4 + 2 * math.sqrt(2)) / (math.sqrt(2) if dy and dx else 1.0)
+            e += bij * float(o.qggmrf_rho(r[y0, x0] - r[y1, x1], prm))
+    assert math.isclose(o.prior_energy(r, prm), e, rel_tol=1e-12)
+
+
+# ---------------------------------------------------------------------------- cubic / ICD
+def _h(r, W, C, s):
+    return np.log(r) + s / r + 0.5 * W * r ** 2 - C * r
+
+
+def test_cubic_argmin_is_global_minimiser():
+    rng = _rng(7)
+    cases = []
+    for _ in range(300):  # generic coefficients
+        W = 10 ** rng.uniform(-1, 3)
+        C = W * 10 ** rng.uniform(-3, 0.5)
+        s = 10 ** rng.uniform(-4, 0)
+        cases.append((W, C, s))
+    for _ in range(300):  # three positive roots by construction
+        x = np.sort(10 ** rng.uniform(-3, 1, 3))
+        W = 1.0 / (x[0] * x[1] + x[0] * x[2] + x[1] * x[2])
+        cases.append((W, W * x.sum(), W * x.prod()))
+    W, C, s = (np.array(v) for v in zip(*cases))
+    r = o.cubic_argmin(W, C, s)
+    grid = np.logspace(-7, 3, 200_001)
+    for i in range(len(cases)):
+        f = W[i] * r[i] ** 3 - C[i] * r[i] ** 2 + r[i] - s[i]
+        scale = W[i] * r[i] ** 3 + C[i] * r[i] ** 2 + r[i] + s[i]
+        assert abs(f) <= 1e-9 * scale
+        hs = _h(grid, W[i], C[i], s[i])
+        hr = _h(r[i], W[i], C[i], s[i])
+        assert hr <= hs.min() + 1e-9 * max(1.0, abs(hr))
+
+
+def test_cubic_w_zero_gives_s():
+    s = np.array([0.3, 2.0])
+    assert np.array_equal(o.cubic_argmin(np.zeros(2), np.zeros(2), s), s)
+
+
+def test_icd_sweep_bruteforce_small_grid():
+    """4-colour sweep on a 5x5 grid vs a pixel-by-pixel dense minimisation of the surrogate,
+    with neighbours and weights enumerated explicitly."""
+    rng = _rng(8)
+    n = 5
+    prm = o.Params(n=n, aperture_diam=2, prior_sigma=0.1, r_floor=1e-10)
+    r0 = rng.uniform(0.01, 0.5, (n, n))
+    s = rng.uniform(0.01, 0.5, (n, n))
+    got = o.icd_sweep(r0, s, prm)
+    r = r0.copy()
+    grid = np.logspace(-6, 1, 70_001)
+    for cx, cy in [(0, 0), (1, 0), (0, 1), (1, 1)]:
+        for yy in range(n):
+            for xx in range(n):
+                if xx % 2 != cx or yy % 2 != cy:
+                    continue
+                terms = []
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        if (dy, dx) == (0, 0):
+                            continue
+                        y1, x1 = yy + dy, xx + dx
+                        if not (0 <= y1 < n and 0 <= x1 < n):
+                            continue
+                        bij = 1 / (4 + 2 * math.sqrt(2)) / (math.sqrt(2) if dy and dx else 1.0)
+                        beta = bij * float(o.qggmrf_weight(np.array([r0[yy, xx] - r0[y1, x1]]), prm)[0])
+                        terms.append((beta, r[y1, x1]))
+                hv = np.log(grid) + s[yy, xx] / grid
+                for beta, rj in terms:
+                    hv = hv + 0.5 * beta * (grid - rj) ** 2
+                k = int(np.argmin(hv))
+                lo, hi = grid[max(k - 1, 0)], grid[min(k + 1, grid.size - 1)]
+                for _ in range(200):  # golden-section refinement
+                    m1, m2 = lo + 0.382 * (hi - lo), hi - 0.382 * (hi - lo)
+                    f1 = np.log(m1) + s[yy, xx] / m1 + sum(0.5 * b_ * (m1 - rj) ** 2 for b_, rj in terms)
+                    f2 = np.log(m2) + s[yy, xx] / m2 + sum(0.5 * b_ * (m2 - rj) ** 2 for b_, rj in terms)
+                    lo, hi = (lo, m2) if f1 < f2 else (m1, hi)
+                r[yy, xx] = 0.5 * (lo + hi)
+    assert np.allclose(got, r, rtol=1e-7)
+
+
+# ---------------------------------------------------------------------------- phase M-step
+def test_phase_mstep_exact_recovery_noiseless():
+    rng = _rng(9)
+    n = 16
+    a = o.aperture(n, 8.0)
+    g = _crandn(rng, n, n)
+    phi = np.where(a, rng.uniform(-math.pi, math.pi, (n, n)), 0.0)
+    y = o.forward_op(g, phi, a)
+    est, z = o.phase_mstep(y, g, np.zeros((n, n)), a)
+    assert np.allclose(o.wrap(est - phi)[a], 0.0, atol=1e-12)
+    assert np.all(est[~a] == 0.0)
+
+
+def test_phase_mstep_minimises_data_term():
+    rng = _rng(10)
+    n = 8
+    a = o.aperture(n, 6.0)
+    y, mu = _crandn(rng, n, n), _crandn(rng, n, n)
+    est, z = o.phase_mstep(y, mu, np.zeros((n, n)), a)
+    base = np.abs(y - np.exp(1j * est) * z) ** 2
+    for dphi in (0.01, -0.01, 0.5, 3.0):
+        assert np.all((base <= np.abs(y - np.exp(1j * (est + dphi)) * z) ** 2 + 1e-12)[a])
+
+
+# ---------------------------------------------------------------------------- EM objective
+def _dense_map_cost(r, phi, y, prm):
+    n = prm.n
+    A = np.diag(np.exp(1j * phi.ravel())) @ _dft_matrix_2d(n)
+    cov = A @ np.diag(r.ravel()) @ A.conj().T + prm.noise_var * np.eye(n * n)
+    sign, logdet = np.linalg.slogdet(cov)
+    quad = np.real(np.vdot(y.ravel(), np.linalg.solve(cov, y.ravel())))
+    return logdet + quad + o.prior_energy(r, prm)
+
+
+def test_em_objective_matches_dense_likelihood():
+    rng = _rng(11)
+    n = 8
+    prm = o.Params(n=n, aperture_diam=1e6, noise_var=0.3, prior_sigma=0.2)
+    r = rng.uniform(0.05, 1.0, (n, n))
+    phi = rng.uniform(-1, 1, (n, n))
+    y = _crandn(rng, n, n)
+    assert math.isclose(o.em_objective_unit_aperture(r, phi, y, prm), _dense_map_cost(r, phi, y, prm),
+                        rel_tol=1e-11)
+
+
+def test_static_em_is_monotone_with_unit_aperture():
+    """With a == 1 the operator is unitary, the E-step exact, and each EM iteration cannot
+    increase the MAP cost of Eq. 2 (evaluated with a dense covariance)."""
+    rng = _rng(12)
+    n = 8
+    prm = o.Params(n=n, aperture_diam=1e6, noise_var=0.2, prior_sigma=0.1)
+    a = o.aperture(n, prm.aperture_diam)
+    assert a.all()
+    g = np.sqrt(rng.uniform(0, 1, (n, n))) * _crandn(rng, n, n)
+    y = np.exp(1j * rng.uniform(-1, 1, (n, n))) * o.fft2u(g) + math.sqrt(0.2) * _crandn(rng, n, n)
+    y, _ = o.normalize(y)
+    r = np.maximum(np.abs(o.adjoint_op(y, np.zeros((n, n)), a)) ** 2, 1e-3)
+    phi = np.zeros((n, n))
+    costs = [_dense_map_cost(r, phi, y, prm)]
+    for _ in range(50):
+        r, phi = o.em_static_step(r, phi, y, prm, a)
+        costs.append(_dense_map_cost(r, phi, y, prm))
+    diffs = np.diff(costs)
+    assert np.all(diffs <= 1e-9 * np.abs(costs[:-1])), diffs.max()
+    assert costs[-1] < costs[0]
+
+
+# ---------------------------------------------------------------------------- Strehl
+def test_strehl_properties():
+    rng = _rng(13)
+    n = 64
+    a = o.aperture(n, 32.0)
+    phi = np.where(a, rng.uniform(-math.pi, math.pi, (n, n)), 0.0)
+    assert math.isclose(o.strehl(phi, phi, a), 1.0, rel_tol=1e-12)
+    assert math.isclose(o.strehl(phi + 1.234, phi, a), 1.0, rel_tol=1e-12)
+    yy, xx = np.mgrid[0:n, 0:n]
+    tilt = 2 * math.pi * (3 * xx - 2 * yy) / n   # integer-cycle tilt shifts the PSF by pixels
+    assert math.isclose(o.strehl(phi + tilt, phi, a), 1.0, rel_tol=1e-12)
+    # Marechal: small Gaussian residual sigma -> S ~ exp(-sigma^2)
+    sig = 0.1
+    err = sig * rng.standard_normal((n, n))
+    S = o.strehl(phi + err, phi, a)
+    assert abs(S - math.exp(-sig ** 2)) < 0.005
+
+
+# ---------------------------------------------------------------------------- step
+def test_first_frame_from_zero_state():
+    cfg = sy.config_single_64(2)
+    st = sy.Stream(cfg)
+    y, _ = st.frame(0)
+    prm = o.default_params(64, 32.0, cfg.snr, prior_sigma=0.1)
+    s1, tr = o.step(o.init_state(64), y, prm)
+    assert tr.stats["tx"] == 0.0 and tr.stats["ty"] == 0.0
+    assert np.allclose(tr.r_init, np.maximum(prm.lam * prm.alpha * np.abs(tr.b) ** 2, prm.r_floor))
+    a = o.aperture(64, 32.0)
+    assert np.all(s1.phi[~a] == 0) and np.all(np.abs(s1.phi) <= math.pi)
+    assert np.all(s1.r >= prm.r_floor) and np.all(np.isfinite(s1.r))
+
+
+# ---------------------------------------------------------------------------- generator
+def test_velocity_matches_paper():
+    gold = _golden()
+    vx, vy = sy.paper_velocity()
+    fg, fs, nn, dr0 = gold["velocity_inputs_fg_fs_N_Dr0"]
+    assert sy.velocity_magnitude(fg, fs, int(nn), dr0) == pytest.approx(math.hypot(vx, vy))
+    assert vx == pytest.approx(gold["velocity_px_per_step"][0], abs=5e-4)
+    assert vy == pytest.approx(gold["velocity_px_per_step"][1], abs=5e-4)
+
+
+def test_default_weights_match_paper():
+    gold = _golden()
+    prm = o.Params(n=8, aperture_diam=4)
+    assert prm.alpha == gold["alpha"][0] and prm.lam == gold["lambda"][0]
+
+
+def test_phase_screen_structure_function():
+    """Kolmogorov D(rho) = 6.88 (rho/r0)^(5/3); the sampled spectral method with subharmonics
+    keeps the 5/3 law and loses part of the power at 1 px sampling."""
+    cfg = sy.config_single_64(20)
+    ratios = {2: [], 4: []}
+    for sid in range(24):
+        st = sy.Stream(sy.with_frames(cfg, 20).__class__(**{**cfg.__dict__, "stream_id": sid}))
+        ph = st.screen(0)
+        for rho in ratios:
+            d = 0.5 * (np.mean((ph[:, rho:] - ph[:, :-rho]) ** 2) + np.mean((ph[rho:, :] - ph[:-rho, :]) ** 2))
+            ratios[rho].append(d / (6.88 * (rho / st.r0_px) ** (5 / 3)))
+    r2, r4 = np.mean(ratios[2]), np.mean(ratios[4])
+    assert 0.6 < r2 < 1.1 and 0.6 < r4 < 1.1
+    assert abs(r2 - r4) < 0.15  # the 5/3 exponent holds between the two separations
