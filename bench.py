@@ -1,0 +1,324 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-frame DDH-MBIR step on GB300.
+
+Workload (one step = one frame of one EM iteration): a single synthetic sensor stream at
+256 x 256 (128 px pupil, D/r0 15, 1 px/frame frozen flow, SNR 5).  Frames come from a ring
+of pre-generated frames resident in HBM that is larger than L2, so every step reads a fresh
+frame from DRAM while the stream state (r, phi) stays resident.
+
+Prints one JSON line: frames/s (whole job), p50/p99 per-frame latency, the dominant kernel's
+roofline figures against the measured HBM copy bandwidth, the end-to-end rate through the
+host-buffer C ABI call, clocks sampled during the timed region, and the FP64 oracle timed
+on the host as the CPU baseline.  ``--impl reference`` times the oracle alone.
+Under torchrun each rank runs its own stream (replicas; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s and p50/p99 frame latency at 256² (1 EM iter/frame); HBM GB/s vs peak"
+UNIT = "frames/s"
+BYTES_PER_PX = 24  # y read (8) + r read/write (8) + phi read/write (8)
+RING_FRAMES = 320  # 320 x 512 KiB = 168 MB of frames > 129 MB L2
+WORKLOAD = ("single stream 256x256 grid, 128 px pupil, D/r0 15, 1 px/frame frozen flow, SNR 5, "
+            "1 EM iteration per frame")
+PROFILE = os.path.join(ROOT, "profiles", "k_ddh_step_256_single_stream.md")
+KERNEL_SOURCES = ["ddh_step.cu", "ddh_device.cuh", "ddh_kernels.cuh"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ring", type=int, default=RING_FRAMES)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+# ----------------------------------------------------------------------------- helpers
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2305_03284_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != kernel_source_sha():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            out, _ = self.proc.communicate(timeout=10)
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def synth_ring(count, stream_id=0):
+    import numpy as np
+    from synth import ddh_synth as sy
+    cfg = sy.replace(sy.config_single_256(frames=count), stream_id=stream_id)
+    st = sy.Stream(cfg)
+    ys = np.empty((count, 256, 256), np.complex64)
+    for i in range(count):
+        ys[i], _ = st.frame(i)
+    return cfg, ys
+
+
+# ------------------------------------------------------------------------- CPU oracle
+def oracle_frames_per_second(seconds, max_frames=None, warm=1):
+    """Time the FP64 oracle (as it stands) on the 256^2 stream for about `seconds`."""
+    from oracle import ddh_oracle as o
+    cfg, ys = synth_ring(64)
+    prm = o.default_params(cfg.n, cfg.aperture_diam, cfg.snr)
+    st = o.init_state(cfg.n)
+    for i in range(warm):
+        st, _ = o.step(st, ys[i % len(ys)], prm)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        st, _ = o.step(st, ys[(warm + done) % len(ys)], prm)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_frames is not None and done >= max_frames):
+            break
+    return done / el, done, el
+
+
+def cpu_worker(args):
+    fps, frames, el = oracle_frames_per_second(args.cpu_seconds)
+    print(json.dumps({"value": fps, "frames": frames, "seconds": el}))
+
+
+def cpu_baseline(seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--cpu-seconds", str(seconds)],
+                         env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": out.stderr[-300:]}
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": res["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{res['frames']} consecutive 256x256 frames of the same stream in {res['seconds']:.1f} s, "
+                      "FP64 NumPy oracle, 1 thread"}
+
+
+# ------------------------------------------------------------------------------ arms
+def run_reference(args):
+    rank, _, world = dist_info()
+    if rank != 0:
+        return
+    warm = min(args.warmup, 2)
+    # each step is one oracle frame; the count is capped so the run stays within minutes
+    fps_probe, _, _ = oracle_frames_per_second(0.0, max_frames=1, warm=warm)
+    steps = max(1, min(args.steps, int(120.0 * fps_probe)))
+    fps, frames, el = oracle_frames_per_second(1e9, max_frames=steps, warm=0)
+    nproc = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world,
+            "steps": frames, "warmup": warm, "ms_per_step": 1e3 * el / frames, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": 256, "streams": 1},
+            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{frames} of {args.steps} requested frames (bounded), host has {nproc} cores"},
+            "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local_rank, world = dist_info()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2305_03284_gb300 import build as _b
+    if rank == 0 or world == 1:
+        _b.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2305_03284_gb300 import ddh
+
+    cfg, ys_host = synth_ring(args.ring, stream_id=rank)
+    n = cfg.n
+    ring = torch.from_numpy(ys_host).cuda()
+    stream = torch.cuda.Stream()
+    p = ddh.default_params(n, cfg.aperture_diam, cfg.snr)
+    with torch.cuda.stream(stream):
+        s = ddh.Stream(p, stream=stream)
+        lib, h = ddh.lib(), s._h
+        ptrs = [ddh.c_void_p(ring[i].data_ptr()) for i in range(args.ring)]
+        for i in range(args.warmup):
+            ddh.check(lib.ddh_step(h, ptrs[i % args.ring]))
+        stream.synchronize()
+
+        def barrier():
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+        # ---- timed region: K frames back to back on the state's stream ------------------
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        with ClockSampler(local_rank) as clk:
+            e0.record(stream)
+            for i in range(args.steps):
+                lib.ddh_step(h, ptrs[(args.warmup + i) % args.ring])
+            e1.record(stream)
+            e1.synchronize()
+        barrier()
+        s.sync()
+        ms = e0.elapsed_time(e1)
+        # ---- per-frame latency, frame resident on the device (isolated frames) -----------
+        lat = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            a, b = ev[i]
+            a.record(stream)
+            lib.ddh_step(h, ptrs[i % args.ring])
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b) * 1e3)
+        s.sync()
+        # ---- end to end through the host-buffer call ------------------------------------
+        hring = torch.from_numpy(ys_host[:32]).pin_memory()
+        phi_out = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        ke = min(args.steps, 300)
+        for i in range(3):
+            s.step_host(hring[i], phi_out)
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(ke):
+            s.step_host(hring[i % 32], phi_out)
+        t_e2e = time.perf_counter() - t0
+        barrier()
+
+    tmax = torch.tensor([ms, t_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    ms, t_e2e = float(tmax[0]), float(tmax[1])
+    if rank != 0:
+        return
+    frames = args.steps * world
+    value = frames / (ms * 1e-3)
+    lat.sort()
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+    peak, peak_src = measured_peak_gbs()
+    bytes_per_launch = BYTES_PER_PX * n * n
+    avg_launch_s = ms * 1e-3 / args.steps
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": n, "streams_per_gpu": 1, "frames_ring": args.ring,
+                   "l2": f"inputs exceed L2: ring of {args.ring} frames = {args.ring * n * n * 8 / 1e6:.0f} MB",
+                   "parallelism": f"replicas x{world}"},
+        "latency_us": {"p50": p50, "p99": p99, "mean": sum(lat) / len(lat),
+                       "definition": "one frame resident in HBM, launch to phi written (CUDA events)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(), "kernel": "k_ddh_step<256>",
+                     "bytes_per_launch": bytes_per_launch, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": {"value": ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 4,
+                "steps": ke},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.cpu_worker:
+        return cpu_worker(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,124 @@
+/*
+ * libddh — Dynamic DH-MBIR per-frame EM step on one GB300 (sm_103a).
+ *
+ * C ABI: plain pointers and sizes only.  Every compute step runs in the library's own CUDA
+ * kernels; there is no CPU path.  All calls are asynchronous on the CUDA stream given to
+ * ddh_init() unless stated otherwise; errors found by the device (non-finite frame, a bounded
+ * wait that expired) are latched in a device status word and returned by the next call that
+ * synchronises (ddh_sync, ddh_phase/ddh_reflectance to host memory, ddh_strehl).
+ *
+ * Method: Sheikh, Pellizzari, Kisner, Buzzard, Bouman, "Dynamic DH-MBIR for Phase-Error
+ * Estimation from Streaming Digital-Holography Data" (arXiv:2305.03284).  Per frame (Fig. 1):
+ * Normalize (Eq. 4), RemoveTipTilt (Sec. 4), r-init (Eq. 3), N_k EM iterations (Sec. 3) on the
+ * isoplanatic model y = D_a D(exp(j phi)) F g + w (Eq. 1, Sec. 2).
+ *
+ * Layouts: an N x N image is row-major (index = row * N + col, row = y, col = x).  Frames are
+ * interleaved complex64 (re, im float pairs).  The aperture D_a is the disc of diameter
+ * `aperture_diam` px centred on ((N-1)/2, (N-1)/2).
+ */
+#ifndef DDH_H_
+#define DDH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes (negative) ------------------------------------------------------------ */
+#define DDH_OK 0
+#define DDH_EINVAL (-1)      /* bad argument (NULL, unsupported N, misaligned pointer, ...) */
+#define DDH_ENOMEM (-2)      /* device allocation failed */
+#define DDH_ECUDA (-3)       /* a CUDA runtime call failed (see ddh_last_cuda_error) */
+#define DDH_ETIMEOUT (-4)    /* a bounded device wait expired; that frame left the state as is */
+#define DDH_ENONFINITE (-5)  /* frame had a non-finite entry or zero variance; state unchanged */
+#define DDH_EBUDGET (-6)     /* admission refused: the memory budget would be exceeded */
+
+/* ---- parameters (Fig. 1 arguments lambda, alpha, N_k; Sec. 5.B values) -------------------- */
+typedef struct ddh_params {
+  int n;                /* grid side N: 64, 128 or 256 */
+  float aperture_diam;  /* pupil diameter in px, 0 < d <= N */
+  float lambda;         /* Eq. 3 weight of the back-projection term (paper: 0.45) */
+  float alpha;          /* Eq. 3 scale of |A^H y|^2 (paper: 0.025) */
+  int n_k;              /* EM iterations per frame, 1..16 (paper: 1) */
+  float noise_var;      /* sigma^2 of the noise after Normalize (> 0) */
+  float prior_p;        /* q-GGMRF shape p, 1 <= p < 2 */
+  float prior_q;        /* q-GGMRF shape q; must be 2 (finite surrogate weight at 0) */
+  float prior_T;        /* q-GGMRF threshold T > 0 */
+  float prior_sigma;    /* q-GGMRF scale sigma_r > 0 */
+  float r_floor;        /* lower bound on the reflectance (> 0) */
+  int tilt_mode;        /* 1: RemoveTipTilt each frame; 0: skip it */
+} ddh_params;
+
+typedef struct ddh_state ddh_state; /* opaque; owned by the library */
+
+/* Fill `p` with the defaults for grid `n`, pupil `aperture_diam` and a linear SNR over the
+ * pupil: lambda 0.45, alpha 0.025 (Sec. 5.B), n_k 1, noise_var 1/(1 + f SNR) with f the
+ * pupil fill fraction, prior p 1.1, q 2, T 1, sigma_r 0.1, r_floor 1e-10, tilt_mode 1. */
+int ddh_default_params(ddh_params *p, int n, float aperture_diam, float snr);
+
+/* Validate `p`, allocate the device state (r = 0, phi = 0, n = 0: Fig. 1 first line) and bind
+ * it to `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The library owns
+ * the state until ddh_free().  Returns DDH_OK or DDH_EINVAL / DDH_ENOMEM / DDH_ECUDA. */
+int ddh_init(ddh_state **out, const ddh_params *p, void *cuda_stream);
+
+/* One DDH-MBIR time step (Fig. 1 loop body) on frame `y_c64_dev`: device pointer to N*N
+ * interleaved complex64, 16-byte aligned, caller-owned; it must stay valid until the step has
+ * run in stream order.  Enqueues one kernel launch and returns; a non-finite frame is
+ * reported later (DDH_ENONFINITE) and leaves r and phi unchanged. */
+int ddh_step(ddh_state *s, const void *y_c64_dev);
+
+/* Same step, also writing the frame's intermediates into `trace_dev` (device, float32,
+ * ddh_trace_floats(N) entries): b = A^H y (complex, N*N), mu (complex, N*N), z = F mu
+ * (complex, N*N), r-init (N*N), s = E|g|^2 (N*N), then 8 scalars (mean re, mean im, scale,
+ * t_x, t_y, 0, 0, 0).  Complex fields are interleaved; all images row-major. */
+int ddh_step_trace(ddh_state *s, const void *y_c64_dev, float *trace_dev);
+size_t ddh_trace_floats(int n);
+
+/* One step from HOST memory: copies the frame in from `y_c64_host` (pinned for overlap),
+ * runs ddh_step, copies phi out to `phi_host_out` (N*N float32), and waits for completion.
+ * The device staging buffer is owned by the state. */
+int ddh_step_host(ddh_state *s, const void *y_c64_host, float *phi_host_out);
+
+/* WriteData (Fig. 1): stream-ordered copy of phi_n / r_n (N*N float32) into `out`, which may
+ * be device or host memory (host copies synchronise the stream and report latched errors). */
+int ddh_phase(const ddh_state *s, float *out);
+int ddh_reflectance(const ddh_state *s, float *out);
+
+/* Overwrite the state (r, phi: N*N float32, device or host pointers) and the frame count;
+ * used to resume from a checkpoint and by teacher-forced comparisons. */
+int ddh_set_state(ddh_state *s, const float *r, const float *phi, int64_t frame_index);
+int64_t ddh_frame_index(const ddh_state *s);
+
+/* Peak Strehl ratio of the current phase estimate against `phi_true_dev` (N*N float32,
+ * device): max |F^H(a exp(j(phi_true - phi)))|^2 / max |F^H a|^2 (Sec. 5.B).  Synchronous:
+ * the value lands in *out.  Evaluation only, never part of a step. */
+int ddh_strehl(ddh_state *s, const float *phi_true_dev, float *out);
+
+/* Advance `count` states by one frame each in one launch per grid size (states with equal N
+ * share one cluster-per-stream launch).  All states must share the stream of states[0]. */
+int ddh_step_batch(ddh_state *const *states, const void *const *y_c64_dev, int count);
+
+/* Unitary 2D DFT (Sec. 2, F) or its inverse (inverse != 0) of one N x N complex64 image,
+ * device in/out (may alias), on `cuda_stream`.  N as for ddh_params. */
+int ddh_fft2(const void *in_c64_dev, void *out_c64_dev, int n, int inverse, void *cuda_stream);
+
+/* Wait for the state's stream; return and clear any latched device error. */
+int ddh_sync(ddh_state *s);
+
+/* Checkpoint: `buf` (host) receives ddh_checkpoint_bytes(N) bytes: params, frame index, r,
+ * phi.  ddh_load restores a state with the same N. */
+size_t ddh_checkpoint_bytes(int n);
+int ddh_save(ddh_state *s, void *buf, size_t bytes);
+int ddh_load(ddh_state *s, const void *buf, size_t bytes);
+
+int ddh_free(ddh_state *s);
+const char *ddh_strerror(int code);
+const char *ddh_last_cuda_error(void);
+int ddh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDH_H_ */

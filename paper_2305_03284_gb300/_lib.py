@@ -1,0 +1,92 @@
+"""ctypes declarations of libddh's C ABI (include/ddh.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_float, c_int, c_int64, c_size_t, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libddh.so")
+
+DDH_OK = 0
+DDH_EINVAL = -1
+DDH_ENOMEM = -2
+DDH_ECUDA = -3
+DDH_ETIMEOUT = -4
+DDH_ENONFINITE = -5
+DDH_EBUDGET = -6
+
+
+class DdhParams(ctypes.Structure):
+    """Mirror of ``ddh_params`` (field order and types must match include/ddh.h)."""
+    _fields_ = [
+        ("n", c_int),
+        ("aperture_diam", c_float),
+        ("lam", c_float),
+        ("alpha", c_float),
+        ("n_k", c_int),
+        ("noise_var", c_float),
+        ("prior_p", c_float),
+        ("prior_q", c_float),
+        ("prior_T", c_float),
+        ("prior_sigma", c_float),
+        ("r_floor", c_float),
+        ("tilt_mode", c_int),
+    ]
+
+
+class DdhError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(what)
+
+
+_SIGS = {
+    "ddh_default_params": (c_int, [POINTER(DdhParams), c_int, c_float, c_float]),
+    "ddh_init": (c_int, [POINTER(c_void_p), POINTER(DdhParams), c_void_p]),
+    "ddh_step": (c_int, [c_void_p, c_void_p]),
+    "ddh_step_trace": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ddh_trace_floats": (c_size_t, [c_int]),
+    "ddh_step_host": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "ddh_phase": (c_int, [c_void_p, c_void_p]),
+    "ddh_reflectance": (c_int, [c_void_p, c_void_p]),
+    "ddh_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
+    "ddh_frame_index": (c_int64, [c_void_p]),
+    "ddh_strehl": (c_int, [c_void_p, c_void_p, POINTER(c_float)]),
+    "ddh_step_batch": (c_int, [POINTER(c_void_p), POINTER(c_void_p), c_int]),
+    "ddh_fft2": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
+    "ddh_sync": (c_int, [c_void_p]),
+    "ddh_checkpoint_bytes": (c_size_t, [c_int]),
+    "ddh_save": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "ddh_load": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "ddh_free": (c_int, [c_void_p]),
+    "ddh_strerror": (c_char_p, [c_int]),
+    "ddh_last_cuda_error": (c_char_p, []),
+    "ddh_version": (c_int, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libddh.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2305_03284_gb300.build.build()")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = h
+    return _lib
+
+
+def check(code: int) -> int:
+    if code != DDH_OK:
+        h = lib()
+        msg = h.ddh_strerror(code).decode()
+        if code == DDH_ECUDA or code == DDH_ENOMEM:
+            msg += f" ({h.ddh_last_cuda_error().decode()})"
+        raise DdhError(code, f"libddh error {code}: {msg}")
+    return code

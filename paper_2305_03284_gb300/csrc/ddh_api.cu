@@ -1,0 +1,428 @@
+// C ABI of libddh (declarations and contracts in include/ddh.h).
+//
+// Host side only: argument validation, device state ownership, parameter derivation, the
+// per-device twiddle tables and kernel attributes, error latching.  Every compute step is one
+// of the kernels in ddh_step.cu.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ddh.h"
+#include "ddh_kernels.cuh"
+
+struct ddh_state {
+  ddh_params prm;
+  ddh::KParams kp;
+  cudaStream_t stream;
+  int device;
+  float* r;
+  float* phi;
+  unsigned* status;
+  float2* ystage;
+  float* scalar;
+  const float2* tw;
+  int64_t frame;
+  int64_t ap_count;
+};
+
+namespace {
+
+constexpr int kVersion = 100;
+constexpr int kMaxDevices = 64;
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DDH_ENOMEM : DDH_ECUDA;
+}
+#define DDH_CUDA(call)                         \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+bool supported_n(int n) { return n == 64 || n == 128 || n == 256; }
+int n_slot(int n) { return n == 64 ? 0 : n == 128 ? 1 : 2; }
+
+std::mutex g_mu;
+bool g_configured[kMaxDevices][3] = {};
+float2* g_twiddle[kMaxDevices][3] = {};
+
+// Per-device, per-N setup: kernel attributes and the twiddle table exp(-2 pi i t / N),
+// evaluated in double precision and rounded once to float.
+int device_setup(int dev, int n, const float2** tw) {
+  if (dev < 0 || dev >= kMaxDevices) return DDH_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  const int s = n_slot(n);
+  if (!g_configured[dev][s]) {
+    int active = 0;
+    DDH_CUDA(ddh::configure(n, &active));
+    if (active < 1) {
+      std::snprintf(g_cuda_err, sizeof(g_cuda_err), "no resident cluster of %d CTAs x %zu B shared memory", n / 16,
+                    ddh::step_smem_bytes(n));
+      return DDH_ECUDA;
+    }
+    std::vector<float2> h(n);
+    for (int t = 0; t < n; ++t) {
+      const double a = -2.0 * M_PI * static_cast<double>(t) / static_cast<double>(n);
+      h[t] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(std::sin(a)));
+    }
+    float2* d = nullptr;
+    DDH_CUDA(cudaMalloc(&d, sizeof(float2) * n));
+    DDH_CUDA(cudaMemcpy(d, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    g_twiddle[dev][s] = d;
+    g_configured[dev][s] = true;
+  }
+  *tw = g_twiddle[dev][s];
+  return DDH_OK;
+}
+
+int64_t aperture_limit(float d) { return static_cast<int64_t>(std::floor(static_cast<double>(d) * d)); }
+
+int64_t aperture_count(int n, int64_t lim) {
+  int64_t c = 0;
+  for (int y = 0; y < n; ++y)
+    for (int x = 0; x < n; ++x) {
+      const int64_t dy = 2 * y - (n - 1), dx = 2 * x - (n - 1);
+      if (dx * dx + dy * dy <= lim) ++c;
+    }
+  return c;
+}
+
+int validate(const ddh_params* p) {
+  if (p == nullptr || !supported_n(p->n)) return DDH_EINVAL;
+  if (!(p->aperture_diam > 0.f && p->aperture_diam <= static_cast<float>(p->n))) return DDH_EINVAL;
+  if (!(p->lambda >= 0.f && p->lambda <= 1.f && p->alpha >= 0.f && std::isfinite(p->alpha))) return DDH_EINVAL;
+  if (p->n_k < 1 || p->n_k > 16) return DDH_EINVAL;
+  if (!(p->noise_var > 0.f && std::isfinite(p->noise_var))) return DDH_EINVAL;
+  if (!(p->prior_p >= 1.f && p->prior_p < 2.f)) return DDH_EINVAL;
+  if (p->prior_q != 2.f) return DDH_EINVAL;
+  if (!(p->prior_T > 0.f && p->prior_sigma > 0.f && std::isfinite(p->prior_T) && std::isfinite(p->prior_sigma)))
+    return DDH_EINVAL;
+  if (!(p->r_floor > 0.f && std::isfinite(p->r_floor))) return DDH_EINVAL;
+  if (p->tilt_mode != 0 && p->tilt_mode != 1) return DDH_EINVAL;
+  return DDH_OK;
+}
+
+ddh::KParams derive(const ddh_params& p) {
+  ddh::KParams k{};
+  k.ap_lim = static_cast<int>(aperture_limit(p.aperture_diam));
+  k.tilt_mode = p.tilt_mode;
+  k.n_k = p.n_k;
+  k.lam1 = static_cast<float>(1.0 - static_cast<double>(p.lambda));
+  k.lam_alpha = static_cast<float>(static_cast<double>(p.lambda) * p.alpha);
+  k.noise_var = p.noise_var;
+  const double ts = static_cast<double>(p.prior_T) * p.prior_sigma;
+  k.w0 = static_cast<float>(std::pow(ts, static_cast<double>(p.prior_p) - 2.0) *
+                            std::pow(static_cast<double>(p.prior_sigma), -static_cast<double>(p.prior_p)));
+  k.inv_tsig = static_cast<float>(1.0 / ts);
+  k.q_minus_p = static_cast<float>(static_cast<double>(p.prior_q) - p.prior_p);
+  k.q_over_p = static_cast<float>(static_cast<double>(p.prior_q) / p.prior_p);
+  k.r_floor = p.r_floor;
+  return k;
+}
+
+bool is_host_pointer(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+size_t image_bytes(int n) { return sizeof(float) * static_cast<size_t>(n) * n; }
+
+int check_status(ddh_state* s) {
+  unsigned h = 0;
+  DDH_CUDA(cudaMemcpyAsync(&h, s->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream));
+  DDH_CUDA(cudaStreamSynchronize(s->stream));
+  if (h == 0) return DDH_OK;
+  DDH_CUDA(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream));
+  DDH_CUDA(cudaStreamSynchronize(s->stream));
+  if (h & ddh::kStatusTimeout) return DDH_ETIMEOUT;
+  return DDH_ENONFINITE;
+}
+
+ddh::FrameArgs frame_args(ddh_state* s, const void* y, float* trace) {
+  ddh::FrameArgs f{};
+  f.y = static_cast<const float2*>(y);
+  f.r = s->r;
+  f.phi = s->phi;
+  f.status = s->status;
+  f.trace = trace;
+  return f;
+}
+
+int enqueue(ddh_state* s, const void* y, float* trace) {
+  if (s == nullptr || y == nullptr) return DDH_EINVAL;
+  if (reinterpret_cast<uintptr_t>(y) % 16 != 0) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  ddh::StepBatch b{};
+  b.prm[0] = s->kp;
+  b.fa[0] = frame_args(s, y, trace);
+  b.tw = s->tw;
+  b.count = 1;
+  DDH_CUDA(ddh::launch_step(s->prm.n, b, s->stream));
+  s->frame += 1;
+  return DDH_OK;
+}
+
+struct CkptHeader {
+  uint32_t magic;
+  uint32_t version;
+  ddh_params prm;
+  int64_t frame;
+};
+constexpr uint32_t kMagic = 0x31484444u;  // "DDH1"
+
+}  // namespace
+
+extern "C" {
+
+int ddh_version(void) { return kVersion; }
+
+const char* ddh_last_cuda_error(void) { return g_cuda_err; }
+
+const char* ddh_strerror(int code) {
+  switch (code) {
+    case DDH_OK: return "ok";
+    case DDH_EINVAL: return "invalid argument";
+    case DDH_ENOMEM: return "device allocation failed";
+    case DDH_ECUDA: return "CUDA runtime error";
+    case DDH_ETIMEOUT: return "bounded device wait expired; frame dropped";
+    case DDH_ENONFINITE: return "frame has a non-finite entry or zero variance; frame dropped";
+    case DDH_EBUDGET: return "memory budget exceeded";
+    default: return "unknown error";
+  }
+}
+
+int ddh_default_params(ddh_params* p, int n, float aperture_diam, float snr) {
+  if (p == nullptr || !supported_n(n) || !(aperture_diam > 0.f) || !(snr >= 0.f)) return DDH_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->n = n;
+  p->aperture_diam = aperture_diam;
+  p->lambda = 0.45f;
+  p->alpha = 0.025f;
+  p->n_k = 1;
+  const double f = static_cast<double>(aperture_count(n, aperture_limit(aperture_diam))) /
+                   (static_cast<double>(n) * n);
+  p->noise_var = static_cast<float>(1.0 / (1.0 + f * snr));
+  p->prior_p = 1.1f;
+  p->prior_q = 2.0f;
+  p->prior_T = 1.0f;
+  p->prior_sigma = 0.1f;
+  p->r_floor = 1e-10f;
+  p->tilt_mode = 1;
+  return DDH_OK;
+}
+
+int ddh_init(ddh_state** out, const ddh_params* p, void* cuda_stream) {
+  if (out == nullptr) return DDH_EINVAL;
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc != DDH_OK) return rc;
+  int dev = 0;
+  DDH_CUDA(cudaGetDevice(&dev));
+  const float2* tw = nullptr;
+  rc = device_setup(dev, p->n, &tw);
+  if (rc != DDH_OK) return rc;
+  ddh_state* s = new ddh_state{};
+  s->prm = *p;
+  s->kp = derive(*p);
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  s->device = dev;
+  s->tw = tw;
+  s->ap_count = aperture_count(p->n, aperture_limit(p->aperture_diam));
+  const size_t img = image_bytes(p->n);
+  cudaError_t e = cudaMalloc(&s->r, img);
+  if (e == cudaSuccess) e = cudaMalloc(&s->phi, img);
+  if (e == cudaSuccess) e = cudaMalloc(&s->status, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&s->ystage, 2 * img);
+  if (e == cudaSuccess) e = cudaMalloc(&s->scalar, 256);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->r, 0, img, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->phi, 0, img, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->status, 0, 256, s->stream);
+  if (e != cudaSuccess) {
+    const int code = cuda_fail(e);
+    ddh_free(s);
+    return code;
+  }
+  *out = s;
+  return DDH_OK;
+}
+
+size_t ddh_trace_floats(int n) { return static_cast<size_t>(n) * n * 8 + 8; }
+
+int ddh_step(ddh_state* s, const void* y) { return enqueue(s, y, nullptr); }
+
+int ddh_step_trace(ddh_state* s, const void* y, float* trace) {
+  if (trace == nullptr) return DDH_EINVAL;
+  return enqueue(s, y, trace);
+}
+
+int ddh_step_host(ddh_state* s, const void* y_host, float* phi_host_out) {
+  if (s == nullptr || y_host == nullptr || phi_host_out == nullptr) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  const size_t img = image_bytes(s->prm.n);
+  DDH_CUDA(cudaMemcpyAsync(s->ystage, y_host, 2 * img, cudaMemcpyHostToDevice, s->stream));
+  int rc = enqueue(s, s->ystage, nullptr);
+  if (rc != DDH_OK) return rc;
+  DDH_CUDA(cudaMemcpyAsync(phi_host_out, s->phi, img, cudaMemcpyDeviceToHost, s->stream));
+  return check_status(s);
+}
+
+static int copy_out(const ddh_state* cs, const float* src, float* out) {
+  ddh_state* s = const_cast<ddh_state*>(cs);
+  if (s == nullptr || out == nullptr) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_CUDA(cudaMemcpyAsync(out, src, image_bytes(s->prm.n), cudaMemcpyDefault, s->stream));
+  if (is_host_pointer(out)) return check_status(s);
+  return DDH_OK;
+}
+
+int ddh_phase(const ddh_state* s, float* out) { return s ? copy_out(s, s->phi, out) : DDH_EINVAL; }
+int ddh_reflectance(const ddh_state* s, float* out) { return s ? copy_out(s, s->r, out) : DDH_EINVAL; }
+
+int ddh_set_state(ddh_state* s, const float* r, const float* phi, int64_t frame_index) {
+  if (s == nullptr || r == nullptr || phi == nullptr || frame_index < 0) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  const size_t img = image_bytes(s->prm.n);
+  DDH_CUDA(cudaMemcpyAsync(s->r, r, img, cudaMemcpyDefault, s->stream));
+  DDH_CUDA(cudaMemcpyAsync(s->phi, phi, img, cudaMemcpyDefault, s->stream));
+  if (is_host_pointer(r) || is_host_pointer(phi)) DDH_CUDA(cudaStreamSynchronize(s->stream));
+  s->frame = frame_index;
+  return DDH_OK;
+}
+
+int64_t ddh_frame_index(const ddh_state* s) { return s ? s->frame : -1; }
+
+int ddh_strehl(ddh_state* s, const float* phi_true_dev, float* out) {
+  if (s == nullptr || phi_true_dev == nullptr || out == nullptr) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  ddh::StrehlArgs a{};
+  a.phi_est = s->phi;
+  a.phi_true = phi_true_dev;
+  a.out = s->scalar;
+  a.tw = s->tw;
+  a.ap_lim = s->kp.ap_lim;
+  a.inv_ap_count2 = static_cast<float>(1.0 / (static_cast<double>(s->ap_count) * s->ap_count));
+  DDH_CUDA(ddh::launch_strehl(s->prm.n, a, s->stream));
+  DDH_CUDA(cudaMemcpyAsync(out, s->scalar, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  return check_status(s);
+}
+
+int ddh_step_batch(ddh_state* const* states, const void* const* ys, int count) {
+  if (states == nullptr || ys == nullptr || count < 0) return DDH_EINVAL;
+  if (count == 0) return DDH_OK;
+  for (int i = 0; i < count; ++i) {
+    if (states[i] == nullptr || ys[i] == nullptr) return DDH_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ys[i]) % 16 != 0) return DDH_EINVAL;
+    if (states[i]->stream != states[0]->stream || states[i]->device != states[0]->device) return DDH_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (states[j] == states[i]) return DDH_EINVAL;  // a stream advances once per batch
+  }
+  DDH_CUDA(cudaSetDevice(states[0]->device));
+  const int sizes[3] = {64, 128, 256};
+  for (int n : sizes) {
+    ddh::StepBatch b{};
+    b.count = 0;
+    for (int i = 0; i < count; ++i) {
+      ddh_state* s = states[i];
+      if (s->prm.n != n) continue;
+      b.prm[b.count] = s->kp;
+      b.fa[b.count] = frame_args(s, ys[i], nullptr);
+      b.tw = s->tw;
+      ++b.count;
+      if (b.count == ddh::kMaxBatch) {
+        DDH_CUDA(ddh::launch_step(n, b, states[0]->stream));
+        b.count = 0;
+      }
+    }
+    if (b.count > 0) DDH_CUDA(ddh::launch_step(n, b, states[0]->stream));
+  }
+  for (int i = 0; i < count; ++i) states[i]->frame += 1;
+  return DDH_OK;
+}
+
+int ddh_fft2(const void* in, void* out, int n, int inverse, void* cuda_stream) {
+  if (in == nullptr || out == nullptr || !supported_n(n)) return DDH_EINVAL;
+  int dev = 0;
+  DDH_CUDA(cudaGetDevice(&dev));
+  const float2* tw = nullptr;
+  int rc = device_setup(dev, n, &tw);
+  if (rc != DDH_OK) return rc;
+  ddh::Fft2Args a{};
+  a.in = static_cast<const float2*>(in);
+  a.out = static_cast<float2*>(out);
+  a.tw = tw;
+  a.inverse = inverse ? 1 : 0;
+  DDH_CUDA(ddh::launch_fft2(n, a, static_cast<cudaStream_t>(cuda_stream)));
+  return DDH_OK;
+}
+
+int ddh_sync(ddh_state* s) {
+  if (s == nullptr) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  return check_status(s);
+}
+
+size_t ddh_checkpoint_bytes(int n) {
+  if (!supported_n(n)) return 0;
+  return sizeof(CkptHeader) + 2 * image_bytes(n);
+}
+
+int ddh_save(ddh_state* s, void* buf, size_t bytes) {
+  if (s == nullptr || buf == nullptr || bytes < ddh_checkpoint_bytes(s->prm.n)) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  CkptHeader h{};
+  h.magic = kMagic;
+  h.version = kVersion;
+  h.prm = s->prm;
+  h.frame = s->frame;
+  std::memcpy(buf, &h, sizeof(h));
+  char* p = static_cast<char*>(buf) + sizeof(h);
+  const size_t img = image_bytes(s->prm.n);
+  DDH_CUDA(cudaMemcpyAsync(p, s->r, img, cudaMemcpyDeviceToHost, s->stream));
+  DDH_CUDA(cudaMemcpyAsync(p + img, s->phi, img, cudaMemcpyDeviceToHost, s->stream));
+  return check_status(s);
+}
+
+int ddh_load(ddh_state* s, const void* buf, size_t bytes) {
+  if (s == nullptr || buf == nullptr || bytes < sizeof(CkptHeader)) return DDH_EINVAL;
+  CkptHeader h{};
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kMagic || h.prm.n != s->prm.n || bytes < ddh_checkpoint_bytes(s->prm.n)) return DDH_EINVAL;
+  if (validate(&h.prm) != DDH_OK) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  const char* p = static_cast<const char*>(buf) + sizeof(h);
+  const size_t img = image_bytes(s->prm.n);
+  DDH_CUDA(cudaMemcpyAsync(s->r, p, img, cudaMemcpyHostToDevice, s->stream));
+  DDH_CUDA(cudaMemcpyAsync(s->phi, p + img, img, cudaMemcpyHostToDevice, s->stream));
+  DDH_CUDA(cudaStreamSynchronize(s->stream));
+  s->prm = h.prm;
+  s->kp = derive(h.prm);
+  s->ap_count = aperture_count(h.prm.n, aperture_limit(h.prm.aperture_diam));
+  s->frame = h.frame;
+  return DDH_OK;
+}
+
+int ddh_free(ddh_state* s) {
+  if (s == nullptr) return DDH_OK;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  cudaFree(s->r);
+  cudaFree(s->phi);
+  cudaFree(s->status);
+  cudaFree(s->ystage);
+  cudaFree(s->scalar);
+  delete s;
+  return DDH_OK;
+}
+
+}  // extern "C"

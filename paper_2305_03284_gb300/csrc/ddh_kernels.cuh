@@ -1,0 +1,73 @@
+// Kernel-side interface of libddh: launch parameter blocks and launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ddh {
+
+constexpr int kMaxBatch = 32;   // streams per launch (kernel parameter block stays < 4 KB)
+constexpr int kThreads = 512;   // 16 warps per CTA
+constexpr int kRowsPerCta = 16; // local rows (cyclic) == slab columns per CTA
+
+// status bits latched by the kernels in the per-stream device status word
+constexpr unsigned kStatusNonFinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+
+// Method parameters in the form the kernels use (derived on the host from ddh_params).
+struct KParams {
+  int ap_lim;        // floor(d^2): pixel in pupil iff (2x-(N-1))^2 + (2y-(N-1))^2 <= ap_lim
+  int tilt_mode;     // RemoveTipTilt on/off
+  int n_k;           // EM iterations per frame
+  float lam1;        // 1 - lambda
+  float lam_alpha;   // lambda * alpha
+  float noise_var;   // sigma^2
+  float w0;          // (T sigma_r)^(p-2) sigma_r^(-p)
+  float inv_tsig;    // 1 / (T sigma_r)
+  float q_minus_p;   // q - p
+  float q_over_p;    // q / p
+  float r_floor;
+};
+
+// One stream's frame: input, state (in/out), status word, optional trace output.
+struct FrameArgs {
+  const float2* y;
+  float* r;
+  float* phi;
+  unsigned* status;
+  float* trace;
+};
+
+struct StepBatch {
+  KParams prm[kMaxBatch];
+  FrameArgs fa[kMaxBatch];
+  const float2* tw;  // twiddle table exp(-2 pi i t / N), t < N
+  int count;
+};
+
+struct StrehlArgs {
+  const float* phi_est;
+  const float* phi_true;
+  float* out;           // one float
+  const float2* tw;
+  int ap_lim;
+  float inv_ap_count2;  // 1 / (sum a)^2
+};
+
+struct Fft2Args {
+  const float2* in;
+  float2* out;
+  const float2* tw;
+  int inverse;
+};
+
+// Launchers (return the CUDA error of the launch).  `n` selects the template instance.
+cudaError_t launch_step(int n, const StepBatch& b, cudaStream_t st);
+cudaError_t launch_strehl(int n, const StrehlArgs& a, cudaStream_t st);
+cudaError_t launch_fft2(int n, const Fft2Args& a, cudaStream_t st);
+// One-time per-device function attributes (shared memory size, cluster size); also checks
+// that a cluster of this shape can be resident.  Returns cudaSuccess or the failing error.
+cudaError_t configure(int n, int* max_active_clusters);
+size_t step_smem_bytes(int n);
+
+}  // namespace ddh

@@ -1,0 +1,551 @@
+// Cluster-per-stream kernels of the DDH-MBIR frame step (sm_103a).
+//
+// One thread-block cluster of C = N/16 CTAs (512 threads each) owns one stream's frame.
+// CTA k holds, in shared memory,
+//   * rows  rho = k + C l (l = 0..15) of the pupil plane: the frame y, phi, and a row buffer;
+//   * the column slab x = 16 k .. 16 k + 15 of the image plane: a column buffer (one column
+//     per warp, contiguous), r, the r-init copy and s = E|g|^2.
+// The 2-D DFT is a row pass (one warp per row), a transpose through distributed shared
+// memory (remote stores into the owner CTA's buffer), and a column pass.  Cluster barriers
+// separate the frame's global dependencies:
+//   B1 Normalize / tip-tilt statistics   B2 row IFFT -> columns   B3 r-init + column FFT -> rows
+//   B4..B7 the four ICD colours (the last also guards shared memory until every reader is done).
+// Per frame the kernel reads y (8 B/px), phi and r (4 B/px each) and writes phi and r.
+#include <cooperative_groups.h>
+
+#include "ddh_device.cuh"
+#include "ddh_kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ddh {
+
+template <int N>
+struct StepLayout {
+  static constexpr int C = N / kRowsPerCta;    // CTAs per cluster
+  static constexpr int R = kRowsPerCta;        // local rows
+  static constexpr int W = kRowsPerCta;        // slab columns
+  static constexpr int CS = N + 1;             // padded column stride (floats / float2)
+  static constexpr size_t al(size_t v) { return (v + 127) & ~size_t(127); }
+  static constexpr size_t tw = 0;
+  static constexpr size_t rowbuf = al(tw + N * 8);
+  static constexpr size_t colbuf = al(rowbuf + size_t(R) * N * 8);
+  static constexpr size_t ybuf = al(colbuf + size_t(W) * CS * 8);
+  static constexpr size_t phib = al(ybuf + size_t(R) * N * 8);
+  static constexpr size_t rS = al(phib + size_t(R) * N * 4);
+  static constexpr size_t r0S = al(rS + size_t(W) * CS * 4);
+  static constexpr size_t sS = al(r0S + size_t(W) * CS * 4);
+  static constexpr size_t red = al(sS + size_t(W) * CS * 4);  // 16 warps x 8 floats
+  static constexpr size_t pub = al(red + 16 * 8 * 4);         // 8 published floats
+  static constexpr size_t glob = al(pub + 8 * 4);             // 8 combined floats
+  static constexpr size_t mbar = al(glob + 8 * 4);
+  static constexpr size_t total = al(mbar + 16);
+};
+
+// Chan et al. pairwise update of (count, complex mean, M2 = sum |y - mean|^2).
+__device__ __forceinline__ void chan_combine(float& n_a, float2& m_a, float& q_a, float n_b, float2 m_b,
+                                             float q_b) {
+  const float n = n_a + n_b;
+  const float2 d = c_sub(m_b, m_a);
+  const float f = n_b / n;
+  m_a = make_float2(fmaf(d.x, f, m_a.x), fmaf(d.y, f, m_a.y));
+  q_a = q_a + q_b + c_abs2(d) * (n_a * f);
+  n_a = n;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant__ StepBatch batch) {
+  using L = StepLayout<N>;
+  constexpr int C = L::C, R = L::R, W = L::W, CS = L::CS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int k = static_cast<int>(cluster.block_rank());
+  const int sidx = blockIdx.x / C;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const KParams P = batch.prm[sidx];
+  const FrameArgs A = batch.fa[sidx];
+
+  float2* tw = reinterpret_cast<float2*>(smem + L::tw);
+  float2* rowbuf = reinterpret_cast<float2*>(smem + L::rowbuf);
+  float2* colbuf = reinterpret_cast<float2*>(smem + L::colbuf);
+  float2* ybuf = reinterpret_cast<float2*>(smem + L::ybuf);
+  float* phib = reinterpret_cast<float*>(smem + L::phib);
+  float* rS = reinterpret_cast<float*>(smem + L::rS);
+  float* r0S = reinterpret_cast<float*>(smem + L::r0S);
+  float* sS = reinterpret_cast<float*>(smem + L::sS);
+  float* red = reinterpret_cast<float*>(smem + L::red);
+  float* pub = reinterpret_cast<float*>(smem + L::pub);
+  float* glob = reinterpret_cast<float*>(smem + L::glob);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + L::mbar);
+  const float cc = 0.5f * static_cast<float>(N - 1);
+  const float invN = 1.f / static_cast<float>(N);
+
+  // ---- phase 0: stage y rows by TMA; phi rows, r slab, twiddles by plain loads ----------
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(mbar, static_cast<uint32_t>(R * N * sizeof(float2)));
+    for (int l = 0; l < R; ++l) {
+      const int rho = k + C * l;
+      tma_load_1d(ybuf + l * N, A.y + static_cast<size_t>(rho) * N, N * sizeof(float2), mbar);
+    }
+  }
+  for (int i = tid; i < N; i += kThreads) tw[i] = batch.tw[i];
+  for (int i = tid; i < R * N; i += kThreads) {
+    const int l = i / N, x = i - l * N;
+    phib[i] = A.phi[static_cast<size_t>(k + C * l) * N + x];
+  }
+  for (int i = tid; i < N * W; i += kThreads) {
+    const int rho = i / W, cl = i - rho * W;
+    rS[cl * CS + rho] = A.r[static_cast<size_t>(rho) * N + W * k + cl];
+  }
+  for (int i = tid; i < W * CS; i += kThreads) colbuf[i] = make_float2(0.f, 0.f);
+  // bounded wait: on expiry the frame is dropped (flag carried into the B1 statistics)
+  const bool loaded = mbar_wait_bounded(mbar, 0, 1u << 22);
+  __syncthreads();
+
+  // ---- phase 1: per-row statistics (Normalize, Eq. 4) and tip/tilt sums (Sec. 4) --------
+  {
+    const int l = warp, rho = k + C * l;
+    const float2* yr = ybuf + l * N;
+    float sre = 0.f, sim = 0.f;
+    for (int x = lane; x < N; x += 32) { sre += yr[x].x; sim += yr[x].y; }
+    sre = warp_sum(sre);
+    sim = warp_sum(sim);
+    const float2 mrow = make_float2(sre * invN, sim * invN);
+    float q = 0.f;
+    for (int x = lane; x < N; x += 32) q += c_abs2(c_sub(yr[x], mrow));
+    q = warp_sum(q);
+    float txs = 0.f, txc = 0.f, tys = 0.f, tyc = 0.f;
+    if (P.tilt_mode) {
+      const float* pr = phib + l * N;
+      const int dy2 = ap_dist2(rho, N);
+      const int dy2n = rho + 1 < N ? ap_dist2(rho + 1, N) : (1 << 30);
+      for (int x = lane; x < N; x += 32) {
+        const int dx2 = ap_dist2(x, N);
+        if (dx2 + dy2 > P.ap_lim) continue;
+        if (x + 1 < N && ap_dist2(x + 1, N) + dy2 <= P.ap_lim) {
+          txs += wrap_pi(pr[x + 1] - pr[x]);
+          txc += 1.f;
+        }
+        if (dx2 + dy2n <= P.ap_lim) {
+          tys += wrap_pi(A.phi[static_cast<size_t>(rho + 1) * N + x] - pr[x]);
+          tyc += 1.f;
+        }
+      }
+      txs = warp_sum(txs); txc = warp_sum(txc); tys = warp_sum(tys); tyc = warp_sum(tyc);
+    }
+    if (lane == 0) {
+      float* o = red + warp * 8;
+      o[0] = mrow.x; o[1] = mrow.y; o[2] = q; o[3] = txs; o[4] = txc; o[5] = tys; o[6] = tyc;
+      o[7] = loaded ? 0.f : 1.f;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float n_a = static_cast<float>(N), q_a = red[2];
+    float2 m_a = make_float2(red[0], red[1]);
+    float t0 = red[3], t1 = red[4], t2 = red[5], t3 = red[6], bad = red[7];
+    for (int w = 1; w < 16; ++w) {
+      const float* o = red + w * 8;
+      chan_combine(n_a, m_a, q_a, static_cast<float>(N), make_float2(o[0], o[1]), o[2]);
+      t0 += o[3]; t1 += o[4]; t2 += o[5]; t3 += o[6]; bad += o[7];
+    }
+    pub[0] = m_a.x; pub[1] = m_a.y; pub[2] = q_a; pub[3] = t0; pub[4] = t1; pub[5] = t2; pub[6] = t3;
+    pub[7] = bad;
+  }
+  cluster.sync();  // B1
+  if (tid == 0) {
+    const float nb = static_cast<float>(R * N);
+    float n_a = nb, q_a = 0.f;
+    float2 m_a = make_float2(0.f, 0.f);
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, bad = 0.f;
+    for (int q = 0; q < C; ++q) {
+      const float* o = cluster.map_shared_rank(pub, q);
+      if (q == 0) { m_a = make_float2(o[0], o[1]); q_a = o[2]; }
+      else chan_combine(n_a, m_a, q_a, nb, make_float2(o[0], o[1]), o[2]);
+      t0 += o[3]; t1 += o[4]; t2 += o[5]; t3 += o[6]; bad += o[7];
+    }
+    const float scale = sqrtf(static_cast<float>(N) * static_cast<float>(N) / q_a);
+    const bool finite = isfinite(m_a.x) && isfinite(m_a.y) && isfinite(q_a) && q_a > 0.f && isfinite(scale);
+    glob[0] = m_a.x;
+    glob[1] = m_a.y;
+    glob[2] = scale;
+    glob[3] = (P.tilt_mode && t1 > 0.f) ? t0 / t1 : 0.f;
+    glob[4] = (P.tilt_mode && t3 > 0.f) ? t2 / t3 : 0.f;
+    glob[5] = (!finite || bad > 0.f) ? 1.f : 0.f;
+    if (k == 0 && A.status != nullptr) {
+      unsigned bits = 0;
+      if (!finite) bits |= kStatusNonFinite;
+      if (bad > 0.f) bits |= kStatusTimeout;
+      if (bits) atomicOr(A.status, bits);
+    }
+    if (k == 0 && A.trace != nullptr) {
+      float* st = A.trace + static_cast<size_t>(N) * N * 8;
+      st[0] = m_a.x; st[1] = m_a.y; st[2] = scale; st[3] = glob[3]; st[4] = glob[4];
+      st[5] = 0.f; st[6] = 0.f; st[7] = 0.f;
+    }
+  }
+  __syncthreads();
+  const float2 ymean = make_float2(glob[0], glob[1]);
+  const float scale = glob[2];
+  const float tx = glob[3], ty = glob[4];
+  if (glob[5] != 0.f) {  // uniform across the cluster: every CTA combined the same partials
+    cluster.sync();
+    return;
+  }
+
+  for (int it = 0; it < P.n_k; ++it) {
+    const bool first = (it == 0);
+    float* trace = first ? A.trace : nullptr;
+    // ---- phase 2: back-projection prologue a e^{-j phi} y~ and row IFFT (aperture rows) --
+    if (!first) {
+      // the scatter below writes only aperture rows of colbuf; clear the others again
+      for (int i = tid; i < W * N; i += kThreads) {
+        const int cl = i / N, rho = i - cl * N;
+        if (ap_dist2(rho, N) > P.ap_lim) colbuf[cl * CS + rho] = make_float2(0.f, 0.f);
+      }
+    }
+    {
+      const int l = warp, rho = k + C * l;
+      const int dy2 = ap_dist2(rho, N);
+      float2* rb = rowbuf + l * N;
+      float* pr = phib + l * N;
+      const float2* yr = ybuf + l * N;
+      if (dy2 <= P.ap_lim) {
+        const float tyr = ty * (static_cast<float>(rho) - cc);
+        for (int x = lane; x < N; x += 32) {
+          if (ap_dist2(x, N) + dy2 <= P.ap_lim) {
+            float ph = pr[x];
+            if (first && P.tilt_mode) ph = wrap_pi(ph - fmaf(tx, static_cast<float>(x) - cc, tyr));
+            pr[x] = ph;
+            const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
+            float sn, cs;
+            sincosf(ph, &sn, &cs);
+            rb[x] = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
+          } else {
+            rb[x] = make_float2(0.f, 0.f);
+            pr[x] = 0.f;
+          }
+        }
+        __syncwarp();
+        fft_row<N, +1>(rb, tw, lane);
+        for (int x = lane; x < N; x += 32) {
+          float2* dst = cluster.map_shared_rank(colbuf, x / W);
+          dst[(x % W) * CS + rho] = rb[x];
+        }
+      } else {
+        for (int x = lane; x < N; x += 32) pr[x] = 0.f;
+      }
+    }
+    cluster.sync();  // B2
+    // ---- phase 3: column IFFT, r-init (Eq. 3) + E-step, column FFT of mu, scatter ---------
+    {
+      const int cl = warp;
+      float2* cb = colbuf + cl * CS;
+      fft_row<N, +1>(cb, tw, lane);
+      for (int rho = lane; rho < N; rho += 32) {
+        const float2 b = c_scale(cb[rho], invN);
+        const float rp = rS[cl * CS + rho];
+        const float ri = first ? fmaxf(fmaf(P.lam1, rp, P.lam_alpha * c_abs2(b)), P.r_floor) : rp;
+        const float wgt = ri / (ri + P.noise_var);
+        const float2 mu = c_scale(b, wgt);
+        const float s = fmaf(P.noise_var, wgt, c_abs2(mu));
+        cb[rho] = mu;
+        rS[cl * CS + rho] = ri;
+        r0S[cl * CS + rho] = ri;
+        sS[cl * CS + rho] = s;
+        if (trace != nullptr) {
+          const size_t gi = static_cast<size_t>(rho) * N + W * k + cl;
+          const size_t M = static_cast<size_t>(N) * N;
+          reinterpret_cast<float2*>(trace)[gi] = b;
+          reinterpret_cast<float2*>(trace)[M + gi] = mu;
+          trace[6 * M + gi] = ri;
+          trace[7 * M + gi] = s;
+        }
+      }
+      __syncwarp();
+      fft_row<N, -1>(cb, tw, lane);
+      for (int rho = lane; rho < N; rho += 32) {
+        if (ap_dist2(rho, N) <= P.ap_lim) {
+          float2* dst = cluster.map_shared_rank(rowbuf, rho % C);
+          dst[(rho / C) * N + W * k + cl] = cb[rho];
+        }
+      }
+    }
+    cluster.sync();  // B3
+    // ---- phase 4: row FFT of mu (aperture rows) and phase M-step ------------------------
+    {
+      const int l = warp, rho = k + C * l;
+      const int dy2 = ap_dist2(rho, N);
+      float2* rb = rowbuf + l * N;
+      float* pr = phib + l * N;
+      const float2* yr = ybuf + l * N;
+      float* phi_out = A.phi + static_cast<size_t>(rho) * N;
+      if (dy2 <= P.ap_lim) {
+        fft_row<N, -1>(rb, tw, lane);
+        for (int x = lane; x < N; x += 32) {
+          float out = 0.f;
+          if (ap_dist2(x, N) + dy2 <= P.ap_lim) {
+            const float2 z = c_scale(rb[x], invN);
+            const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
+            // v = y~ conj(z)
+            const float vr = fmaf(yt.x, z.x, yt.y * z.y);
+            const float vi = fmaf(yt.y, z.x, -yt.x * z.y);
+            out = (vr != 0.f || vi != 0.f) ? atan2f(vi, vr) : pr[x];
+            pr[x] = out;
+            if (trace != nullptr) {
+              const size_t M = static_cast<size_t>(N) * N;
+              reinterpret_cast<float2*>(trace)[2 * M + static_cast<size_t>(rho) * N + x] = z;
+            }
+          }
+          phi_out[x] = out;
+        }
+      } else {
+        for (int x = lane; x < N; x += 32) phi_out[x] = 0.f;
+      }
+    }
+    // ---- phase 5: r M-step, 4-colour ICD sweep on the q-GGMRF surrogate ------------------
+    for (int c = 0; c < 4; ++c) {
+      const int cx = c & 1, cy = c >> 1;  // colours (0,0), (1,0), (0,1), (1,1)
+      for (int idx = tid; idx < 4 * N; idx += kThreads) {
+        const int cl = cx + 2 * (idx & 7);
+        const int rho = cy + 2 * (idx >> 3);
+        const int x = W * k + cl;
+        const float r0i = r0S[cl * CS + rho];
+        float Wsum = 0.f, Csum = 0.f;
+#pragma unroll
+        for (int nb = 0; nb < 8; ++nb) {
+          const int dy = (nb < 2) ? (nb == 0 ? -1 : 1) : (nb < 4 ? 0 : (nb < 6 ? -1 : 1));
+          const int dx = (nb < 2) ? 0 : (nb < 4 ? (nb == 2 ? -1 : 1) : ((nb & 1) ? 1 : -1));
+          const int rr = rho + dy, xx = x + dx;
+          if (rr < 0 || rr >= N || xx < 0 || xx >= N) continue;
+          int ccl = cl + dx, q = k;
+          if (ccl < 0) { ccl += W; q = k - 1; }
+          else if (ccl >= W) { ccl -= W; q = k + 1; }
+          float rj, r0j;
+          if (q == k) {
+            rj = rS[ccl * CS + rr];
+            r0j = r0S[ccl * CS + rr];
+          } else {
+            rj = cluster.map_shared_rank(rS, q)[ccl * CS + rr];
+            r0j = cluster.map_shared_rank(r0S, q)[ccl * CS + rr];
+          }
+          const float beta = (nb < 4 ? kBnn : kBdiag) * prior_weight(r0i - r0j, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p);
+          Wsum += beta;
+          Csum = fmaf(beta, rj, Csum);
+        }
+        const float root = icd_root(Wsum, Csum, sS[cl * CS + rho]);
+        rS[cl * CS + rho] = fmaxf(root, P.r_floor);
+      }
+      cluster.sync();  // B4..B7
+    }
+  }
+  // ---- write the reflectance slab back (row-major N x N) ---------------------------------
+  for (int i = tid; i < N * W; i += kThreads) {
+    const int rho = i / W, cl = i - rho * W;
+    A.r[static_cast<size_t>(rho) * N + W * k + cl] = rS[cl * CS + rho];
+  }
+}
+
+// Strehl ratio (Sec. 5.B): max |F^H(a e^{j(phi_true - phi_est)})|^2 / max |F^H a|^2.
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) k_strehl(const __grid_constant__ StrehlArgs a) {
+  using L = StepLayout<N>;
+  constexpr int C = L::C, W = L::W, CS = L::CS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int k = static_cast<int>(cluster.block_rank());
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* tw = reinterpret_cast<float2*>(smem + L::tw);
+  float2* rowbuf = reinterpret_cast<float2*>(smem + L::rowbuf);
+  float2* colbuf = reinterpret_cast<float2*>(smem + L::colbuf);
+  float* red = reinterpret_cast<float*>(smem + L::red);
+  float* pub = reinterpret_cast<float*>(smem + L::pub);
+  for (int i = tid; i < N; i += kThreads) tw[i] = a.tw[i];
+  for (int i = tid; i < W * CS; i += kThreads) colbuf[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  cluster.sync();
+  {
+    const int l = warp, rho = k + C * l;
+    const int dy2 = ap_dist2(rho, N);
+    if (dy2 <= a.ap_lim) {
+      float2* rb = rowbuf + l * N;
+      for (int x = lane; x < N; x += 32) {
+        float2 v = make_float2(0.f, 0.f);
+        if (ap_dist2(x, N) + dy2 <= a.ap_lim) {
+          const size_t gi = static_cast<size_t>(rho) * N + x;
+          float sn, cs;
+          sincosf(a.phi_true[gi] - a.phi_est[gi], &sn, &cs);
+          v = make_float2(cs, sn);
+        }
+        rb[x] = v;
+      }
+      __syncwarp();
+      fft_row<N, +1>(rb, tw, lane);
+      for (int x = lane; x < N; x += 32) cluster.map_shared_rank(colbuf, x / W)[(x % W) * CS + rho] = rb[x];
+    }
+  }
+  cluster.sync();
+  float m = 0.f;
+  {
+    float2* cb = colbuf + warp * CS;
+    fft_row<N, +1>(cb, tw, lane);
+    for (int rho = lane; rho < N; rho += 32) m = fmaxf(m, c_abs2(cb[rho]));
+    m = warp_max(m);
+  }
+  if (lane == 0) red[warp] = m;
+  __syncthreads();
+  if (tid == 0) {
+    float mm = red[0];
+    for (int w = 1; w < 16; ++w) mm = fmaxf(mm, red[w]);
+    pub[0] = mm;
+  }
+  cluster.sync();
+  if (k == 0 && tid == 0) {
+    float mm = 0.f;
+    for (int q = 0; q < C; ++q) mm = fmaxf(mm, cluster.map_shared_rank(pub, q)[0]);
+    // unscaled transforms: |F^H u|^2 = |v|^2 / N^2 and max |F^H a|^2 = (sum a)^2 / N^2
+    a.out[0] = mm * a.inv_ap_count2;
+  }
+  cluster.sync();
+}
+
+// Unitary 2-D DFT (or inverse) of one N x N image; in and out may alias.
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) k_fft2(const __grid_constant__ Fft2Args a) {
+  using L = StepLayout<N>;
+  constexpr int C = L::C, R = L::R, W = L::W, CS = L::CS;
+  extern __shared__ __align__(128) unsigned char smem[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int k = static_cast<int>(cluster.block_rank());
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* tw = reinterpret_cast<float2*>(smem + L::tw);
+  float2* rowbuf = reinterpret_cast<float2*>(smem + L::rowbuf);
+  float2* colbuf = reinterpret_cast<float2*>(smem + L::colbuf);
+  for (int i = tid; i < N; i += kThreads) tw[i] = a.tw[i];
+  for (int i = tid; i < R * N; i += kThreads) {
+    const int l = i / N, x = i - l * N;
+    rowbuf[i] = a.in[static_cast<size_t>(k + C * l) * N + x];
+  }
+  __syncthreads();
+  cluster.sync();  // every read of `in` precedes every write of `out`
+  {
+    const int l = warp, rho = k + C * l;
+    float2* rb = rowbuf + l * N;
+    if (a.inverse) fft_row<N, +1>(rb, tw, lane);
+    else fft_row<N, -1>(rb, tw, lane);
+    for (int x = lane; x < N; x += 32) cluster.map_shared_rank(colbuf, x / W)[(x % W) * CS + rho] = rb[x];
+  }
+  cluster.sync();
+  {
+    float2* cb = colbuf + warp * CS;
+    if (a.inverse) fft_row<N, +1>(cb, tw, lane);
+    else fft_row<N, -1>(cb, tw, lane);
+  }
+  __syncthreads();
+  const float invN = 1.f / static_cast<float>(N);
+  for (int i = tid; i < N * W; i += kThreads) {
+    const int rho = i / W, cl = i - rho * W;
+    a.out[static_cast<size_t>(rho) * N + W * k + cl] = c_scale(colbuf[cl * CS + rho], invN);
+  }
+  cluster.sync();
+}
+
+// ------------------------------------------------------------------------------ launchers
+template <typename Kern, typename Arg>
+static cudaError_t launch_cluster(Kern kern, int c, int clusters, size_t smem, cudaStream_t st, const Arg& arg) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(c * clusters), 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = static_cast<unsigned>(c);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
+template <int N>
+static cudaError_t configure_n(int* max_active) {
+  using L = StepLayout<N>;
+  const void* kerns[3] = {reinterpret_cast<const void*>(k_ddh_step<N>), reinterpret_cast<const void*>(k_strehl<N>),
+                          reinterpret_cast<const void*>(k_fft2<N>)};
+  for (const void* f : kerns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::total));
+    if (e != cudaSuccess) return e;
+    if (L::C > 8) {
+      e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (max_active != nullptr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(L::C, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = L::total;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = L::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(max_active, reinterpret_cast<const void*>(k_ddh_step<N>), &cfg);
+  }
+  return cudaSuccess;
+}
+
+cudaError_t configure(int n, int* max_active) {
+  switch (n) {
+    case 64: return configure_n<64>(max_active);
+    case 128: return configure_n<128>(max_active);
+    case 256: return configure_n<256>(max_active);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t step_smem_bytes(int n) {
+  switch (n) {
+    case 64: return StepLayout<64>::total;
+    case 128: return StepLayout<128>::total;
+    case 256: return StepLayout<256>::total;
+    default: return 0;
+  }
+}
+
+cudaError_t launch_step(int n, const StepBatch& b, cudaStream_t st) {
+  switch (n) {
+    case 64: return launch_cluster(k_ddh_step<64>, StepLayout<64>::C, b.count, StepLayout<64>::total, st, b);
+    case 128: return launch_cluster(k_ddh_step<128>, StepLayout<128>::C, b.count, StepLayout<128>::total, st, b);
+    case 256: return launch_cluster(k_ddh_step<256>, StepLayout<256>::C, b.count, StepLayout<256>::total, st, b);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_strehl(int n, const StrehlArgs& a, cudaStream_t st) {
+  switch (n) {
+    case 64: return launch_cluster(k_strehl<64>, StepLayout<64>::C, 1, StepLayout<64>::total, st, a);
+    case 128: return launch_cluster(k_strehl<128>, StepLayout<128>::C, 1, StepLayout<128>::total, st, a);
+    case 256: return launch_cluster(k_strehl<256>, StepLayout<256>::C, 1, StepLayout<256>::total, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fft2(int n, const Fft2Args& a, cudaStream_t st) {
+  switch (n) {
+    case 64: return launch_cluster(k_fft2<64>, StepLayout<64>::C, 1, StepLayout<64>::total, st, a);
+    case 128: return launch_cluster(k_fft2<128>, StepLayout<128>::C, 1, StepLayout<128>::total, st, a);
+    case 256: return launch_cluster(k_fft2<256>, StepLayout<256>::C, 1, StepLayout<256>::total, st, a);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ddh

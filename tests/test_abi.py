@@ -1,0 +1,73 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every declared entry
+point, and its pure-host helpers agree with the oracle's definitions (no GPU needed)."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from oracle import ddh_oracle as o
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ddh.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2305_03284_gb300 import build
+    build.build()
+    from paper_2305_03284_gb300 import _lib
+    return _lib.lib()
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ddh_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header(lib):
+    from paper_2305_03284_gb300 import _lib
+    assert set(_declared()) == set(_lib._SIGS)
+
+
+@pytest.mark.parametrize("n,d,snr", [(64, 32.0, 10.0), (256, 128.0, 5.0), (128, 31.3, 7.0)])
+def test_default_params_match_oracle(lib, n, d, snr):
+    from paper_2305_03284_gb300._lib import DdhParams
+    p = DdhParams()
+    assert lib.ddh_default_params(ctypes.byref(p), n, d, snr) == 0
+    ref = o.default_params(n, d, snr)
+    assert p.n == n and p.n_k == 1 and p.tilt_mode == 1
+    assert math.isclose(p.lam, ref.lam, rel_tol=1e-7) and math.isclose(p.alpha, ref.alpha, rel_tol=1e-7)
+    # the C aperture count (integer test) equals the oracle's disc
+    assert math.isclose(p.noise_var, ref.noise_var, rel_tol=1e-6)
+    assert math.isclose(p.prior_sigma, ref.prior_sigma, rel_tol=1e-7)
+    assert p.prior_q == 2.0 and math.isclose(p.prior_p, 1.1, rel_tol=1e-7)
+
+
+def test_default_params_rejects_bad_grid(lib):
+    from paper_2305_03284_gb300._lib import DdhParams, DDH_EINVAL
+    p = DdhParams()
+    assert lib.ddh_default_params(ctypes.byref(p), 100, 50.0, 10.0) == DDH_EINVAL
+    assert lib.ddh_default_params(ctypes.byref(p), 64, -1.0, 10.0) == DDH_EINVAL
+    assert lib.ddh_default_params(None, 64, 32.0, 10.0) == DDH_EINVAL
+
+
+def test_host_helpers(lib):
+    assert lib.ddh_version() >= 100
+    assert lib.ddh_strerror(-5).decode().startswith("frame has a non-finite")
+    assert lib.ddh_trace_floats(64) == 64 * 64 * 8 + 8
+    assert lib.ddh_checkpoint_bytes(64) > 2 * 64 * 64 * 4
+    assert lib.ddh_checkpoint_bytes(100) == 0
+    # calls on a NULL state are argument errors, not crashes
+    assert lib.ddh_step(None, None) == -1
+    assert lib.ddh_sync(None) == -1
+    assert lib.ddh_step_batch(None, None, 0) == -1

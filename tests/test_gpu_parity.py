@@ -1,0 +1,323 @@
+"""GPU parity: libddh's CUDA path against the FP64 oracle on seeded synthetic streams.
+
+Tolerance: relative L2 error 2e-5 on phi (wrapped difference over the aperture), r and the
+per-frame Strehl ratio, the figure the design targets for complex64/FP32 arithmetic against
+an FP64 reference.  Every call goes through the C ABI (the ctypes binding).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import ddh_oracle as o
+from synth import ddh_synth as sy
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def ddh():
+    from paper_2305_03284_gb300 import build
+    build.build()
+    from paper_2305_03284_gb300 import ddh as mod
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return mod
+
+
+def oracle_params(p) -> o.Params:
+    """The oracle runs on exactly the (float32) parameter values the library received."""
+    return o.Params(n=p.n, aperture_diam=float(p.aperture_diam), lam=float(p.lam), alpha=float(p.alpha),
+                    n_k=p.n_k, noise_var=float(p.noise_var), prior_p=float(p.prior_p),
+                    prior_q=float(p.prior_q), prior_T=float(p.prior_T), prior_sigma=float(p.prior_sigma),
+                    r_floor=float(p.r_floor), tilt_mode=p.tilt_mode)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def rel_l2_phase(a, b, ap):
+    d = o.wrap(np.asarray(a, np.float64) - b)[ap]
+    return float(np.linalg.norm(d) / np.linalg.norm(b[ap]))
+
+
+def cu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def np32(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def make(ddh, cfg, frames, **over):
+    st = sy.Stream(sy.with_frames(cfg, frames))
+    ys, ph = st.frames(frames)
+    p = ddh.default_params(cfg.n, cfg.aperture_diam, cfg.snr, **over)
+    return st, ys, ph, p
+
+
+# ------------------------------------------------------------------------------ FFT
+@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_fft2_matches_oracle(ddh, n, inverse):
+    rng = np.random.default_rng(n + inverse)
+    x = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))).astype(np.complex64)
+    got = np32(ddh.fft2(cu(x), inverse=inverse))
+    ref = (o.ifft2u if inverse else o.fft2u)(x.astype(np.complex128))
+    assert rel_l2(got, ref) < 2e-6
+
+
+def test_fft2_in_place(ddh):
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal((64, 64)) + 1j * rng.standard_normal((64, 64))).astype(np.complex64)
+    t = cu(x)
+    ddh.fft2(t, out=t)
+    assert rel_l2(np32(t), o.fft2u(x.astype(np.complex128))) < 2e-6
+
+
+# ----------------------------------------------------------------- one frame, stage by stage
+def test_first_frame_intermediates_64(ddh):
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 2)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    s = ddh.Stream(p)
+    s.step(cu(ys[0]))
+    tr = s.step_trace(cu(ys[1]))  # second frame: nonzero phase, tilt and r history
+    st0, _ = o.step(o.init_state(cfg.n), ys[0], prm)
+    _, ot = o.step(st0, ys[1], prm)
+    stats = np32(tr["stats"])
+    assert abs(stats[0] + 1j * stats[1] - ot.stats["mean"]) < 1e-5 / ot.stats["scale"]
+    assert math.isclose(stats[2], ot.stats["scale"], rel_tol=1e-5)
+    assert abs(stats[3] - ot.stats["tx"]) < 1e-6 and abs(stats[4] - ot.stats["ty"]) < 1e-6
+    assert rel_l2(np32(tr["b"]), ot.b) < TOL
+    assert rel_l2(np32(tr["r_init"]), ot.r_init) < TOL
+    assert rel_l2(np32(tr["mu"]), ot.mu) < TOL
+    assert rel_l2(np32(tr["s"]), ot.s) < TOL
+    assert rel_l2(np32(tr["z"])[a], ot.z[a]) < TOL
+
+
+# ------------------------------------------------------------------- multi-frame parity
+def _run_free(ddh, p, ys, ph, with_strehl=True):
+    s = ddh.Stream(p)
+    phis, rs, S = [], [], []
+    for i in range(len(ys)):
+        s.step(cu(ys[i]))
+        phis.append(np32(s.phase()))
+        rs.append(np32(s.reflectance()))
+        if with_strehl:
+            S.append(s.strehl(cu(ph[i].astype(np.float32))))
+    s.sync()
+    return np.array(phis), np.array(rs), np.array(S)
+
+
+def _run_oracle(prm, ys, ph):
+    a = o.aperture(prm.n, prm.aperture_diam)
+    st = o.init_state(prm.n)
+    phis, rs, S = [], [], []
+    for i in range(len(ys)):
+        st, _ = o.step(st, ys[i], prm)
+        phis.append(st.phi)
+        rs.append(st.r)
+        S.append(o.strehl(st.phi, ph[i], a))
+    return np.array(phis), np.array(rs), np.array(S)
+
+
+def test_free_running_parity_64_100_frames(ddh):
+    """North-star parity: 64x64 stream (32 px pupil, D/r0 10, 0.5 px/frame, SNR 10),
+    100 frames of one EM iteration each."""
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 100)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    gphi, gr, gS = _run_free(ddh, p, ys, ph)
+    ophi, orr, oS = _run_oracle(prm, ys, ph)
+    assert rel_l2_phase(gphi[-1], ophi[-1], a) < TOL
+    assert rel_l2(gr[-1], orr[-1]) < TOL
+    assert rel_l2(gS, oS) < TOL
+    assert np.all(gphi[:, ~a] == 0.0)
+
+
+def test_teacher_forced_parity_64(ddh):
+    """Each frame starts the GPU from the oracle's previous state: one-step error alone."""
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 30)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    s = ddh.Stream(p)
+    ost = o.init_state(cfg.n)
+    for i in range(30):
+        s.set_state(cu(ost.r.astype(np.float32)), cu(ost.phi.astype(np.float32)), i)
+        s.step(cu(ys[i]))
+        start = o.State(r=ost.r.astype(np.float32).astype(np.float64),
+                        phi=ost.phi.astype(np.float32).astype(np.float64), n=i)
+        nxt, _ = o.step(start, ys[i], prm)
+        assert rel_l2_phase(np32(s.phase()), nxt.phi, a) < TOL
+        assert rel_l2(np32(s.reflectance()), nxt.r) < TOL
+        ost, _ = o.step(ost, ys[i], prm)
+
+
+@pytest.mark.parametrize("which", ["128", "256"])
+def test_parity_larger_grids(ddh, which):
+    if which == "256":
+        cfg = sy.config_single_256(frames=6)
+    else:
+        cfg = sy.config_batched(frames=6)[0]  # a 128^2 stream of the batched workload
+    st, ys, ph, p = make(ddh, cfg, 6)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    gphi, gr, gS = _run_free(ddh, p, ys, ph)
+    ophi, orr, oS = _run_oracle(prm, ys, ph)
+    assert rel_l2_phase(gphi[-1], ophi[-1], a) < TOL
+    assert rel_l2(gr[-1], orr[-1]) < TOL
+    assert rel_l2(gS, oS) < TOL
+
+
+def test_parity_256_sampled_long_run(ddh):
+    """The benchmark's launch configuration (single 256^2 stream, one launch per frame) over
+    300 frames; at sampled frames the oracle takes one step from the GPU's own state."""
+    cfg = sy.config_single_256(frames=300)
+    st = sy.Stream(cfg)
+    p = ddh.default_params(cfg.n, cfg.aperture_diam, cfg.snr)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    s = ddh.Stream(p)
+    checks = {60, 180, 299}
+    for i in range(300):
+        y, _ = st.frame(i)
+        if i in checks:
+            r0 = np32(s.reflectance()).astype(np.float64)
+            p0 = np32(s.phase()).astype(np.float64)
+        s.step(cu(y))
+        if i in checks:
+            nxt, _ = o.step(o.State(r=r0, phi=p0, n=i), y, prm)
+            assert rel_l2_phase(np32(s.phase()), nxt.phi, a) < TOL
+            assert rel_l2(np32(s.reflectance()), nxt.r) < TOL
+    s.sync()
+
+
+@pytest.mark.parametrize("over", [{"n_k": 2}, {"n_k": 3}, {"tilt_mode": 0}, {"aperture_diam": 31.3},
+                                  {"prior_sigma": 0.05, "prior_p": 1.5}])
+def test_parity_variants_64(ddh, over):
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 12, **over)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, float(p.aperture_diam))
+    gphi, gr, _ = _run_free(ddh, p, ys, ph, with_strehl=False)
+    ophi, orr, _ = _run_oracle(prm, ys, ph)
+    assert rel_l2_phase(gphi[-1], ophi[-1], a) < TOL
+    assert rel_l2(gr[-1], orr[-1]) < TOL
+
+
+def test_empty_aperture(ddh):
+    """A pupil that contains no pixel: phase stays zero, r follows the prior-only EM."""
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 3, aperture_diam=0.5)
+    prm = oracle_params(p)
+    gphi, gr, _ = _run_free(ddh, p, ys, ph, with_strehl=False)
+    ophi, orr, _ = _run_oracle(prm, ys, ph)
+    assert np.all(gphi == 0.0)
+    assert rel_l2(gr[-1], orr[-1]) < TOL
+
+
+def test_strehl_matches_oracle(ddh):
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 1)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    s = ddh.Stream(p)
+    rng = np.random.default_rng(3)
+    est = np.where(a, ph[0] + 0.3 * rng.standard_normal(ph[0].shape), 0.0).astype(np.float32)
+    s.set_state(cu(np.zeros((64, 64), np.float32)), cu(est), 0)
+    got = s.strehl(cu(ph[0].astype(np.float32)))
+    ref = o.strehl(est.astype(np.float64), ph[0].astype(np.float32).astype(np.float64), a)
+    assert abs(got - ref) < 1e-5 * ref
+    s.set_state(cu(np.zeros((64, 64), np.float32)), cu(ph[0].astype(np.float32) * a), 0)
+    assert abs(s.strehl(cu(ph[0].astype(np.float32))) - 1.0) < 1e-5
+
+
+# -------------------------------------------------------------------------- API behaviour
+def test_batch_equals_individual_steps(ddh):
+    cfgs = [sy.config_single_64(), sy.config_batched(4)[0], sy.config_single_256(4), sy.config_batched(4)[1]]
+    data = [make(ddh, c, 4) for c in cfgs]
+    solo = [ddh.Stream(d[3]) for d in data]
+    batch = [ddh.Stream(d[3]) for d in data]
+    for f in range(4):
+        ys = [cu(d[1][f]) for d in data]
+        for s, y in zip(solo, ys):
+            s.step(y)
+        ddh.step_batch(batch, ys)
+    for s1, s2 in zip(solo, batch):
+        assert torch.equal(s1.phase(), s2.phase())
+        assert torch.equal(s1.reflectance(), s2.reflectance())
+    with pytest.raises(ddh.DdhError):
+        ddh.step_batch([batch[0], batch[0]], [cu(data[0][1][0])] * 2)
+    ddh.step_batch([], [])
+
+
+def test_step_host_equals_device(ddh):
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 3)
+    a, b = ddh.Stream(p), ddh.Stream(p)
+    out = torch.empty((64, 64), dtype=torch.float32).pin_memory()
+    for i in range(3):
+        a.step(cu(ys[i]))
+        b.step_host(torch.from_numpy(ys[i]).pin_memory(), out)
+    assert torch.equal(a.phase().cpu(), out)
+    assert b.frame_index == 3
+
+
+def test_checkpoint_roundtrip(ddh):
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 6)
+    s = ddh.Stream(p)
+    for i in range(3):
+        s.step(cu(ys[i]))
+    blob = s.save()
+    for i in range(3, 6):
+        s.step(cu(ys[i]))
+    ref = s.phase().clone()
+    t = ddh.Stream(p)
+    t.load(blob)
+    assert t.frame_index == 3
+    for i in range(3, 6):
+        t.step(cu(ys[i]))
+    assert torch.equal(t.phase(), ref)
+
+
+def test_nonfinite_frame_is_rejected_and_state_kept(ddh):
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 3)
+    s = ddh.Stream(p)
+    s.step(cu(ys[0]))
+    s.sync()
+    phi0, r0 = s.phase().clone(), s.reflectance().clone()
+    bad = ys[1].copy()
+    bad[10, 20] = np.nan
+    s.step(cu(bad))
+    with pytest.raises(ddh.DdhError) as e:
+        s.sync()
+    assert e.value.code == -5
+    assert torch.equal(s.phase(), phi0) and torch.equal(s.reflectance(), r0)
+    const = np.full((64, 64), 1 + 1j, np.complex64)  # zero variance: Normalize undefined
+    s.step(cu(const))
+    with pytest.raises(ddh.DdhError):
+        s.sync()
+    s.step(cu(ys[1]))
+    s.sync()
+    assert not torch.equal(s.phase(), phi0)
+
+
+def test_argument_errors(ddh):
+    p = ddh.default_params(64, 32.0, 10.0)
+    s = ddh.Stream(p)
+    buf = torch.zeros(64 * 64 + 1, dtype=torch.complex64, device="cuda")
+    rc = ddh.lib().ddh_step(s._h, ddh.c_void_p(buf.data_ptr() + 8))
+    assert rc == -1  # misaligned frame
+    for bad in ({"prior_q": 1.5}, {"n_k": 0}, {"noise_var": 0.0}, {"aperture_diam": 65.0}, {"n": 100}):
+        q = ddh.default_params(64, 32.0, 10.0, **bad)
+        with pytest.raises(ddh.DdhError):
+            ddh.Stream(q)
