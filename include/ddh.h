@@ -49,13 +49,16 @@ typedef struct ddh_params {
   float prior_sigma;    /* q-GGMRF scale sigma_r > 0 */
   float r_floor;        /* lower bound on the reflectance (> 0) */
   int tilt_mode;        /* 1: RemoveTipTilt each frame; 0: skip it */
+  int phase_block;      /* 1: per-pixel phase; 2 or 4: phase constant on aligned G x G tiles,
+                           phi_B = angle(sum over the tile of a y~ conj(F mu)) */
 } ddh_params;
 
 typedef struct ddh_state ddh_state; /* opaque; owned by the library */
 
 /* Fill `p` with the defaults for grid `n`, pupil `aperture_diam` and a linear SNR over the
  * pupil: lambda 0.45, alpha 0.025 (Sec. 5.B), n_k 1, noise_var 1/(1 + f SNR) with f the
- * pupil fill fraction, prior p 1.1, q 2, T 1, sigma_r 0.1, r_floor 1e-10, tilt_mode 1. */
+ * pupil fill fraction, prior p 1.1, q 2, T 1, sigma_r 0.1, r_floor 1e-10, tilt_mode 1,
+ * phase_block 1. */
 int ddh_default_params(ddh_params *p, int n, float aperture_diam, float snr);
 
 /* Validate `p`, allocate the device state (r = 0, phi = 0, n = 0: Fig. 1 first line) and bind

@@ -17,7 +17,8 @@ reading of its forward model (Eq. 1, Sec. 2) and MAP objective (Eq. 2):
   8-neighbour prior, majorised by the symmetric-bound quadratic surrogate formed once at the
   sweep's entry values; each pixel minimises a 1-D function whose stationarity condition is the
   cubic ``W r^3 - C r^2 + r - s = 0``;
-* phase M-step: ``phi_i = angle(y_i conj(z_i))`` on the aperture, ``z = F mu``;
+* phase M-step: ``phi_i = angle(y_i conj(z_i))`` on the aperture, ``z = F mu`` (or, with the
+  phase held constant on G x G tiles, the angle of the tile sum of ``y conj(z)``);
 * loop (Fig. 1): Normalize (Eq. 4), RemoveTipTilt, r-init (Eq. 3), ``N_k`` EM iterations.
 
 Arithmetic is float64 throughout; the input frame is the complex64 frame promoted to complex128.
@@ -57,6 +58,7 @@ class Params:
     prior_sigma: float = 0.1
     r_floor: float = 1e-10
     tilt_mode: int = 1           # 1: RemoveTipTilt each frame, 0: skip
+    phase_block: int = 1         # 1: per-pixel phase; G > 1: phase constant on G x G blocks
 
 
 @dataclass
@@ -310,12 +312,19 @@ def icd_sweep(r_entry: np.ndarray, s: np.ndarray, prm: Params) -> np.ndarray:
 # ---------------------------------------------------------------------------------------
 # phase M-step
 # ---------------------------------------------------------------------------------------
-def phase_mstep(y_norm: np.ndarray, mu: np.ndarray, phi_old: np.ndarray, a: np.ndarray):
-    """Minimise ``sum_i a_i |y_i - exp(j phi_i) z_i|^2`` with ``z = F mu``:
-    ``phi_i = angle(y_i conj(z_i))`` on the aperture (old value kept where that product is 0);
-    zero off the aperture.  Returns (phi, z)."""
+def phase_mstep(y_norm: np.ndarray, mu: np.ndarray, phi_old: np.ndarray, a: np.ndarray, block: int = 1):
+    """Minimise ``sum_i a_i |y_i - exp(j phi_i) z_i|^2`` with ``z = F mu``.
+
+    Per-pixel phase (``block == 1``): ``phi_i = angle(y_i conj(z_i))`` on the aperture.
+    Phase constant on aligned ``block x block`` tiles: ``phi_B = angle(sum_{i in B} a_i y_i
+    conj(z_i))``, the exact minimiser over one tile.  Where the (summed) product is 0 the old
+    value is kept; the phase is zero off the aperture.  Returns (phi, z)."""
     z = fft2u(mu)
-    v = y_norm * np.conj(z)
+    v = np.where(a, y_norm * np.conj(z), 0.0)
+    if block > 1:
+        n = v.shape[0]
+        vb = v.reshape(n // block, block, n // block, block).sum(axis=(1, 3))
+        v = np.kron(vb, np.ones((block, block)))
     phi = np.where(v != 0, np.angle(v), phi_old)
     return np.where(a, phi, 0.0), z
 
@@ -345,7 +354,7 @@ def step(state: State, y: np.ndarray, prm: Params) -> tuple[State, Trace]:
             b = adjoint_op(yt, phi, a)
         mu, s, _ = estep(r, b, prm)
         r_new = icd_sweep(r, s, prm)
-        phi, z = phase_mstep(yt, mu, phi, a)
+        phi, z = phase_mstep(yt, mu, phi, a, prm.phase_block)
         r = r_new
         if it == 0:
             tr.mu, tr.s, tr.z = mu, s, z
@@ -388,7 +397,7 @@ def em_static_step(r, phi, y_norm, prm: Params, a=None):
     b = adjoint_op(y_norm, phi, a)
     mu, s, _ = estep(r, b, prm)
     r_new = np.maximum(icd_sweep(r, s, prm), prm.r_floor)
-    phi_new, _ = phase_mstep(y_norm, mu, phi, a)
+    phi_new, _ = phase_mstep(y_norm, mu, phi, a, prm.phase_block)
     return r_new, phi_new
 
 

@@ -31,6 +31,7 @@ class DdhParams(ctypes.Structure):
         ("prior_sigma", c_float),
         ("r_floor", c_float),
         ("tilt_mode", c_int),
+        ("phase_block", c_int),
     ]
 
 

@@ -106,6 +106,7 @@ int validate(const ddh_params* p) {
     return DDH_EINVAL;
   if (!(p->r_floor > 0.f && std::isfinite(p->r_floor))) return DDH_EINVAL;
   if (p->tilt_mode != 0 && p->tilt_mode != 1) return DDH_EINVAL;
+  if (p->phase_block != 1 && p->phase_block != 2 && p->phase_block != 4) return DDH_EINVAL;
   return DDH_OK;
 }
 
@@ -114,6 +115,7 @@ ddh::KParams derive(const ddh_params& p) {
   k.ap_lim = static_cast<int>(aperture_limit(p.aperture_diam));
   k.tilt_mode = p.tilt_mode;
   k.n_k = p.n_k;
+  k.g_shift = p.phase_block == 4 ? 2 : p.phase_block == 2 ? 1 : 0;
   k.lam1 = static_cast<float>(1.0 - static_cast<double>(p.lambda));
   k.lam_alpha = static_cast<float>(static_cast<double>(p.lambda) * p.alpha);
   k.noise_var = p.noise_var;
@@ -219,6 +221,7 @@ int ddh_default_params(ddh_params* p, int n, float aperture_diam, float snr) {
   p->prior_sigma = 0.1f;
   p->r_floor = 1e-10f;
   p->tilt_mode = 1;
+  p->phase_block = 1;
   return DDH_OK;
 }
 

@@ -19,6 +19,7 @@ struct KParams {
   int ap_lim;        // floor(d^2): pixel in pupil iff (2x-(N-1))^2 + (2y-(N-1))^2 <= ap_lim
   int tilt_mode;     // RemoveTipTilt on/off
   int n_k;           // EM iterations per frame
+  int g_shift;       // log2 of the phase tile G; rows are dealt to CTAs in groups of G
   float lam1;        // 1 - lambda
   float lam_alpha;   // lambda * alpha
   float noise_var;   // sigma^2

@@ -42,6 +42,20 @@ struct StepLayout {
   static constexpr size_t total = al(mbar + 16);
 };
 
+// Rows are dealt to the cluster's CTAs cyclically in groups of G = 2^gs consecutive rows, so
+// that a G x G phase tile stays inside one CTA: local row l of CTA k is global row
+// G (k + C floor(l/G)) + (l mod G).
+template <int C>
+__device__ __forceinline__ int row_of(int k, int l, int gs) {
+  return (((l >> gs) * C + k) << gs) + (l & ((1 << gs) - 1));
+}
+template <int C>
+__device__ __forceinline__ int row_owner(int rho, int gs) { return (rho >> gs) % C; }
+template <int C>
+__device__ __forceinline__ int row_local(int rho, int gs) {
+  return (((rho >> gs) / C) << gs) + (rho & ((1 << gs) - 1));
+}
+
 // Chan et al. pairwise update of (count, complex mean, M2 = sum |y - mean|^2).
 __device__ __forceinline__ void chan_combine(float& n_a, float2& m_a, float& q_a, float n_b, float2 m_b,
                                              float q_b) {
@@ -89,14 +103,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   if (tid == 0) {
     mbar_arrive_expect_tx(mbar, static_cast<uint32_t>(R * N * sizeof(float2)));
     for (int l = 0; l < R; ++l) {
-      const int rho = k + C * l;
+      const int rho = row_of<C>(k, l, P.g_shift);
       tma_load_1d(ybuf + l * N, A.y + static_cast<size_t>(rho) * N, N * sizeof(float2), mbar);
     }
   }
   for (int i = tid; i < N; i += kThreads) tw[i] = batch.tw[i];
   for (int i = tid; i < R * N; i += kThreads) {
     const int l = i / N, x = i - l * N;
-    phib[i] = A.phi[static_cast<size_t>(k + C * l) * N + x];
+    phib[i] = A.phi[static_cast<size_t>(row_of<C>(k, l, P.g_shift)) * N + x];
   }
   for (int i = tid; i < N * W; i += kThreads) {
     const int rho = i / W, cl = i - rho * W;
@@ -109,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
 
   // ---- phase 1: per-row statistics (Normalize, Eq. 4) and tip/tilt sums (Sec. 4) --------
   {
-    const int l = warp, rho = k + C * l;
+    const int l = warp, rho = row_of<C>(k, l, P.g_shift);
     const float2* yr = ybuf + l * N;
     float sre = 0.f, sim = 0.f;
     for (int x = lane; x < N; x += 32) { sre += yr[x].x; sim += yr[x].y; }
@@ -158,17 +172,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     pub[7] = bad;
   }
   cluster.sync();  // B1
-  if (tid == 0) {
+  if (warp == 0) {
+    // lane q fetches CTA q's partials (C <= 32 remote loads in parallel), then lane 0
+    // combines them in rank order, so every CTA derives bit-identical statistics
+    float o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = 0.f;
+    if (lane < C) {
+      const float* src = cluster.map_shared_rank(pub, lane);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) o[j] = src[j];
+    }
     const float nb = static_cast<float>(R * N);
     float n_a = nb, q_a = 0.f;
     float2 m_a = make_float2(0.f, 0.f);
     float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, bad = 0.f;
     for (int q = 0; q < C; ++q) {
-      const float* o = cluster.map_shared_rank(pub, q);
-      if (q == 0) { m_a = make_float2(o[0], o[1]); q_a = o[2]; }
-      else chan_combine(n_a, m_a, q_a, nb, make_float2(o[0], o[1]), o[2]);
-      t0 += o[3]; t1 += o[4]; t2 += o[5]; t3 += o[6]; bad += o[7];
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(0xffffffffu, o[j], q);
+      if (q == 0) { m_a = make_float2(v[0], v[1]); q_a = v[2]; }
+      else chan_combine(n_a, m_a, q_a, nb, make_float2(v[0], v[1]), v[2]);
+      t0 += v[3]; t1 += v[4]; t2 += v[5]; t3 += v[6]; bad += v[7];
     }
+    if (lane == 0) {
     const float scale = sqrtf(static_cast<float>(N) * static_cast<float>(N) / q_a);
     const bool finite = isfinite(m_a.x) && isfinite(m_a.y) && isfinite(q_a) && q_a > 0.f && isfinite(scale);
     glob[0] = m_a.x;
@@ -187,6 +214,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       float* st = A.trace + static_cast<size_t>(N) * N * 8;
       st[0] = m_a.x; st[1] = m_a.y; st[2] = scale; st[3] = glob[3]; st[4] = glob[4];
       st[5] = 0.f; st[6] = 0.f; st[7] = 0.f;
+    }
     }
   }
   __syncthreads();
@@ -210,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       }
     }
     {
-      const int l = warp, rho = k + C * l;
+      const int l = warp, rho = row_of<C>(k, l, P.g_shift);
       const int dy2 = ap_dist2(rho, N);
       float2* rb = rowbuf + l * N;
       float* pr = phib + l * N;
@@ -271,41 +299,57 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       fft_row<N, -1>(cb, tw, lane);
       for (int rho = lane; rho < N; rho += 32) {
         if (ap_dist2(rho, N) <= P.ap_lim) {
-          float2* dst = cluster.map_shared_rank(rowbuf, rho % C);
-          dst[(rho / C) * N + W * k + cl] = cb[rho];
+          float2* dst = cluster.map_shared_rank(rowbuf, row_owner<C>(rho, P.g_shift));
+          dst[row_local<C>(rho, P.g_shift) * N + W * k + cl] = cb[rho];
         }
       }
     }
     cluster.sync();  // B3
     // ---- phase 4: row FFT of mu (aperture rows) and phase M-step ------------------------
+    // v = a y~ conj(z) per pixel (summed over the G x G tile when G > 1); phi = angle(v).
     {
-      const int l = warp, rho = k + C * l;
+      const int gs = P.g_shift, G = 1 << gs;
+      const int l = warp, rho = row_of<C>(k, l, gs);
       const int dy2 = ap_dist2(rho, N);
+      const bool row_ap = dy2 <= P.ap_lim;
       float2* rb = rowbuf + l * N;
-      float* pr = phib + l * N;
       const float2* yr = ybuf + l * N;
-      float* phi_out = A.phi + static_cast<size_t>(rho) * N;
-      if (dy2 <= P.ap_lim) {
-        fft_row<N, -1>(rb, tw, lane);
-        for (int x = lane; x < N; x += 32) {
-          float out = 0.f;
-          if (ap_dist2(x, N) + dy2 <= P.ap_lim) {
-            const float2 z = c_scale(rb[x], invN);
-            const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
-            // v = y~ conj(z)
-            const float vr = fmaf(yt.x, z.x, yt.y * z.y);
-            const float vi = fmaf(yt.y, z.x, -yt.x * z.y);
-            out = (vr != 0.f || vi != 0.f) ? atan2f(vi, vr) : pr[x];
-            pr[x] = out;
-            if (trace != nullptr) {
-              const size_t M = static_cast<size_t>(N) * N;
-              reinterpret_cast<float2*>(trace)[2 * M + static_cast<size_t>(rho) * N + x] = z;
-            }
+      if (row_ap) fft_row<N, -1>(rb, tw, lane);
+      for (int x = lane; x < N; x += 32) {
+        float2 v = make_float2(0.f, 0.f);
+        if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
+          const float2 z = c_scale(rb[x], invN);
+          const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
+          v = make_float2(fmaf(yt.x, z.x, yt.y * z.y), fmaf(yt.y, z.x, -yt.x * z.y));
+          if (trace != nullptr) {
+            const size_t M = static_cast<size_t>(N) * N;
+            reinterpret_cast<float2*>(trace)[2 * M + static_cast<size_t>(rho) * N + x] = z;
           }
-          phi_out[x] = out;
         }
-      } else {
-        for (int x = lane; x < N; x += 32) phi_out[x] = 0.f;
+        for (int o = 1; o < G; o <<= 1) {  // sum over the G consecutive x of the tile
+          v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+          v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        }
+        rb[x] = v;
+      }
+    }
+    if (P.g_shift > 0) __syncthreads();  // tile rows are other warps of this CTA
+    {
+      const int gs = P.g_shift, G = 1 << gs;
+      const int l = warp, rho = row_of<C>(k, l, gs);
+      const int dy2 = ap_dist2(rho, N);
+      const int l0 = l & ~(G - 1);
+      float* pr = phib + l * N;
+      float* phi_out = A.phi + static_cast<size_t>(rho) * N;
+      for (int x = lane; x < N; x += 32) {
+        float out = 0.f;
+        if (dy2 <= P.ap_lim && ap_dist2(x, N) + dy2 <= P.ap_lim) {
+          float2 v = rowbuf[l0 * N + x];
+          for (int j = 1; j < G; ++j) v = c_add(v, rowbuf[(l0 + j) * N + x]);
+          out = (v.x != 0.f || v.y != 0.f) ? atan2f(v.y, v.x) : pr[x];
+          pr[x] = out;
+        }
+        phi_out[x] = out;
       }
     }
     // ---- phase 5: r M-step, 4-colour ICD sweep on the q-GGMRF surrogate ------------------

@@ -13,7 +13,7 @@ import torch
 from ._lib import DdhError, DdhParams, check, lib  # noqa: F401
 
 
-def default_params(n: int, aperture_diam: float, snr: float, **overrides) -> DdhParams:
+def default_params(n: int, aperture_diam: float, snr: float, /, **overrides) -> DdhParams:
     """``ddh_default_params`` plus keyword overrides (field names of :class:`DdhParams`)."""
     p = DdhParams()
     check(lib().ddh_default_params(byref(p), int(n), float(aperture_diam), float(snr)))

@@ -410,3 +410,92 @@ def test_phase_screen_structure_function():
     r2, r4 = np.mean(ratios[2]), np.mean(ratios[4])
     assert 0.6 < r2 < 1.1 and 0.6 < r4 < 1.1
     assert abs(r2 - r4) < 0.15  # the 5/3 exponent holds between the two separations
+
+
+# ---------------------------------------------------------------------------- tiled phase
+def test_tiled_phase_mstep_recovers_tile_constant_phase():
+    rng = _rng(14)
+    n, G = 16, 2
+    a = o.aperture(n, 12.0)
+    g = _crandn(rng, n, n)
+    tiles = rng.uniform(-math.pi, math.pi, (n // G, n // G))
+    phi = np.where(a, np.kron(tiles, np.ones((G, G))), 0.0)
+    y = o.forward_op(g, phi, a)
+    est, _ = o.phase_mstep(y, g, np.zeros((n, n)), a, block=G)
+    assert np.allclose(o.wrap(est - phi)[a], 0.0, atol=1e-12)
+
+
+def test_tiled_phase_mstep_minimises_tile_data_term():
+    rng = _rng(15)
+    n, G = 8, 4
+    a = o.aperture(n, 7.0)
+    y, mu = _crandn(rng, n, n), _crandn(rng, n, n)
+    est, z = o.phase_mstep(y, mu, np.zeros((n, n)), a, block=G)
+    for ty in range(n // G):
+        for tx in range(n // G):
+            sl = (slice(ty * G, ty * G + G), slice(tx * G, tx * G + G))
+            m = a[sl]
+            if not m.any():
+                continue
+            ph0 = est[sl][m][0]
+            assert np.allclose(est[sl][m], ph0)  # constant on the tile
+            cost = lambda t: float(np.sum(np.abs(y[sl][m] - np.exp(1j * t) * z[sl][m]) ** 2))
+            grid = np.linspace(-math.pi, math.pi, 20001)
+            assert cost(ph0) <= min(cost(t) for t in grid) + 1e-9
+
+
+def test_tiled_block_one_is_per_pixel():
+    rng = _rng(16)
+    a = o.aperture(16, 10.0)
+    y, mu = _crandn(rng, 16, 16), _crandn(rng, 16, 16)
+    e1, _ = o.phase_mstep(y, mu, np.zeros((16, 16)), a)
+    e2, _ = o.phase_mstep(y, mu, np.zeros((16, 16)), a, block=1)
+    assert np.array_equal(e1, e2)
+
+
+def test_static_em_monotone_with_tiled_phase():
+    rng = _rng(17)
+    n = 8
+    prm = o.Params(n=n, aperture_diam=1e6, noise_var=0.2, prior_sigma=0.1, phase_block=2)
+    a = o.aperture(n, prm.aperture_diam)
+    g = np.sqrt(rng.uniform(0, 1, (n, n))) * _crandn(rng, n, n)
+    y = np.exp(1j * rng.uniform(-1, 1, (n, n))) * o.fft2u(g) + math.sqrt(0.2) * _crandn(rng, n, n)
+    y, _ = o.normalize(y)
+    r = np.maximum(np.abs(o.adjoint_op(y, np.zeros((n, n)), a)) ** 2, 1e-3)
+    phi = np.zeros((n, n))
+    costs = [_dense_map_cost(r, phi, y, prm)]
+    for _ in range(30):
+        r, phi = o.em_static_step(r, phi, y, prm, a)
+        costs.append(_dense_map_cost(r, phi, y, prm))
+    assert np.all(np.diff(costs) <= 1e-9 * np.abs(costs[:-1]))
+
+
+# ---------------------------------------------------------------------------- sensitivity
+def _divergence(block, frames):
+    cfg = sy.config_single_64(frames)
+    ys, _ = sy.Stream(cfg).frames(frames)
+    prm = o.default_params(64, 32.0, cfg.snr, phase_block=block)
+    a = o.aperture(64, 32.0)
+    A, B = o.init_state(64), o.init_state(64)
+    rng = _rng(18)
+    out = []
+    for i in range(frames):
+        A, _ = o.step(A, ys[i], prm)
+        B, _ = o.step(B, ys[i], prm)
+        if i == 0:
+            B.r = B.r * (1 + 1e-7 * rng.standard_normal(B.r.shape))
+            B.phi = np.where(a, B.phi + 1e-7 * rng.standard_normal(B.phi.shape), 0.0)
+        out.append(np.linalg.norm(o.wrap(A.phi - B.phi)[a]) / np.linalg.norm(A.phi[a]))
+    return np.array(out)
+
+
+def test_per_pixel_phase_iteration_amplifies_perturbations():
+    """Property of the per-pixel reading on this workload: a 1e-7 change of the state grows by
+    orders of magnitude within 40 frames (bounds any free-running comparison horizon)."""
+    d = _divergence(1, 40)
+    assert d[-1] > 1e-3
+
+
+def test_tiled_phase_iteration_contracts():
+    d = _divergence(2, 40)
+    assert d.max() < 1e-5 and d[-1] < 1e-6
