@@ -29,13 +29,14 @@ struct StepLayout {
   static constexpr size_t al(size_t v) { return (v + 127) & ~size_t(127); }
   static constexpr size_t tw = 0;
   static constexpr size_t rowbuf = al(tw + N * 8);
-  static constexpr size_t colbuf = al(rowbuf + size_t(R) * N * 8);
+  static constexpr size_t colbuf = al(rowbuf + size_t(R) * CS * 8);
   static constexpr size_t ybuf = al(colbuf + size_t(W) * CS * 8);
   static constexpr size_t phib = al(ybuf + size_t(R) * N * 8);
   static constexpr size_t rS = al(phib + size_t(R) * N * 4);
   static constexpr size_t r0S = al(rS + size_t(W) * CS * 4);
   static constexpr size_t sS = al(r0S + size_t(W) * CS * 4);
-  static constexpr size_t red = al(sS + size_t(W) * CS * 4);  // 16 warps x 8 floats
+  static constexpr size_t halo = al(sS + size_t(W) * CS * 4);  // 3 x N halo-pair weights
+  static constexpr size_t red = al(halo + size_t(3) * N * 4);  // 16 warps x 8 floats
   static constexpr size_t pub = al(red + 16 * 8 * 4);         // 8 published floats
   static constexpr size_t glob = al(pub + 8 * 4);             // 8 combined floats
   static constexpr size_t mbar = al(glob + 8 * 4);
@@ -87,6 +88,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   float* rS = reinterpret_cast<float*>(smem + L::rS);
   float* r0S = reinterpret_cast<float*>(smem + L::r0S);
   float* sS = reinterpret_cast<float*>(smem + L::sS);
+  float* halo = reinterpret_cast<float*>(smem + L::halo);
   float* red = reinterpret_cast<float*>(smem + L::red);
   float* pub = reinterpret_cast<float*>(smem + L::pub);
   float* glob = reinterpret_cast<float*>(smem + L::glob);
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     {
       const int l = warp, rho = row_of<C>(k, l, P.g_shift);
       const int dy2 = ap_dist2(rho, N);
-      float2* rb = rowbuf + l * N;
+      float2* rb = rowbuf + l * CS;
       float* pr = phib + l * N;
       const float2* yr = ybuf + l * N;
       if (dy2 <= P.ap_lim) {
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       for (int rho = lane; rho < N; rho += 32) {
         if (ap_dist2(rho, N) <= P.ap_lim) {
           float2* dst = cluster.map_shared_rank(rowbuf, row_owner<C>(rho, P.g_shift));
-          dst[row_local<C>(rho, P.g_shift) * N + W * k + cl] = cb[rho];
+          dst[row_local<C>(rho, P.g_shift) * CS + W * k + cl] = cb[rho];
         }
       }
     }
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       const int l = warp, rho = row_of<C>(k, l, gs);
       const int dy2 = ap_dist2(rho, N);
       const bool row_ap = dy2 <= P.ap_lim;
-      float2* rb = rowbuf + l * N;
+      float2* rb = rowbuf + l * CS;
       const float2* yr = ybuf + l * N;
       if (row_ap) fft_row<N, -1>(rb, tw, lane);
       for (int x = lane; x < N; x += 32) {
@@ -344,48 +346,88 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       for (int x = lane; x < N; x += 32) {
         float out = 0.f;
         if (dy2 <= P.ap_lim && ap_dist2(x, N) + dy2 <= P.ap_lim) {
-          float2 v = rowbuf[l0 * N + x];
-          for (int j = 1; j < G; ++j) v = c_add(v, rowbuf[(l0 + j) * N + x]);
+          float2 v = rowbuf[l0 * CS + x];
+          for (int j = 1; j < G; ++j) v = c_add(v, rowbuf[(l0 + j) * CS + x]);
           out = (v.x != 0.f || v.y != 0.f) ? atan2f(v.y, v.x) : pr[x];
           pr[x] = out;
         }
         phi_out[x] = out;
       }
     }
+    __syncthreads();  // phase 4 reads of the row buffer end before it holds weights
     // ---- phase 5: r M-step, 4-colour ICD sweep on the q-GGMRF surrogate ------------------
-    for (int c = 0; c < 4; ++c) {
-      const int cx = c & 1, cy = c >> 1;  // colours (0,0), (1,0), (0,1), (1,1)
-      for (int idx = tid; idx < 4 * N; idx += kThreads) {
-        const int cl = cx + 2 * (idx & 7);
-        const int rho = cy + 2 * (idx >> 3);
+    // Surrogate weights beta_ij = b_ij rho'(D)/D at the entry values, once per pixel pair:
+    // E, S, SE, SW pairs of every slab pixel (in the free column/row buffers), and the three
+    // pairs that cross into the left/right slabs from this side (W, NW at cl = 0; NE at
+    // cl = W-1).  A pair shared by two CTAs gets the same value on both sides (|D| symmetric).
+    {
+      float* bE = reinterpret_cast<float*>(colbuf);
+      float* bS = bE + W * CS;
+      float* bSE = reinterpret_cast<float*>(rowbuf);
+      float* bSW = bSE + W * CS;
+      const float* r0L = k > 0 ? cluster.map_shared_rank(r0S, k - 1) : r0S;
+      const float* r0R = k < C - 1 ? cluster.map_shared_rank(r0S, k + 1) : r0S;
+      auto wgt = [&](float d) { return prior_weight_fast(d, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p); };
+      for (int i = tid; i < W * N; i += kThreads) {
+        const int cl = i / N, rho = i - cl * N;
         const int x = W * k + cl;
         const float r0i = r0S[cl * CS + rho];
-        float Wsum = 0.f, Csum = 0.f;
-#pragma unroll
-        for (int nb = 0; nb < 8; ++nb) {
-          const int dy = (nb < 2) ? (nb == 0 ? -1 : 1) : (nb < 4 ? 0 : (nb < 6 ? -1 : 1));
-          const int dx = (nb < 2) ? 0 : (nb < 4 ? (nb == 2 ? -1 : 1) : ((nb & 1) ? 1 : -1));
-          const int rr = rho + dy, xx = x + dx;
-          if (rr < 0 || rr >= N || xx < 0 || xx >= N) continue;
-          int ccl = cl + dx, q = k;
-          if (ccl < 0) { ccl += W; q = k - 1; }
-          else if (ccl >= W) { ccl -= W; q = k + 1; }
-          float rj, r0j;
-          if (q == k) {
-            rj = rS[ccl * CS + rr];
-            r0j = r0S[ccl * CS + rr];
-          } else {
-            rj = cluster.map_shared_rank(rS, q)[ccl * CS + rr];
-            r0j = cluster.map_shared_rank(r0S, q)[ccl * CS + rr];
-          }
-          const float beta = (nb < 4 ? kBnn : kBdiag) * prior_weight(r0i - r0j, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p);
-          Wsum += beta;
-          Csum = fmaf(beta, rj, Csum);
-        }
-        const float root = icd_root(Wsum, Csum, sS[cl * CS + rho]);
-        rS[cl * CS + rho] = fmaxf(root, P.r_floor);
+        const bool dn = rho + 1 < N;
+        // right / lower neighbours (the right column of the slab lives in CTA k+1)
+        const float rE = cl + 1 < W ? r0S[(cl + 1) * CS + rho] : (x + 1 < N ? r0R[rho] : 0.f);
+        bE[cl * CS + rho] = x + 1 < N ? kBnn * wgt(r0i - rE) : 0.f;
+        bS[cl * CS + rho] = dn ? kBnn * wgt(r0i - r0S[cl * CS + rho + 1]) : 0.f;
+        const float rSE = cl + 1 < W ? (dn ? r0S[(cl + 1) * CS + rho + 1] : 0.f) : (x + 1 < N && dn ? r0R[rho + 1] : 0.f);
+        bSE[cl * CS + rho] = (x + 1 < N && dn) ? kBdiag * wgt(r0i - rSE) : 0.f;
+        const float rSW = cl > 0 ? (dn ? r0S[(cl - 1) * CS + rho + 1] : 0.f) : (x > 0 && dn ? r0L[(W - 1) * CS + rho + 1] : 0.f);
+        bSW[cl * CS + rho] = (x > 0 && dn) ? kBdiag * wgt(r0i - rSW) : 0.f;
       }
-      cluster.sync();  // B4..B7
+      for (int rho = tid; rho < N; rho += kThreads) {
+        // hW: pair (rho, x0-1)-(rho, x0); hNW: (rho-1, x0-1)-(rho, x0); hNE: (rho-1, x1+1)-(rho, x1)
+        const float a0 = r0S[rho], a1 = r0S[(W - 1) * CS + rho];
+        halo[rho] = k > 0 ? kBnn * wgt(a0 - r0L[(W - 1) * CS + rho]) : 0.f;
+        halo[N + rho] = (k > 0 && rho > 0) ? kBdiag * wgt(a0 - r0L[(W - 1) * CS + rho - 1]) : 0.f;
+        halo[2 * N + rho] = (k < C - 1 && rho > 0) ? kBdiag * wgt(a1 - r0R[rho - 1]) : 0.f;
+      }
+      __syncthreads();
+      const float* rL = k > 0 ? cluster.map_shared_rank(rS, k - 1) : rS;
+      const float* rR = k < C - 1 ? cluster.map_shared_rank(rS, k + 1) : rS;
+      for (int c = 0; c < 4; ++c) {
+        const int cx = c & 1, cy = c >> 1;  // colours (0,0), (1,0), (0,1), (1,1)
+        for (int idx = tid; idx < 4 * N; idx += kThreads) {
+          const int j = idx % (N / 2), ci = idx / (N / 2);
+          const int cl = cx + 2 * ci, rho = cy + 2 * j;
+          const int o = cl * CS + rho;
+          const bool up = rho > 0, dn = rho + 1 < N;
+          // neighbour values: current r (earlier colours already updated)
+          const float rW = cl > 0 ? rS[o - CS] : rL[(W - 1) * CS + rho];
+          const float rE = cl + 1 < W ? rS[o + CS] : rR[rho];
+          const float rN = up ? rS[o - 1] : 0.f;
+          const float rSo = dn ? rS[o + 1] : 0.f;
+          const float rNW = !up ? 0.f : (cl > 0 ? rS[o - CS - 1] : rL[(W - 1) * CS + rho - 1]);
+          const float rNE = !up ? 0.f : (cl + 1 < W ? rS[o + CS - 1] : rR[rho - 1]);
+          const float rSW = !dn ? 0.f : (cl > 0 ? rS[o - CS + 1] : rL[(W - 1) * CS + rho + 1]);
+          const float rSE = !dn ? 0.f : (cl + 1 < W ? rS[o + CS + 1] : rR[rho + 1]);
+          // pair weights (zero where the neighbour is off the grid)
+          const float wE = bE[o], wS = bS[o], wSE = bSE[o], wSW = bSW[o];
+          const float wW = cl > 0 ? bE[o - CS] : halo[rho];
+          const float wN = up ? bS[o - 1] : 0.f;
+          const float wNW = !up ? 0.f : (cl > 0 ? bSE[o - CS - 1] : halo[N + rho]);
+          const float wNE = !up ? 0.f : (cl + 1 < W ? bSW[o + CS - 1] : halo[2 * N + rho]);
+          const float Wsum = ((wN + wS) + (wW + wE)) + ((wNW + wNE) + (wSW + wSE));
+          float Csum = wN * rN;
+          Csum = fmaf(wS, rSo, Csum);
+          Csum = fmaf(wW, rW, Csum);
+          Csum = fmaf(wE, rE, Csum);
+          Csum = fmaf(wNW, rNW, Csum);
+          Csum = fmaf(wNE, rNE, Csum);
+          Csum = fmaf(wSW, rSW, Csum);
+          Csum = fmaf(wSE, rSE, Csum);
+          const float root = icd_root(Wsum, Csum, sS[o]);
+          rS[o] = fmaxf(root, P.r_floor);
+        }
+        cluster.sync();  // B4..B7
+      }
     }
   }
   // ---- write the reflectance slab back (row-major N x N) ---------------------------------
