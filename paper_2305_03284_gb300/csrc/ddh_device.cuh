@@ -242,6 +242,26 @@ __device__ __forceinline__ float icd_root(float W, float C, float s) {
   return newton_cubic(r, W, C, s);
 }
 
+// Same root, solved first by Newton from `r_start` (the pixel's entry value, close to the
+// update) when f is monotone (C^2 <= 3W: a single real root, so Newton cannot pick another
+// one).  Accepted when the last step changed r by less than 2^-20 relative; otherwise, and
+// whenever f is not monotone, the closed form above decides.
+__device__ __forceinline__ float icd_root_from(float W, float C, float s, float r_start) {
+  if (W > 0.f && C * C <= 3.f * W && r_start > 0.f) {
+    float r = r_start;
+    float step = 0.f;
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const float f = fmaf(fmaf(fmaf(W, r, -C), r, 1.f), r, -s);
+      const float fp = fmaf(fmaf(3.f * W, r, -2.f * C), r, 1.f);  // >= 1 - C^2/(3W) >= 0
+      step = __fdividef(f, fp);
+      r -= step;
+    }
+    if (r > 0.f && fabsf(step) <= 9.5367431640625e-7f * r) return r;
+  }
+  return icd_root(W, C, s);
+}
+
 // ------------------------------------------------------------------- TMA and mbarrier
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -32,7 +32,8 @@ struct StepLayout {
   static constexpr size_t colbuf = al(rowbuf + size_t(R) * CS * 8);
   static constexpr size_t ybuf = al(colbuf + size_t(W) * CS * 8);
   static constexpr size_t phib = al(ybuf + size_t(R) * N * 8);
-  static constexpr size_t rS = al(phib + size_t(R) * N * 4);
+  static constexpr size_t phin = al(phib + size_t(R) * N * 4);  // phi of row rho + 1
+  static constexpr size_t rS = al(phin + size_t(R) * N * 4);
   static constexpr size_t r0S = al(rS + size_t(W) * CS * 4);
   static constexpr size_t sS = al(r0S + size_t(W) * CS * 4);
   static constexpr size_t halo = al(sS + size_t(W) * CS * 4);  // 3 x N halo-pair weights
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   float2* colbuf = reinterpret_cast<float2*>(smem + L::colbuf);
   float2* ybuf = reinterpret_cast<float2*>(smem + L::ybuf);
   float* phib = reinterpret_cast<float*>(smem + L::phib);
+  float* phin = reinterpret_cast<float*>(smem + L::phin);
   float* rS = reinterpret_cast<float*>(smem + L::rS);
   float* r0S = reinterpret_cast<float*>(smem + L::r0S);
   float* sS = reinterpret_cast<float*>(smem + L::sS);
@@ -110,13 +112,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     }
   }
   for (int i = tid; i < N; i += kThreads) tw[i] = batch.tw[i];
-  for (int i = tid; i < R * N; i += kThreads) {
-    const int l = i / N, x = i - l * N;
-    phib[i] = A.phi[static_cast<size_t>(row_of<C>(k, l, P.g_shift)) * N + x];
-  }
-  for (int i = tid; i < N * W; i += kThreads) {
-    const int rho = i / W, cl = i - rho * W;
-    rS[cl * CS + rho] = A.r[static_cast<size_t>(rho) * N + W * k + cl];
+  {
+    // phi rows rho and rho + 1 (the latter for the y tip/tilt pairs), 16-byte vectors
+    constexpr int V = N / 4;
+    const float4* src = reinterpret_cast<const float4*>(A.phi);
+    for (int i = tid; i < R * V; i += kThreads) {
+      const int l = i / V, xv = i - l * V;
+      const int rho = row_of<C>(k, l, P.g_shift);
+      reinterpret_cast<float4*>(phib)[i] = src[static_cast<size_t>(rho) * V + xv];
+      reinterpret_cast<float4*>(phin)[i] =
+          rho + 1 < N ? src[static_cast<size_t>(rho + 1) * V + xv] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // reflectance slab: W = 16 consecutive floats per row = 4 vectors
+    for (int i = tid; i < N * (W / 4); i += kThreads) {
+      const int rho = i / (W / 4), cv = i - rho * (W / 4);
+      const float4 v = reinterpret_cast<const float4*>(A.r + static_cast<size_t>(rho) * N + W * k)[cv];
+      rS[(4 * cv + 0) * CS + rho] = v.x;
+      rS[(4 * cv + 1) * CS + rho] = v.y;
+      rS[(4 * cv + 2) * CS + rho] = v.z;
+      rS[(4 * cv + 3) * CS + rho] = v.w;
+    }
   }
   for (int i = tid; i < W * CS; i += kThreads) colbuf[i] = make_float2(0.f, 0.f);
   // bounded wait: on expiry the frame is dropped (flag carried into the B1 statistics)
@@ -148,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           txc += 1.f;
         }
         if (dx2 + dy2n <= P.ap_lim) {
-          tys += wrap_pi(A.phi[static_cast<size_t>(rho + 1) * N + x] - pr[x]);
+          tys += wrap_pi(phin[l * N + x] - pr[x]);
           tyc += 1.f;
         }
       }
@@ -254,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
             pr[x] = ph;
             const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
             float sn, cs;
-            sincosf(ph, &sn, &cs);
+            __sincosf(ph, &sn, &cs);  // |ph| <= pi: absolute error ~ 5e-7
             rb[x] = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
           } else {
             rb[x] = make_float2(0.f, 0.f);
@@ -423,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           Csum = fmaf(wNE, rNE, Csum);
           Csum = fmaf(wSW, rSW, Csum);
           Csum = fmaf(wSE, rSE, Csum);
-          const float root = icd_root(Wsum, Csum, sS[o]);
+          const float root = icd_root_from(Wsum, Csum, sS[o], r0S[o]);
           rS[o] = fmaxf(root, P.r_floor);
         }
         cluster.sync();  // B4..B7
