@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument("--ring", type=int, default=RING_FRAMES)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -202,6 +203,75 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def batched_measure(ddh, peak_gbs, timesteps=200, ring=10, warm=5):
+    """Many independent streams of mixed grid size (the <= 256^2 part of the 64-stream mix):
+    one launch per stream per time step ("plain") against one captured graph per time step."""
+    import torch
+    from synth import ddh_synth as sy
+    cfgs = [c for c in sy.config_batched(frames=timesteps) if c.n <= 256]
+    rings = []
+    for c in cfgs:
+        ys, _ = sy.Stream(c).frames(ring)
+        rings.append(torch.from_numpy(ys).cuda())
+    stream = torch.cuda.Stream()
+    out = {"workload": f"{len(cfgs)} independent streams: "
+                       f"{sum(c.n == 128 for c in cfgs)} x 128^2 + {sum(c.n == 256 for c in cfgs)} x 256^2, "
+                       "pupil = grid/2, seeded D/r0 and wind per stream, 1 EM iteration per frame",
+           "timesteps": timesteps, "frames_ring_per_stream": ring,
+           "ring_bytes": int(sum(r.numel() * 8 for r in rings))}
+    px = sum(c.n * c.n for c in cfgs)
+    with torch.cuda.stream(stream):
+        lib = ddh.lib()
+        ptr_tab = [[ddh.c_void_p(rings[i][t].data_ptr()) for i in range(len(cfgs))] for t in range(ring)]
+        arrs = [(ddh.c_void_p * len(cfgs))(*row) for row in ptr_tab]
+
+        def measure(kind):
+            sts = [ddh.Stream(ddh.default_params(c.n, c.aperture_diam, c.snr), stream=stream) for c in cfgs]
+            hs = [s._h for s in sts]
+            g = ddh.BatchGraph(sts) if kind == "graph" else None
+
+            def one(t):
+                if g is not None:
+                    g.run_ptrs(arrs[t % ring])
+                else:
+                    for h, ptr in zip(hs, ptr_tab[t % ring]):
+                        lib.ddh_step(h, ptr)
+            for t in range(warm):
+                one(t)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for t in range(timesteps):
+                one(warm + t)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            lat = []
+            for t in range(min(timesteps, 100)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                one(t)
+                b.record(stream)
+                b.synchronize()
+                lat.append(a.elapsed_time(b) * 1e3)
+            for s in sts:
+                s.sync()
+            if g is not None:
+                g.close()
+            lat.sort()
+            per_step_s = ms * 1e-3 / timesteps
+            return {"frames_per_s": len(cfgs) / per_step_s, "us_per_timestep": per_step_s * 1e6,
+                    "latency_us_p50": lat[len(lat) // 2], "latency_us_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                    "hbm_gbs_algorithmic": BYTES_PER_PX * px / per_step_s / 1e9,
+                    "hbm_frac": BYTES_PER_PX * px / per_step_s / 1e9 / peak_gbs,
+                    "launches_per_timestep": (len(cfgs) if g is None else "1 graph")}
+        out["plain"] = measure("plain")
+        out["graph"] = measure("graph")
+    out["speedup_frames_per_s"] = out["graph"]["frames_per_s"] / out["plain"]["frames_per_s"]
+    out["latency"] = "per time step (every stream advanced one frame), frames resident in HBM"
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -287,6 +357,11 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_PX * n * n
     avg_launch_s = ms * 1e-3 / args.steps
     achieved = bytes_per_launch / avg_launch_s / 1e9
+    batched = None
+    if not args.no_batched and world == 1:
+        from paper_2305_03284_gb300 import autotune
+        autotune.apply()
+        batched = batched_measure(ddh, peak)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -307,6 +382,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "batched": batched,
     }
     print(json.dumps(line))
 

@@ -99,9 +99,31 @@ int64_t ddh_frame_index(const ddh_state *s);
  * the value lands in *out.  Evaluation only, never part of a step. */
 int ddh_strehl(ddh_state *s, const float *phi_true_dev, float *out);
 
-/* Advance `count` states by one frame each in one launch per grid size (states with equal N
- * share one cluster-per-stream launch).  All states must share the stream of states[0]. */
+/* Advance `count` states by one frame each: one cluster-per-stream launch per grid size (up to
+ * 32 streams per launch), the grid-size groups on concurrent library-owned branches forked
+ * from and joined back into the stream of states[0], which all states must share.  Each state
+ * appears at most once; frames as for ddh_step. */
 int ddh_step_batch(ddh_state *const *states, const void *const *y_c64_dev, int count);
+
+/* Batched step as a captured CUDA graph.  ddh_batch_create() records one step of every state
+ * (any mix of N; all states on the stream and device of states[0], each at most once) into a
+ * graph whose grid-size groups run on concurrent branches; the graph reads each stream's frame
+ * through a device table of frame pointers owned by the batch.  ddh_batch_run() uploads the
+ * table from `y_c64_dev` (count device pointers, 16-byte aligned, valid until the step has
+ * run) and launches the graph on that stream: one graph launch per time step.  The graph
+ * holds each state's parameters as they were at creation: rebuild it after ddh_load.  The
+ * batch does not own the states; free it before them. */
+typedef struct ddh_batch ddh_batch;
+int ddh_batch_create(ddh_batch **out, ddh_state *const *states, int count);
+int ddh_batch_run(ddh_batch *b, const void *const *y_c64_dev);
+int ddh_batch_free(ddh_batch *b);
+
+/* FFT radix schedule used for grid size n on the current device (the autotuner's choice):
+ * count of schedules, select one (affects later launches and later ddh_batch_create), query.
+ * Schedules differ only in rounding. */
+int ddh_fft_schedule_count(int n);
+int ddh_set_fft_schedule(int n, int schedule);
+int ddh_get_fft_schedule(int n);
 
 /* Unitary 2D DFT (Sec. 2, F) or its inverse (inverse != 0) of one N x N complex64 image,
  * device in/out (may alias), on `cuda_stream`.  N as for ddh_params. */

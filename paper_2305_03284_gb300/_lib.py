@@ -54,6 +54,12 @@ _SIGS = {
     "ddh_frame_index": (c_int64, [c_void_p]),
     "ddh_strehl": (c_int, [c_void_p, c_void_p, POINTER(c_float)]),
     "ddh_step_batch": (c_int, [POINTER(c_void_p), POINTER(c_void_p), c_int]),
+    "ddh_batch_create": (c_int, [POINTER(c_void_p), POINTER(c_void_p), c_int]),
+    "ddh_batch_run": (c_int, [c_void_p, POINTER(c_void_p)]),
+    "ddh_batch_free": (c_int, [c_void_p]),
+    "ddh_fft_schedule_count": (c_int, [c_int]),
+    "ddh_set_fft_schedule": (c_int, [c_int, c_int]),
+    "ddh_get_fft_schedule": (c_int, [c_int]),
     "ddh_fft2": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "ddh_sync": (c_int, [c_void_p]),
     "ddh_checkpoint_bytes": (c_size_t, [c_int]),

@@ -52,6 +52,30 @@ int n_slot(int n) { return n == 64 ? 0 : n == 128 ? 1 : 2; }
 std::mutex g_mu;
 bool g_configured[kMaxDevices][3] = {};
 float2* g_twiddle[kMaxDevices][3] = {};
+int g_schedule[kMaxDevices][3] = {};  // FFT radix schedule used for each grid size
+
+// Library-owned side streams that let the grid-size groups of one batch run concurrently.
+struct SideStreams {
+  bool ready = false;
+  cudaStream_t s[3] = {};
+  cudaEvent_t fork = nullptr, join[3] = {};
+};
+SideStreams g_side[kMaxDevices];
+
+int side_streams(int dev, SideStreams** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  SideStreams& ss = g_side[dev];
+  if (!ss.ready) {
+    for (int i = 0; i < 3; ++i) {
+      DDH_CUDA(cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking));
+      DDH_CUDA(cudaEventCreateWithFlags(&ss.join[i], cudaEventDisableTiming));
+    }
+    DDH_CUDA(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+    ss.ready = true;
+  }
+  *out = &ss;
+  return DDH_OK;
+}
 
 // Per-device, per-N setup: kernel attributes and the twiddle table exp(-2 pi i t / N),
 // evaluated in double precision and rounded once to float.
@@ -170,8 +194,63 @@ int enqueue(ddh_state* s, const void* y, float* trace) {
   b.fa[0] = frame_args(s, y, trace);
   b.tw = s->tw;
   b.count = 1;
-  DDH_CUDA(ddh::launch_step(s->prm.n, b, s->stream));
+  DDH_CUDA(ddh::launch_step(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], b, s->stream));
   s->frame += 1;
+  return DDH_OK;
+}
+
+// Enqueue one step of every state (all on `main`'s device): states are grouped by grid size,
+// each group (chunks of kMaxBatch) on its own side stream, forked from and joined back into
+// `main`.  Frames come from `ys[i]` or, when `ytab` is set, from ytab[i] on the device.
+int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2* const* ytab, int count,
+                  cudaStream_t main, int dev) {
+  const int sizes[3] = {64, 128, 256};
+  int groups = 0;
+  for (int n : sizes)
+    for (int i = 0; i < count; ++i)
+      if (states[i]->prm.n == n) { ++groups; break; }
+  SideStreams* ss = nullptr;
+  if (groups > 1) {
+    int rc = side_streams(dev, &ss);
+    if (rc != DDH_OK) return rc;
+    DDH_CUDA(cudaEventRecord(ss->fork, main));
+  }
+  int g = 0;
+  for (int n : sizes) {
+    ddh::StepBatch b{};
+    b.ytab = ytab;
+    int first = -1, members = 0;
+    for (int i = 0; i < count; ++i)
+      if (states[i]->prm.n == n) { if (first < 0) first = i; ++members; }
+    if (members == 0) continue;
+    cudaStream_t st = main;
+    if (ss != nullptr) {
+      st = ss->s[g];
+      DDH_CUDA(cudaStreamWaitEvent(st, ss->fork, 0));
+    }
+    const int sched = g_schedule[dev][n_slot(n)];
+    b.count = 0;
+    for (int i = 0; i < count; ++i) {
+      ddh_state* s = states[i];
+      if (s->prm.n != n) continue;
+      if (b.count == 0) b.ytab_base = i;  // ytab rows of one launch must be consecutive
+      b.prm[b.count] = s->kp;
+      b.fa[b.count] = frame_args(s, ys != nullptr ? ys[i] : nullptr, nullptr);
+      b.tw = s->tw;
+      ++b.count;
+      const bool next_same = i + 1 < count && states[i + 1]->prm.n == n;
+      if (b.count == ddh::kMaxBatch || (ytab != nullptr && !next_same)) {
+        DDH_CUDA(ddh::launch_step(n, sched, b, st));
+        b.count = 0;
+      }
+    }
+    if (b.count > 0) DDH_CUDA(ddh::launch_step(n, sched, b, st));
+    if (ss != nullptr) {
+      DDH_CUDA(cudaEventRecord(ss->join[g], st));
+      DDH_CUDA(cudaStreamWaitEvent(main, ss->join[g], 0));
+    }
+    ++g;
+  }
   return DDH_OK;
 }
 
@@ -320,37 +399,141 @@ int ddh_strehl(ddh_state* s, const float* phi_true_dev, float* out) {
   return check_status(s);
 }
 
-int ddh_step_batch(ddh_state* const* states, const void* const* ys, int count) {
-  if (states == nullptr || ys == nullptr || count < 0) return DDH_EINVAL;
-  if (count == 0) return DDH_OK;
+static int validate_batch(ddh_state* const* states, int count) {
+  if (states == nullptr || count < 0) return DDH_EINVAL;
   for (int i = 0; i < count; ++i) {
-    if (states[i] == nullptr || ys[i] == nullptr) return DDH_EINVAL;
-    if (reinterpret_cast<uintptr_t>(ys[i]) % 16 != 0) return DDH_EINVAL;
+    if (states[i] == nullptr) return DDH_EINVAL;
     if (states[i]->stream != states[0]->stream || states[i]->device != states[0]->device) return DDH_EINVAL;
     for (int j = 0; j < i; ++j)
       if (states[j] == states[i]) return DDH_EINVAL;  // a stream advances once per batch
   }
+  return DDH_OK;
+}
+
+int ddh_step_batch(ddh_state* const* states, const void* const* ys, int count) {
+  if (ys == nullptr) return DDH_EINVAL;
+  int rc = validate_batch(states, count);
+  if (rc != DDH_OK) return rc;
+  if (count == 0) return DDH_OK;
+  for (int i = 0; i < count; ++i)
+    if (ys[i] == nullptr || reinterpret_cast<uintptr_t>(ys[i]) % 16 != 0) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(states[0]->device));
-  const int sizes[3] = {64, 128, 256};
-  for (int n : sizes) {
-    ddh::StepBatch b{};
-    b.count = 0;
-    for (int i = 0; i < count; ++i) {
-      ddh_state* s = states[i];
-      if (s->prm.n != n) continue;
-      b.prm[b.count] = s->kp;
-      b.fa[b.count] = frame_args(s, ys[i], nullptr);
-      b.tw = s->tw;
-      ++b.count;
-      if (b.count == ddh::kMaxBatch) {
-        DDH_CUDA(ddh::launch_step(n, b, states[0]->stream));
-        b.count = 0;
-      }
-    }
-    if (b.count > 0) DDH_CUDA(ddh::launch_step(n, b, states[0]->stream));
-  }
+  rc = enqueue_batch(states, ys, nullptr, count, states[0]->stream, states[0]->device);
+  if (rc != DDH_OK) return rc;
   for (int i = 0; i < count; ++i) states[i]->frame += 1;
   return DDH_OK;
+}
+
+struct ddh_batch {
+  int count;
+  int device;
+  cudaStream_t stream;
+  cudaStream_t capture;
+  std::vector<ddh_state*> states;
+  const float2** ytab;      // device table of frame pointers read by the graph's kernels
+  const void** staging[4];  // pinned host copies of the table (a ring, one per run in flight)
+  cudaEvent_t slot_done[4];
+  int run;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+int ddh_batch_free(ddh_batch* b) {
+  if (b == nullptr) return DDH_OK;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  cudaFree(const_cast<float2**>(b->ytab));
+  for (int i = 0; i < 4; ++i) {
+    if (b->staging[i]) cudaFreeHost(b->staging[i]);
+    if (b->slot_done[i]) cudaEventDestroy(b->slot_done[i]);
+  }
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
+  return DDH_OK;
+}
+
+int ddh_batch_create(ddh_batch** out, ddh_state* const* states, int count) {
+  if (out == nullptr) return DDH_EINVAL;
+  *out = nullptr;
+  int rc = validate_batch(states, count);
+  if (rc != DDH_OK) return rc;
+  if (count == 0) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(states[0]->device));
+  ddh_batch* b = new ddh_batch{};
+  b->count = count;
+  b->device = states[0]->device;
+  b->stream = states[0]->stream;
+  b->states.assign(states, states + count);
+  cudaError_t e = cudaMalloc(&b->ytab, sizeof(float2*) * count);
+  for (int i = 0; e == cudaSuccess && i < 4; ++i) {
+    e = cudaMallocHost(&b->staging[i], sizeof(void*) * count);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->slot_done[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    const int code = cuda_fail(e);
+    ddh_batch_free(b);
+    return code;
+  }
+  // capture one batched step (grid-size groups on concurrent branches) into a graph
+  e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = enqueue_batch(states, nullptr, b->ytab, count, b->capture, b->device);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
+    b->graph = g;
+    if (rc == DDH_OK && e2 != cudaSuccess) rc = cuda_fail(e2);
+    if (rc == DDH_OK) {
+      e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      if (e != cudaSuccess) rc = cuda_fail(e);
+    }
+  } else {
+    rc = cuda_fail(e);
+  }
+  if (rc != DDH_OK) {
+    ddh_batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return DDH_OK;
+}
+
+int ddh_batch_run(ddh_batch* b, const void* const* ys) {
+  if (b == nullptr || ys == nullptr) return DDH_EINVAL;
+  for (int i = 0; i < b->count; ++i)
+    if (ys[i] == nullptr || reinterpret_cast<uintptr_t>(ys[i]) % 16 != 0) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(b->device));
+  const int slot = b->run & 3;
+  DDH_CUDA(cudaEventSynchronize(b->slot_done[slot]));  // that slot's previous upload has run
+  std::memcpy(b->staging[slot], ys, sizeof(void*) * b->count);
+  DDH_CUDA(cudaMemcpyAsync(const_cast<float2**>(b->ytab), b->staging[slot], sizeof(void*) * b->count,
+                           cudaMemcpyHostToDevice, b->stream));
+  DDH_CUDA(cudaEventRecord(b->slot_done[slot], b->stream));
+  DDH_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  b->run += 1;
+  for (ddh_state* s : b->states) s->frame += 1;
+  return DDH_OK;
+}
+
+int ddh_fft_schedule_count(int n) { return supported_n(n) ? ddh::schedule_count(n) : 0; }
+
+int ddh_set_fft_schedule(int n, int schedule) {
+  if (!supported_n(n) || schedule < 0 || schedule >= ddh::schedule_count(n)) return DDH_EINVAL;
+  int dev = 0;
+  DDH_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return DDH_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_schedule[dev][n_slot(n)] = schedule;
+  return DDH_OK;
+}
+
+int ddh_get_fft_schedule(int n) {
+  if (!supported_n(n)) return DDH_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DDH_ECUDA;
+  return g_schedule[dev][n_slot(n)];
 }
 
 int ddh_fft2(const void* in, void* out, int n, int inverse, void* cuda_stream) {

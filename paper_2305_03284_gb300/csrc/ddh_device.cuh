@@ -121,21 +121,60 @@ __device__ __forceinline__ void stockham_pass(float2* row, const float2* __restr
   __syncwarp();
 }
 
-// Unscaled length-N DFT of one shared-memory row by one warp (S = -1 forward, +1 inverse).
-template <int N, int S>
+// Radix schedules of the length-N row DFT (the autotuner picks one per N; every schedule is
+// the same DFT, up to rounding).
+template <int N>
+struct FftSchedules;
+template <>
+struct FftSchedules<64> { static constexpr int count = 2; };
+template <>
+struct FftSchedules<128> { static constexpr int count = 2; };
+template <>
+struct FftSchedules<256> { static constexpr int count = 3; };
+template <>
+struct FftSchedules<512> { static constexpr int count = 1; };
+
+// Unscaled length-N DFT of one shared-memory row by one warp (S = -1 forward, +1 inverse),
+// radix schedule V:  64: {8,8} | {4,4,4};  128: {8,4,4} | {2,8,8};
+// 256: {8,8,4} | {4,4,4,4} | {4,8,8};  512: {8,8,8}.
+template <int N, int S, int V = 0>
 __device__ __forceinline__ void fft_row(float2* row, const float2* __restrict__ tw, int lane) {
   static_assert(N == 64 || N == 128 || N == 256 || N == 512, "unsupported N");
+  static_assert(V >= 0 && V < FftSchedules<N>::count, "unknown schedule");
   if constexpr (N == 64) {
-    stockham_pass<64, 8, 1, S>(row, tw, lane);
-    stockham_pass<64, 8, 8, S>(row, tw, lane);
+    if constexpr (V == 0) {
+      stockham_pass<64, 8, 1, S>(row, tw, lane);
+      stockham_pass<64, 8, 8, S>(row, tw, lane);
+    } else {
+      stockham_pass<64, 4, 1, S>(row, tw, lane);
+      stockham_pass<64, 4, 4, S>(row, tw, lane);
+      stockham_pass<64, 4, 16, S>(row, tw, lane);
+    }
   } else if constexpr (N == 128) {
-    stockham_pass<128, 8, 1, S>(row, tw, lane);
-    stockham_pass<128, 4, 8, S>(row, tw, lane);
-    stockham_pass<128, 4, 32, S>(row, tw, lane);
+    if constexpr (V == 0) {
+      stockham_pass<128, 8, 1, S>(row, tw, lane);
+      stockham_pass<128, 4, 8, S>(row, tw, lane);
+      stockham_pass<128, 4, 32, S>(row, tw, lane);
+    } else {
+      stockham_pass<128, 2, 1, S>(row, tw, lane);
+      stockham_pass<128, 8, 2, S>(row, tw, lane);
+      stockham_pass<128, 8, 16, S>(row, tw, lane);
+    }
   } else if constexpr (N == 256) {
-    stockham_pass<256, 8, 1, S>(row, tw, lane);
-    stockham_pass<256, 8, 8, S>(row, tw, lane);
-    stockham_pass<256, 4, 64, S>(row, tw, lane);
+    if constexpr (V == 0) {
+      stockham_pass<256, 8, 1, S>(row, tw, lane);
+      stockham_pass<256, 8, 8, S>(row, tw, lane);
+      stockham_pass<256, 4, 64, S>(row, tw, lane);
+    } else if constexpr (V == 1) {
+      stockham_pass<256, 4, 1, S>(row, tw, lane);
+      stockham_pass<256, 4, 4, S>(row, tw, lane);
+      stockham_pass<256, 4, 16, S>(row, tw, lane);
+      stockham_pass<256, 4, 64, S>(row, tw, lane);
+    } else {
+      stockham_pass<256, 4, 1, S>(row, tw, lane);
+      stockham_pass<256, 8, 4, S>(row, tw, lane);
+      stockham_pass<256, 8, 32, S>(row, tw, lane);
+    }
   } else {
     stockham_pass<512, 8, 1, S>(row, tw, lane);
     stockham_pass<512, 8, 8, S>(row, tw, lane);

@@ -42,7 +42,9 @@ struct FrameArgs {
 struct StepBatch {
   KParams prm[kMaxBatch];
   FrameArgs fa[kMaxBatch];
-  const float2* tw;  // twiddle table exp(-2 pi i t / N), t < N
+  const float2* tw;                  // twiddle table exp(-2 pi i t / N), t < N
+  const float2* const* ytab;         // if set, stream i's frame is ytab[ytab_base + i]
+  int ytab_base;
   int count;
 };
 
@@ -63,12 +65,13 @@ struct Fft2Args {
 };
 
 // Launchers (return the CUDA error of the launch).  `n` selects the template instance.
-cudaError_t launch_step(int n, const StepBatch& b, cudaStream_t st);
+cudaError_t launch_step(int n, int schedule, const StepBatch& b, cudaStream_t st);
 cudaError_t launch_strehl(int n, const StrehlArgs& a, cudaStream_t st);
 cudaError_t launch_fft2(int n, const Fft2Args& a, cudaStream_t st);
 // One-time per-device function attributes (shared memory size, cluster size); also checks
 // that a cluster of this shape can be resident.  Returns cudaSuccess or the failing error.
 cudaError_t configure(int n, int* max_active_clusters);
 size_t step_smem_bytes(int n);
+int schedule_count(int n);  // FFT radix schedules available for grid n
 
 }  // namespace ddh

@@ -69,7 +69,7 @@ __device__ __forceinline__ void chan_combine(float& n_a, float2& m_a, float& q_a
   n_a = n;
 }
 
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant__ StepBatch batch) {
   using L = StepLayout<N>;
   constexpr int C = L::C, R = L::R, W = L::W, CS = L::CS;
@@ -106,9 +106,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   __syncthreads();
   if (tid == 0) {
     mbar_arrive_expect_tx(mbar, static_cast<uint32_t>(R * N * sizeof(float2)));
+    const float2* y = batch.ytab != nullptr ? batch.ytab[batch.ytab_base + sidx] : A.y;
     for (int l = 0; l < R; ++l) {
       const int rho = row_of<C>(k, l, P.g_shift);
-      tma_load_1d(ybuf + l * N, A.y + static_cast<size_t>(rho) * N, N * sizeof(float2), mbar);
+      tma_load_1d(ybuf + l * N, y + static_cast<size_t>(rho) * N, N * sizeof(float2), mbar);
     }
   }
   for (int i = tid; i < N; i += kThreads) tw[i] = batch.tw[i];
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           }
         }
         __syncwarp();
-        fft_row<N, +1>(rb, tw, lane);
+        fft_row<N, +1, V>(rb, tw, lane);
         for (int x = lane; x < N; x += 32) {
           float2* dst = cluster.map_shared_rank(colbuf, x / W);
           dst[(x % W) * CS + rho] = rb[x];
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     {
       const int cl = warp;
       float2* cb = colbuf + cl * CS;
-      fft_row<N, +1>(cb, tw, lane);
+      fft_row<N, +1, V>(cb, tw, lane);
       for (int rho = lane; rho < N; rho += 32) {
         const float2 b = c_scale(cb[rho], invN);
         const float rp = rS[cl * CS + rho];
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
         }
       }
       __syncwarp();
-      fft_row<N, -1>(cb, tw, lane);
+      fft_row<N, -1, V>(cb, tw, lane);
       for (int rho = lane; rho < N; rho += 32) {
         if (ap_dist2(rho, N) <= P.ap_lim) {
           float2* dst = cluster.map_shared_rank(rowbuf, row_owner<C>(rho, P.g_shift));
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       const bool row_ap = dy2 <= P.ap_lim;
       float2* rb = rowbuf + l * CS;
       const float2* yr = ybuf + l * N;
-      if (row_ap) fft_row<N, -1>(rb, tw, lane);
+      if (row_ap) fft_row<N, -1, V>(rb, tw, lane);
       for (int x = lane; x < N; x += 32) {
         float2 v = make_float2(0.f, 0.f);
         if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
@@ -574,11 +575,31 @@ static cudaError_t launch_cluster(Kern kern, int c, int clusters, size_t smem, c
   return cudaLaunchKernelEx(&cfg, kern, arg);
 }
 
+template <int N, int V>
+static cudaError_t configure_nv(int* max_active) {
+  using L = StepLayout<N>;
+  const void* f = reinterpret_cast<const void*>(k_ddh_step<N, V>);
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::total));
+  if (e == cudaSuccess && L::C > 8) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess || max_active == nullptr) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L::C, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = L::total;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = L::C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(max_active, f, &cfg);
+}
+
 template <int N>
 static cudaError_t configure_n(int* max_active) {
   using L = StepLayout<N>;
-  const void* kerns[3] = {reinterpret_cast<const void*>(k_ddh_step<N>), reinterpret_cast<const void*>(k_strehl<N>),
-                          reinterpret_cast<const void*>(k_fft2<N>)};
+  const void* kerns[2] = {reinterpret_cast<const void*>(k_strehl<N>), reinterpret_cast<const void*>(k_fft2<N>)};
   for (const void* f : kerns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L::total));
     if (e != cudaSuccess) return e;
@@ -587,20 +608,10 @@ static cudaError_t configure_n(int* max_active) {
       if (e != cudaSuccess) return e;
     }
   }
-  if (max_active != nullptr) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(L::C, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = L::total;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = L::C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(max_active, reinterpret_cast<const void*>(k_ddh_step<N>), &cfg);
-  }
+  cudaError_t e = configure_nv<N, 0>(max_active);
+  if (e != cudaSuccess) return e;
+  if constexpr (FftSchedules<N>::count > 1) { e = configure_nv<N, 1>(nullptr); if (e != cudaSuccess) return e; }
+  if constexpr (FftSchedules<N>::count > 2) { e = configure_nv<N, 2>(nullptr); if (e != cudaSuccess) return e; }
   return cudaSuccess;
 }
 
@@ -613,6 +624,15 @@ cudaError_t configure(int n, int* max_active) {
   }
 }
 
+int schedule_count(int n) {
+  switch (n) {
+    case 64: return FftSchedules<64>::count;
+    case 128: return FftSchedules<128>::count;
+    case 256: return FftSchedules<256>::count;
+    default: return 0;
+  }
+}
+
 size_t step_smem_bytes(int n) {
   switch (n) {
     case 64: return StepLayout<64>::total;
@@ -622,11 +642,24 @@ size_t step_smem_bytes(int n) {
   }
 }
 
-cudaError_t launch_step(int n, const StepBatch& b, cudaStream_t st) {
+template <int N>
+static cudaError_t launch_step_n(int v, const StepBatch& b, cudaStream_t st) {
+  using L = StepLayout<N>;
+  if (v == 0) return launch_cluster(k_ddh_step<N, 0>, L::C, b.count, L::total, st, b);
+  if constexpr (FftSchedules<N>::count > 1) {
+    if (v == 1) return launch_cluster(k_ddh_step<N, 1>, L::C, b.count, L::total, st, b);
+  }
+  if constexpr (FftSchedules<N>::count > 2) {
+    if (v == 2) return launch_cluster(k_ddh_step<N, 2>, L::C, b.count, L::total, st, b);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step(int n, int v, const StepBatch& b, cudaStream_t st) {
   switch (n) {
-    case 64: return launch_cluster(k_ddh_step<64>, StepLayout<64>::C, b.count, StepLayout<64>::total, st, b);
-    case 128: return launch_cluster(k_ddh_step<128>, StepLayout<128>::C, b.count, StepLayout<128>::total, st, b);
-    case 256: return launch_cluster(k_ddh_step<256>, StepLayout<256>::C, b.count, StepLayout<256>::total, st, b);
+    case 64: return launch_step_n<64>(v, b, st);
+    case 128: return launch_step_n<128>(v, b, st);
+    case 256: return launch_step_n<256>(v, b, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -146,6 +146,51 @@ def step_batch(streams: list[Stream], frames: list[torch.Tensor]) -> None:
     check(lib().ddh_step_batch(hs, ys, len(streams)))
 
 
+class BatchGraph:
+    """One captured CUDA graph advancing every stream of a fixed set by one frame."""
+
+    def __init__(self, streams: list[Stream]):
+        self.streams = list(streams)
+        self._h = c_void_p()
+        hs = (c_void_p * len(streams))(*[s._h for s in streams])
+        check(lib().ddh_batch_create(byref(self._h), hs, len(streams)))
+
+    def run(self, frames: list[torch.Tensor]) -> None:
+        if len(frames) != len(self.streams):
+            raise ValueError("one frame per stream")
+        for s, y in zip(self.streams, frames):
+            _check_frame(y, s.n)
+        ys = (c_void_p * len(frames))(*[c_void_p(y.data_ptr()) for y in frames])
+        check(lib().ddh_batch_run(self._h, ys))
+
+    def run_ptrs(self, ptr_array) -> None:
+        """Run with a prepared ``(c_void_p * count)`` array of frame device pointers."""
+        check(lib().ddh_batch_run(self._h, ptr_array))
+
+    def close(self) -> None:
+        if self._h:
+            lib().ddh_batch_free(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fft_schedule_count(n: int) -> int:
+    return int(lib().ddh_fft_schedule_count(int(n)))
+
+
+def set_fft_schedule(n: int, schedule: int) -> None:
+    check(lib().ddh_set_fft_schedule(int(n), int(schedule)))
+
+
+def get_fft_schedule(n: int) -> int:
+    return int(lib().ddh_get_fft_schedule(int(n)))
+
+
 def fft2(x: torch.Tensor, inverse: bool = False, out: torch.Tensor | None = None) -> torch.Tensor:
     """Unitary 2-D DFT (``F`` of Sec. 2) or its inverse, computed by libddh."""
     n = x.shape[0]

@@ -1,0 +1,118 @@
+"""GPU: batched steps (concurrent grid-size groups, captured CUDA graph) and FFT schedules."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ddh_oracle as o
+from synth import ddh_synth as sy
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def ddh():
+    from paper_2305_03284_gb300 import build
+    build.build()
+    from paper_2305_03284_gb300 import ddh as mod
+    assert torch.cuda.is_available()
+    return mod
+
+
+def _cfgs():
+    b = sy.config_batched(4)
+    # interleaved grid sizes, so that equal sizes are not adjacent
+    return [sy.config_single_64(4), b[0], sy.config_single_256(4), b[1], sy.config_single_64(4).__class__(
+        **{**sy.config_single_64(4).__dict__, "stream_id": 7}), b[33]]
+
+
+def _data(ddh, cfgs, frames):
+    out = []
+    for c in cfgs:
+        ys, _ = sy.Stream(sy.with_frames(c, frames)).frames(frames)
+        out.append((torch.from_numpy(ys).cuda(), ddh.default_params(c.n, c.aperture_diam, c.snr)))
+    return out
+
+
+def test_batch_graph_equals_solo_steps(ddh):
+    data = _data(ddh, _cfgs(), 4)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        solo = [ddh.Stream(p, stream=stream) for _, p in data]
+        grouped = [ddh.Stream(p, stream=stream) for _, p in data]
+        g = ddh.BatchGraph(grouped)
+        for f in range(4):
+            for s, (ys, _) in zip(solo, data):
+                s.step(ys[f])
+            g.run([ys[f] for ys, _ in data])
+        stream.synchronize()
+        for a, b in zip(solo, grouped):
+            assert torch.equal(a.phase(), b.phase()) and torch.equal(a.reflectance(), b.reflectance())
+            assert b.frame_index == 4
+        g.close()
+
+
+def test_step_batch_interleaved_sizes_equals_solo(ddh):
+    data = _data(ddh, _cfgs(), 3)
+    solo = [ddh.Stream(p) for _, p in data]
+    grouped = [ddh.Stream(p) for _, p in data]
+    for f in range(3):
+        for s, (ys, _) in zip(solo, data):
+            s.step(ys[f])
+        ddh.step_batch(grouped, [ys[f] for ys, _ in data])
+    for a, b in zip(solo, grouped):
+        assert torch.equal(a.phase(), b.phase()) and torch.equal(a.reflectance(), b.reflectance())
+
+
+def test_batch_graph_argument_errors(ddh):
+    data = _data(ddh, _cfgs()[:2], 1)
+    sts = [ddh.Stream(p) for _, p in data]
+    with pytest.raises(ddh.DdhError):
+        ddh.BatchGraph([sts[0], sts[0]])
+    g = ddh.BatchGraph(sts)
+    buf = torch.zeros(64 * 64 + 2, dtype=torch.complex64, device="cuda")
+    ptrs = (ddh.c_void_p * 2)(ddh.c_void_p(buf.data_ptr() + 8), ddh.c_void_p(data[1][0][0].data_ptr()))
+    assert ddh.lib().ddh_batch_run(g._h, ptrs) == -1  # misaligned frame
+    g.close()
+
+
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_every_fft_schedule_matches_oracle(ddh, n):
+    cfg = {64: sy.config_single_64(3), 128: sy.config_batched(3)[0], 256: sy.config_single_256(3)}[n]
+    ys, _ = sy.Stream(cfg).frames(3)
+    p = ddh.default_params(cfg.n, cfg.aperture_diam, cfg.snr)
+    prm = o.Params(n=p.n, aperture_diam=float(p.aperture_diam), lam=float(p.lam), alpha=float(p.alpha),
+                   n_k=p.n_k, noise_var=float(p.noise_var), prior_p=float(p.prior_p), prior_q=float(p.prior_q),
+                   prior_T=float(p.prior_T), prior_sigma=float(p.prior_sigma), r_floor=float(p.r_floor),
+                   tilt_mode=p.tilt_mode, phase_block=p.phase_block)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    ost = o.init_state(cfg.n)
+    for y in ys:
+        ost, _ = o.step(ost, y, prm)
+    old = ddh.get_fft_schedule(n)
+    try:
+        for sched in range(ddh.fft_schedule_count(n)):
+            ddh.set_fft_schedule(n, sched)
+            s = ddh.Stream(p)
+            for y in ys:
+                s.step(torch.from_numpy(y).cuda())
+            s.sync()
+            phi = s.phase().cpu().numpy().astype(np.float64)
+            r = s.reflectance().cpu().numpy().astype(np.float64)
+            assert np.linalg.norm(o.wrap(phi - ost.phi)[a]) / np.linalg.norm(ost.phi[a]) < TOL, sched
+            assert np.linalg.norm(r - ost.r) / np.linalg.norm(ost.r) < TOL, sched
+    finally:
+        ddh.set_fft_schedule(n, old)
+    with pytest.raises(ddh.DdhError):
+        ddh.set_fft_schedule(n, ddh.fft_schedule_count(n))
+
+
+def test_autotune_small(ddh, tmp_path):
+    from paper_2305_03284_gb300 import autotune
+    old = ddh.get_fft_schedule(64)
+    table = autotune.tune(sizes=(64,), streams_for={64: 2}, path=str(tmp_path / "t.json"))
+    assert set(table) == {"64"} and 0 <= table["64"]["schedule"] < ddh.fft_schedule_count(64)
+    assert ddh.get_fft_schedule(64) == table["64"]["schedule"]
+    assert autotune.apply(str(tmp_path / "t.json"))["64"]["schedule"] == table["64"]["schedule"]
+    ddh.set_fft_schedule(64, old)
