@@ -272,6 +272,55 @@ def batched_measure(ddh, peak_gbs, timesteps=200, ring=10, warm=5):
     return out
 
 
+def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
+    """Streaming service (continuous batching) against the same scheduler launching every
+    frame on its own, replaying one seeded Poisson arrival trace of the sensor mix."""
+    import numpy as np
+    import torch
+    from paper_2305_03284_gb300 import serve
+    from synth import ddh_synth as sy
+    cfgs = [c for c in sy.config_service(frames_total=total_frames) if c.n <= 256]
+    rates = np.array([c.rate_khz * 1e3 for c in cfgs])
+    horizon = total_frames / rates.sum()
+    rng = np.random.default_rng(seed)
+    rings = [torch.from_numpy(sy.Stream(sy.with_frames(c, ring)).frames(ring)[0]).cuda() for c in cfgs]
+    arrivals = []
+    for i, c in enumerate(cfgs):
+        t, k = 0.0, 0
+        while True:
+            t += rng.exponential(1.0 / rates[i])
+            if t > horizon:
+                break
+            arrivals.append((t, i, rings[i][k % ring]))
+            k += 1
+    arrivals.sort(key=lambda a: a[0])
+    out = {"workload": f"{len(cfgs)} sensors ({sum(c.n == 128 for c in cfgs)} x 128^2, "
+                       f"{sum(c.n == 256 for c in cfgs)} x 256^2), Poisson arrivals at 0.5-5 kHz per sensor, "
+                       f"{len(arrivals)} frames over {horizon * 1e3:.1f} ms",
+           "offered_frames_per_s": len(arrivals) / horizon}
+
+    def one(backend_cls, trace):
+        stream = torch.cuda.Stream()
+        svc = serve.Service(backend=backend_cls(stream), deliver_phase=False)
+        for i, c in enumerate(cfgs):
+            svc.admit(i, ddh.default_params(c.n, c.aperture_diam, c.snr))
+        svc.drive([(0.0, i, rings[i][0]) for i in range(len(cfgs))])  # warm-up frame each
+        t0 = time.perf_counter()
+        res = svc.drive(trace)
+        wall = time.perf_counter() - t0
+        lat = sorted(r.latency_s * 1e6 for r in res)
+        return {"frames_per_s": len(res) / wall, "latency_us_p50": lat[len(lat) // 2],
+                "latency_us_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "mean_batch": float(np.mean(svc.batch_sizes)), "launch_groups": svc.batches_launched}
+    out["continuous_batching"] = one(serve.LibddhBackend, arrivals)
+    out["per_frame_launch"] = one(serve.PerFrameLaunchBackend, arrivals)
+    burst = [(0.0, i, rings[i][k % ring]) for k in range(40) for i in range(len(cfgs))]
+    out["saturation_frames_per_s"] = {"continuous_batching": one(serve.LibddhBackend, burst)["frames_per_s"],
+                                      "per_frame_launch": one(serve.PerFrameLaunchBackend, burst)["frames_per_s"]}
+    out["latency"] = "scheduled arrival to completion event observed on the host"
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -361,6 +410,7 @@ def run_ours(args):
     batched = None
     if not args.no_batched and world == 1:
         batched = batched_measure(ddh, peak)
+        batched["service"] = service_measure(ddh)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)

@@ -83,13 +83,21 @@ class Stream:
             out = torch.empty((self.n, self.n), dtype=torch.float32, device="cuda")
         _check_image(out, self.n)
         check(lib().ddh_phase(self._h, c_void_p(out.data_ptr())))
+        self._join_current()
         return out
+
+    def _join_current(self) -> None:
+        """Order the caller's current stream after this state's stream (device copies)."""
+        cur = torch.cuda.current_stream()
+        if cur != self.torch_stream:
+            cur.wait_stream(self.torch_stream)
 
     def reflectance(self, out: torch.Tensor | None = None) -> torch.Tensor:
         if out is None:
             out = torch.empty((self.n, self.n), dtype=torch.float32, device="cuda")
         _check_image(out, self.n)
         check(lib().ddh_reflectance(self._h, c_void_p(out.data_ptr())))
+        self._join_current()
         return out
 
     def set_state(self, r: torch.Tensor, phi: torch.Tensor, frame_index: int) -> None:
