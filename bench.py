@@ -299,25 +299,29 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
                        f"{len(arrivals)} frames over {horizon * 1e3:.1f} ms",
            "offered_frames_per_s": len(arrivals) / horizon}
 
-    def one(backend_cls, trace):
-        stream = torch.cuda.Stream()
-        svc = serve.Service(backend=backend_cls(stream), deliver_phase=False)
+    def one(per_frame, trace):
+        svc = serve.NativeService(per_frame_launch=per_frame)
         for i, c in enumerate(cfgs):
             svc.admit(i, ddh.default_params(c.n, c.aperture_diam, c.snr))
         svc.drive([(0.0, i, rings[i][0]) for i in range(len(cfgs))])  # warm-up frame each
-        t0 = time.perf_counter()
+        st0 = svc.stats()
         res = svc.drive(trace)
-        wall = time.perf_counter() - t0
-        lat = sorted(r.latency_s * 1e6 for r in res)
-        return {"frames_per_s": len(res) / wall, "latency_us_p50": lat[len(lat) // 2],
+        st1 = svc.stats()
+        svc.close()
+        first = min(r[3] for r in res)
+        last = max(r[4] for r in res)
+        lat = sorted((r[4] - r[3]) * 1e6 for r in res)
+        batches = st1["batches"] - st0["batches"]
+        return {"frames_per_s": len(res) / (last - first), "latency_us_p50": lat[len(lat) // 2],
                 "latency_us_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                "mean_batch": float(np.mean(svc.batch_sizes)), "launch_groups": svc.batches_launched}
-    out["continuous_batching"] = one(serve.LibddhBackend, arrivals)
-    out["per_frame_launch"] = one(serve.PerFrameLaunchBackend, arrivals)
+                "mean_frames_per_launch_group": len(res) / max(1, batches), "launch_groups": batches}
+    out["continuous_batching"] = one(False, arrivals)
+    out["per_frame_launch"] = one(True, arrivals)
     burst = [(0.0, i, rings[i][k % ring]) for k in range(40) for i in range(len(cfgs))]
-    out["saturation_frames_per_s"] = {"continuous_batching": one(serve.LibddhBackend, burst)["frames_per_s"],
-                                      "per_frame_launch": one(serve.PerFrameLaunchBackend, burst)["frames_per_s"]}
-    out["latency"] = "scheduled arrival to completion event observed on the host"
+    out["saturation_frames_per_s"] = {"continuous_batching": one(False, burst)["frames_per_s"],
+                                      "per_frame_launch": one(True, burst)["frames_per_s"]}
+    out["scheduler"] = "libddh native scheduler thread (ddh_service_*), batches via ddh_step_batch"
+    out["latency"] = "scheduled arrival to completion event observed by the scheduler"
     return out
 
 

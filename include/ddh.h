@@ -118,6 +118,48 @@ int ddh_batch_create(ddh_batch **out, ddh_state *const *states, int count);
 int ddh_batch_run(ddh_batch *b, const void *const *y_c64_dev);
 int ddh_batch_free(ddh_batch *b);
 
+/* ---- streaming service: native continuous-batching scheduler -------------------------------
+ * Sensors are admitted against a device-memory budget and keep their state resident; frames
+ * are queued per sensor; a scheduler (a library thread after ddh_service_start, or each
+ * ddh_service_poll call otherwise) resolves finished batches and launches the next frame of
+ * every sensor that has one queued and none on the device, as one ddh_step_batch, without
+ * waiting for batches still running (at most `max_in_flight`).  A sensor's results do not
+ * depend on which other sensors share its launches.  The paper has a frame loop per sensor
+ * (Fig. 1); the multi-sensor service around it is this library's. */
+#define DDH_SERVICE_PER_FRAME_LAUNCH 1u /* comparison mode: one ddh_step launch per frame */
+typedef struct ddh_service ddh_service;
+typedef struct ddh_completion {
+  uint64_t tag;         /* the caller's tag from ddh_service_submit */
+  int sensor;           /* sensor id */
+  int64_t frame_index;  /* frames completed by this sensor, this one included */
+  double arrival_s;     /* arrival time (ddh_service_now() clock) */
+  double done_s;        /* time the scheduler saw the frame's batch complete */
+} ddh_completion;
+/* Create a service on `cuda_stream` (a non-default cudaStream_t; every admitted state is bound
+ * to it).  mem_budget_bytes 0 = free device memory at creation minus 1 GiB. */
+int ddh_service_create(ddh_service **out, void *cuda_stream, size_t mem_budget_bytes, int max_in_flight,
+                       unsigned flags);
+/* Device bytes one admitted state of grid n holds (r, phi, staging, status); 0 if n invalid. */
+size_t ddh_state_bytes(int n);
+/* Admit sensor `sensor_id` (unique) with parameters `p`: DDH_EBUDGET if its state would
+ * exceed the budget.  Release frees the state once its queued and running frames are done. */
+int ddh_service_admit(ddh_service *s, int sensor_id, const ddh_params *p);
+int ddh_service_release(ddh_service *s, int sensor_id);
+/* The sensor's state (for ddh_phase / ddh_reflectance between frames); NULL if unknown. */
+ddh_state *ddh_service_state(ddh_service *s, int sensor_id);
+/* Queue one frame (device pointer, caller-owned, valid until its completion is returned).
+ * arrival_s < 0 stamps the current time. */
+int ddh_service_submit(ddh_service *s, int sensor_id, const void *y_c64_dev, double arrival_s, uint64_t tag);
+/* Return up to max_out completions in arrival order of their batches; drives one scheduler
+ * iteration first when no library thread runs.  Returns a latched scheduler error if any. */
+int ddh_service_poll(ddh_service *s, ddh_completion *out, int max_out, int *n_out);
+int64_t ddh_service_pending(ddh_service *s); /* queued + running + unreturned frames */
+int ddh_service_stats(ddh_service *s, int64_t *batches, int64_t *frames, size_t *used_bytes);
+double ddh_service_now(void);                /* monotonic clock in seconds */
+int ddh_service_start(ddh_service *s);      /* run the scheduler on a library thread */
+int ddh_service_stop(ddh_service *s);
+int ddh_service_free(ddh_service *s);        /* stops, waits for the stream, frees the states */
+
 /* FFT radix schedule used for grid size n on the current device (the autotuner's choice):
  * count of schedules, select one (affects later launches and later ddh_batch_create), query.
  * Schedules differ only in rounding. */

@@ -35,6 +35,17 @@ class DdhParams(ctypes.Structure):
     ]
 
 
+class DdhCompletion(ctypes.Structure):
+    """Mirror of ``ddh_completion``."""
+    _fields_ = [
+        ("tag", ctypes.c_uint64),
+        ("sensor", c_int),
+        ("frame_index", c_int64),
+        ("arrival_s", ctypes.c_double),
+        ("done_s", ctypes.c_double),
+    ]
+
+
 class DdhError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
@@ -57,6 +68,19 @@ _SIGS = {
     "ddh_batch_create": (c_int, [POINTER(c_void_p), POINTER(c_void_p), c_int]),
     "ddh_batch_run": (c_int, [c_void_p, POINTER(c_void_p)]),
     "ddh_batch_free": (c_int, [c_void_p]),
+    "ddh_service_create": (c_int, [POINTER(c_void_p), c_void_p, c_size_t, c_int, ctypes.c_uint]),
+    "ddh_state_bytes": (c_size_t, [c_int]),
+    "ddh_service_admit": (c_int, [c_void_p, c_int, POINTER(DdhParams)]),
+    "ddh_service_release": (c_int, [c_void_p, c_int]),
+    "ddh_service_state": (c_void_p, [c_void_p, c_int]),
+    "ddh_service_submit": (c_int, [c_void_p, c_int, c_void_p, ctypes.c_double, ctypes.c_uint64]),
+    "ddh_service_poll": (c_int, [c_void_p, POINTER(DdhCompletion), c_int, POINTER(c_int)]),
+    "ddh_service_pending": (c_int64, [c_void_p]),
+    "ddh_service_stats": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_size_t)]),
+    "ddh_service_now": (ctypes.c_double, []),
+    "ddh_service_start": (c_int, [c_void_p]),
+    "ddh_service_stop": (c_int, [c_void_p]),
+    "ddh_service_free": (c_int, [c_void_p]),
     "ddh_fft_schedule_count": (c_int, [c_int]),
     "ddh_set_fft_schedule": (c_int, [c_int, c_int]),
     "ddh_get_fft_schedule": (c_int, [c_int]),

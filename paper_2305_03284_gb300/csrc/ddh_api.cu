@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/ddh.h"
+#include "ddh_internal.h"
 #include "ddh_kernels.cuh"
 
 struct ddh_state {
@@ -263,6 +264,8 @@ struct CkptHeader {
 constexpr uint32_t kMagic = 0x31484444u;  // "DDH1"
 
 }  // namespace
+
+int ddh_internal_cuda_fail(cudaError_t e) { return cuda_fail(e); }
 
 extern "C" {
 

@@ -78,3 +78,49 @@ def test_background_loop_and_phase_delivery(mods):
         ref.step(frames[k])
     assert [r.frame_index for r in res] == [1, 2, 3, 4]
     assert torch.equal(res[-1].phase, ref.phase())
+
+
+# ------------------------------------------------------------------ native scheduler
+def test_native_alone_equals_mix_and_per_frame_mode(mods):
+    ddh, serve = mods
+    cfgs = _sensors()
+    frames = [torch.from_numpy(sy.Stream(c).frames(6)[0]).cuda() for c in cfgs]
+    params = [ddh.default_params(c.n, c.aperture_diam, c.snr) for c in cfgs]
+    alone = serve.NativeService(mem_budget_bytes=1 << 34)
+    alone.admit(0, params[0])
+    res = alone.drive([(0.0, 0, frames[0][k]) for k in range(6)])
+    assert sorted(r[2] for r in res) == [1, 2, 3, 4, 5, 6]
+    rng = np.random.default_rng(1)
+    arrivals = sorted((float(t), i, frames[i][k]) for i in range(len(cfgs))
+                      for k, t in enumerate(np.cumsum(rng.exponential(2e-4, 6))))
+    outs = {}
+    for mode in (False, True):
+        mix = serve.NativeService(mem_budget_bytes=1 << 34, per_frame_launch=mode)
+        for i, p in enumerate(params):
+            mix.admit(i, p)
+        res = mix.drive(arrivals)
+        assert len(res) == 36 and all(r[4] >= r[3] for r in res)
+        for i in range(len(cfgs)):  # per-sensor completion order follows arrival order
+            idx = [r[0] for r in res if r[1] == i]
+            assert [r[2] for r in res if r[1] == i] == list(range(1, 7)) and idx == sorted(idx)
+        outs[mode] = (mix.phase(0), mix.reflectance(0), mix.stats())
+        mix.close()
+    assert outs[False][2]["batches"] < 36   # frames shared launches
+    for mode in (False, True):
+        assert torch.equal(alone.phase(0), outs[mode][0]) and torch.equal(alone.reflectance(0), outs[mode][1])
+    alone.close()
+
+
+def test_native_admission_budget(mods):
+    ddh, serve = mods
+    p256 = ddh.default_params(256, 128.0, 5.0)
+    need = ddh.lib().ddh_state_bytes(256)
+    svc = serve.NativeService(mem_budget_bytes=2 * need + 10)
+    svc.admit(1, p256)
+    svc.admit(2, p256)
+    with pytest.raises(serve.AdmissionError):
+        svc.admit(3, p256)
+    svc.release(1)
+    svc.admit(3, p256)
+    assert svc.stats()["used_bytes"] == 2 * need
+    svc.close()
