@@ -37,7 +37,7 @@ extern "C" {
 
 /* ---- parameters (Fig. 1 arguments lambda, alpha, N_k; Sec. 5.B values) -------------------- */
 typedef struct ddh_params {
-  int n;                /* grid side N: 64, 128 or 256 */
+  int n;                /* grid side N: 32, 64, 128 or 256 */
   float aperture_diam;  /* pupil diameter in px, 0 < d <= N */
   float lambda;         /* Eq. 3 weight of the back-projection term (paper: 0.45) */
   float alpha;          /* Eq. 3 scale of |A^H y|^2 (paper: 0.025) */
@@ -117,6 +117,25 @@ typedef struct ddh_batch ddh_batch;
 int ddh_batch_create(ddh_batch **out, ddh_state *const *states, int count);
 int ddh_batch_run(ddh_batch *b, const void *const *y_c64_dev);
 int ddh_batch_free(ddh_batch *b);
+
+/* ---- adjoint of one frame step (reverse mode through the EM iteration) -------------------
+ * The paper defines no derivative; this is the chain rule through the step of ddh_step
+ * (one EM iteration per frame, per-pixel phase: n_k 1 and phase_block 1, else DDH_EINVAL).
+ * Inputs (device, N*N float32 unless noted): the frame `y` (complex64, 16-byte aligned); the
+ * state entering the frame (`r_prev`, `phi_prev`); the frame's ddh_step_trace output `trace`
+ * recorded from that same state; the frame's output reflectance `r_new`; the gradients of a
+ * scalar loss with respect to the outputs (`r_bar`, `phi_bar`).  Outputs: the gradients with
+ * respect to the state entering the frame (`r_prev_bar`, `phi_prev_bar`, overwritten) and
+ * `grads` (3 floats, ADDED to): dL/dprior_sigma, dL/dprior_p, dL/dnoise_var.  `workspace` is
+ * caller-owned device memory of ddh_backward_workspace_bytes(N) bytes (16-byte aligned); the
+ * call allocates nothing.  Enqueued on the state's stream; the state's own r, phi are untouched.
+ * Non-differentiable points (floors, root-branch switches, zero surrogate differences) take
+ * the one-sided or zero derivative. */
+size_t ddh_backward_workspace_bytes(int n);
+int ddh_step_backward(ddh_state *s, const void *y_c64_dev, const float *r_prev, const float *phi_prev,
+                      const float *trace, const float *r_new, const float *r_bar, const float *phi_bar,
+                      float *r_prev_bar, float *phi_prev_bar, float *grads, void *workspace,
+                      size_t workspace_bytes);
 
 /* ---- streaming service: native continuous-batching scheduler -------------------------------
  * Sensors are admitted against a device-memory budget and keep their state resident; frames

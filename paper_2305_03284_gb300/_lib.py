@@ -81,6 +81,9 @@ _SIGS = {
     "ddh_service_start": (c_int, [c_void_p]),
     "ddh_service_stop": (c_int, [c_void_p]),
     "ddh_service_free": (c_int, [c_void_p]),
+    "ddh_backward_workspace_bytes": (c_size_t, [c_int]),
+    "ddh_step_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_void_p, c_void_p, c_size_t]),
     "ddh_fft_schedule_count": (c_int, [c_int]),
     "ddh_set_fft_schedule": (c_int, [c_int, c_int]),
     "ddh_get_fft_schedule": (c_int, [c_int]),

@@ -1,0 +1,423 @@
+// Hand-written adjoint of one DDH-MBIR frame step (one EM iteration, per-pixel phase).
+//
+// Given dL/dr_n and dL/dphi_n for the frame's outputs, the kernels below produce dL/dr_{n-1},
+// dL/dphi_{n-1} and the frame's contribution to dL/dsigma_r, dL/dp (q-GGMRF scale and shape)
+// and dL/dsigma^2, by the chain rule through the stages of the step in reverse:
+//   phase M-step phi = angle(v), v = y~ conj(z), z = F mu      (v_bar = phi_bar i v / |v|^2)
+//   ICD sweep, colours 3..0: r_i = root(W_i, C_i, s_i) differentiated implicitly,
+//       W = sum beta, C = sum beta r_j, beta_ij = b_ij w(r0_i - r0_j; sigma_r, p)
+//   E-step w = r0/(r0 + s2), mu = w b, s = |mu|^2 + s2 w; r-init (Eq. 3) with its floor
+//   back-projection b = F^H(a e^{-j phi'} y~), RemoveTipTilt phi' = phi - plane
+// The forward intermediates come from ddh_step_trace of the same frame from the same state
+// (the caller's per-frame checkpoint).  Complex gradients are dL/dRe + i dL/dIm.  All sums are
+// in a fixed order (deterministic).  The caller provides every buffer, workspace included.
+#include <cmath>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ddh.h"
+#include "ddh_device.cuh"
+#include "ddh_internal.h"
+#include "ddh_kernels.cuh"
+
+namespace ddh {
+namespace {
+
+constexpr int kBwThreads = 256;
+
+struct BwParams {
+  int n, ap_lim, tilt_mode;
+  float lam1, lam_alpha, noise_var, r_floor;
+  float w0, inv_tsig, q_minus_p, q_over_p, q, p, sigma, log_t;
+  float gx_scale, gy_scale;  // 1/|P_x|, 1/|P_y| (0 when there is no pair)
+};
+
+struct BwBuffers {
+  const float2* y;
+  const float* r_prev;
+  const float* phi_prev;
+  const float* trace;
+  const float* r_new;
+  const float* r_bar;
+  const float* phi_bar;
+  float* r_prev_bar;
+  float* phi_prev_bar;
+  float* grads;
+  // workspace
+  float2* cbuf1;  // z_bar -> mu_bar
+  float2* cbuf2;  // b_bar -> u_bar
+  float* abar;
+  float* r0bar;
+  float* sbar;
+  float* cbar;
+  float* wbar;
+  float* pg;      // 3 x M per-pixel parameter partials (sigma_r, p, sigma^2)
+  float* red;     // block partials of the tilt sums
+};
+
+struct WD {
+  float w, dd, ds, dp;
+};
+
+// w(D) = rho'(D)/D (q = 2) with its partial derivatives in D, sigma_r and p.
+__device__ __forceinline__ WD weight_derivs(float delta, const BwParams& P) {
+  const float ad = fabsf(delta);
+  const float t = ad * P.inv_tsig;
+  const float lt = t > 0.f ? logf(t) : 0.f;
+  const float u = t > 0.f ? expf(P.q_minus_p * lt) : 0.f;
+  const float A = P.q_over_p + u, B = 1.f + u;
+  WD r;
+  r.w = P.w0 * A / (B * B);
+  const float k = 1.f / A - 2.f / B;
+  const float du_dd = ad > 0.f ? P.q_minus_p * u / delta : 0.f;
+  r.dd = r.w * k * du_dd;
+  const float du_ds = -P.q_minus_p * u / P.sigma;
+  r.ds = r.w * (-2.f / P.sigma + k * du_ds);
+  const float du_dp = -u * lt;
+  r.dp = r.w * (P.log_t + (-P.q / (P.p * P.p) + du_dp) / A - 2.f * du_dp / B);
+  return r;
+}
+
+__device__ __forceinline__ int colour_of(int row, int col) { return (col & 1) + 2 * (row & 1); }
+
+__device__ __forceinline__ void neighbour(int nb, int& dy, int& dx, float& bij) {
+  // order: N, S, W, E, NW, NE, SW, SE (orthogonal weight first four)
+  const int dys[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
+  const int dxs[8] = {0, 0, -1, 1, -1, 1, -1, 1};
+  dy = dys[nb];
+  dx = dxs[nb];
+  bij = nb < 4 ? kBnn : kBdiag;
+}
+
+// phase M-step adjoint; also initialises the accumulators
+__global__ void k_bw_phase(BwParams P, BwBuffers B) {
+  const int n = P.n, M = n * n;
+  const float* stats = B.trace + static_cast<size_t>(8) * M;
+  const float2 mean = make_float2(stats[0], stats[1]);
+  const float scale = stats[2];
+  const float2* z = reinterpret_cast<const float2*>(B.trace) + 2 * M;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int row = i / n, col = i - row * n;
+    float2 zb = make_float2(0.f, 0.f);
+    if (ap_dist2(row, n) + ap_dist2(col, n) <= P.ap_lim) {
+      const float2 yt = c_scale(c_sub(B.y[i], mean), scale);
+      const float2 zz = z[i];
+      const float2 v = make_float2(fmaf(yt.x, zz.x, yt.y * zz.y), fmaf(yt.y, zz.x, -yt.x * zz.y));
+      const float m2 = c_abs2(v);
+      if (m2 > 0.f) {
+        const float g = B.phi_bar[i] / m2;
+        const float2 vb = make_float2(-v.y * g, v.x * g);  // phi_bar i v / |v|^2
+        zb = c_mul(yt, make_float2(vb.x, -vb.y));          // y~ conj(v_bar)
+      }
+    }
+    B.cbuf1[i] = zb;
+    B.abar[i] = B.r_bar[i];
+    B.r0bar[i] = 0.f;
+    B.sbar[i] = 0.f;
+    B.pg[i] = 0.f;
+    B.pg[M + i] = 0.f;
+    B.pg[2 * M + i] = 0.f;
+  }
+}
+
+// ICD adjoint, pass A for the pixels of colour c: implicit derivative of the root.
+__global__ void k_bw_icd_a(BwParams P, BwBuffers B, int c) {
+  const int n = P.n, M = n * n;
+  const float* r0 = B.trace + static_cast<size_t>(6) * M;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int row = i / n, col = i - row * n;
+    if (colour_of(row, col) != c) continue;
+    const float rn = B.r_new[i];
+    const float r0i = r0[i];
+    float Wsum = 0.f, Csum = 0.f;
+    float beta[8], cur[8];
+    WD wd[8];
+    bool in[8];
+    for (int nb = 0; nb < 8; ++nb) {
+      int dy, dx;
+      float bij;
+      neighbour(nb, dy, dx, bij);
+      const int rr = row + dy, cc = col + dx;
+      in[nb] = rr >= 0 && rr < n && cc >= 0 && cc < n;
+      if (!in[nb]) continue;
+      const int j = rr * n + cc;
+      wd[nb] = weight_derivs(r0i - r0[j], P);
+      beta[nb] = bij * wd[nb].w;
+      cur[nb] = colour_of(rr, cc) < c ? B.r_new[j] : r0[j];
+      Wsum += beta[nb];
+      Csum = fmaf(beta[nb], cur[nb], Csum);
+    }
+    const bool clamped = !(rn > P.r_floor);
+    const float gbar = clamped ? 0.f : B.abar[i];
+    B.abar[i] = 0.f;
+    const float gp = fmaf(fmaf(3.f * Wsum, rn, -2.f * Csum), rn, 1.f);
+    const float inv = gbar != 0.f ? gbar / gp : 0.f;
+    const float wbar = -inv * rn * rn * rn;
+    const float cbar = inv * rn * rn;
+    B.sbar[i] = inv;
+    B.cbar[i] = cbar;
+    B.wbar[i] = wbar;
+    float r0b = 0.f, gs = 0.f, gpp = 0.f;
+    for (int nb = 0; nb < 8; ++nb) {
+      if (!in[nb]) continue;
+      int dy, dx;
+      float bij;
+      neighbour(nb, dy, dx, bij);
+      const float bb = fmaf(cbar, cur[nb], wbar) * bij;
+      r0b = fmaf(bb, wd[nb].dd, r0b);
+      gs = fmaf(bb, wd[nb].ds, gs);
+      gpp = fmaf(bb, wd[nb].dp, gpp);
+    }
+    B.r0bar[i] += r0b;
+    B.pg[i] += gs;
+    B.pg[M + i] += gpp;
+  }
+}
+
+// ICD adjoint, pass B: every pixel gathers from its colour-c neighbours.
+__global__ void k_bw_icd_b(BwParams P, BwBuffers B, int c) {
+  const int n = P.n, M = n * n;
+  const float* r0 = B.trace + static_cast<size_t>(6) * M;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    const int row = j / n, col = j - row * n;
+    const int cj = colour_of(row, col);
+    if (cj == c) continue;
+    const float cur = cj < c ? B.r_new[j] : r0[j];
+    float ab = 0.f, r0b = 0.f;
+    for (int nb = 0; nb < 8; ++nb) {
+      int dy, dx;
+      float bij;
+      neighbour(nb, dy, dx, bij);
+      const int rr = row + dy, cc = col + dx;
+      if (rr < 0 || rr >= n || cc < 0 || cc >= n || colour_of(rr, cc) != c) continue;
+      const int i = rr * n + cc;
+      const WD wd = weight_derivs(r0[i] - r0[j], P);  // the pair as pixel i saw it
+      const float ci = B.cbar[i];
+      ab = fmaf(ci, bij * wd.w, ab);
+      r0b = fmaf(fmaf(ci, cur, B.wbar[i]) * bij, wd.dd, r0b);
+    }
+    B.abar[j] += ab;
+    B.r0bar[j] -= r0b;
+  }
+}
+
+// E-step and r-init adjoint.
+__global__ void k_bw_estep(BwParams P, BwBuffers B) {
+  const int n = P.n, M = n * n;
+  const float2* bt = reinterpret_cast<const float2*>(B.trace);
+  const float2* mut = bt + M;
+  const float* r0 = B.trace + static_cast<size_t>(6) * M;
+  const float s2 = P.noise_var;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const float2 b = bt[i], mu = mut[i];
+    const float r = r0[i];
+    const float sb = B.sbar[i];
+    float r0b = B.r0bar[i] + B.abar[i];
+    const float2 mub = make_float2(fmaf(2.f * sb, mu.x, B.cbuf1[i].x), fmaf(2.f * sb, mu.y, B.cbuf1[i].y));
+    const float d = r + s2;
+    const float w = r / d;
+    const float wb = fmaf(mub.x, b.x, mub.y * b.y) + sb * s2;
+    float2 bb = c_scale(mub, w);
+    B.pg[2 * M + i] = fmaf(sb, w, wb * (-r / (d * d)));
+    r0b = fmaf(wb, s2 / (d * d), r0b);
+    const float pre = fmaf(P.lam1, B.r_prev[i], P.lam_alpha * c_abs2(b));
+    const bool live = pre > P.r_floor;
+    B.r_prev_bar[i] = live ? P.lam1 * r0b : 0.f;
+    if (live) {
+      const float g = 2.f * P.lam_alpha * r0b;
+      bb = make_float2(fmaf(g, b.x, bb.x), fmaf(g, b.y, bb.y));
+    }
+    B.cbuf2[i] = bb;
+  }
+}
+
+// Back-projection adjoint: phi'_bar = Im(conj(u_bar) u) on the pupil, plus block partials of
+// the tilt adjoints t_x_bar = -sum phi'_bar (x - c), t_y_bar = -sum phi'_bar (y - c).
+__global__ void k_bw_tilt_a(BwParams P, BwBuffers B) {
+  const int n = P.n, M = n * n;
+  const float* stats = B.trace + static_cast<size_t>(8) * M;
+  const float2 mean = make_float2(stats[0], stats[1]);
+  const float scale = stats[2], tx = stats[3], ty = stats[4];
+  const float cc = 0.5f * static_cast<float>(n - 1);
+  float sx = 0.f, sy = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int row = i / n, col = i - row * n;
+    float pb = 0.f;
+    if (ap_dist2(row, n) + ap_dist2(col, n) <= P.ap_lim) {
+      float ph = B.phi_prev[i];
+      if (P.tilt_mode) ph = wrap_pi(ph - fmaf(tx, static_cast<float>(col) - cc, ty * (static_cast<float>(row) - cc)));
+      const float2 yt = c_scale(c_sub(B.y[i], mean), scale);
+      float sn, cs;
+      sincosf(ph, &sn, &cs);
+      const float2 u = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
+      const float2 ub = B.cbuf2[i];
+      pb = ub.x * u.y - ub.y * u.x;  // Im(conj(u_bar) u)
+      sx = fmaf(-pb, static_cast<float>(col) - cc, sx);
+      sy = fmaf(-pb, static_cast<float>(row) - cc, sy);
+    }
+    B.phi_prev_bar[i] = pb;
+  }
+  __shared__ float shx[kBwThreads], shy[kBwThreads];
+  shx[threadIdx.x] = sx;
+  shy[threadIdx.x] = sy;
+  __syncthreads();
+  for (int o = kBwThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      shx[threadIdx.x] += shx[threadIdx.x + o];
+      shy[threadIdx.x] += shy[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    B.red[2 * blockIdx.x] = shx[0];
+    B.red[2 * blockIdx.x + 1] = shy[0];
+  }
+}
+
+// Tilt-estimate adjoint (one block): phi_bar(x+1) += t_bar/|P|, phi_bar(x) -= t_bar/|P| for
+// every aperture pair; then the per-pixel parameter partials are reduced into grads.
+__global__ void k_bw_tilt_b(BwParams P, BwBuffers B, int blocks) {
+  const int n = P.n, M = n * n;
+  __shared__ float g[2];
+  __shared__ float sh[3][1024];
+  if (threadIdx.x == 0) {
+    float tx = 0.f, ty = 0.f;
+    for (int b = 0; b < blocks; ++b) {
+      tx += B.red[2 * b];
+      ty += B.red[2 * b + 1];
+    }
+    g[0] = P.tilt_mode ? tx * P.gx_scale : 0.f;
+    g[1] = P.tilt_mode ? ty * P.gy_scale : 0.f;
+  }
+  __syncthreads();
+  const float gx = g[0], gy = g[1];
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const int row = i / n, col = i - row * n;
+    const int dy2 = ap_dist2(row, n);
+    if (dy2 + ap_dist2(col, n) > P.ap_lim) {
+      B.phi_prev_bar[i] = 0.f;
+      continue;
+    }
+    float add = 0.f;
+    if (col > 0 && dy2 + ap_dist2(col - 1, n) <= P.ap_lim) add += gx;      // pair (x-1, x): right end
+    if (col + 1 < n && dy2 + ap_dist2(col + 1, n) <= P.ap_lim) add -= gx;  // pair (x, x+1): left end
+    const int dx2 = ap_dist2(col, n);
+    if (row > 0 && ap_dist2(row - 1, n) + dx2 <= P.ap_lim) add += gy;
+    if (row + 1 < n && ap_dist2(row + 1, n) + dx2 <= P.ap_lim) add -= gy;
+    B.phi_prev_bar[i] += add;
+  }
+  // parameter partials: fixed-order block reduction
+  for (int k = 0; k < 3; ++k) {
+    float acc = 0.f;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) acc += B.pg[k * M + i];
+    sh[k][threadIdx.x] = acc;
+  }
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 3; ++k) B.grads[k] += sh[k][0];
+}
+
+}  // namespace
+}  // namespace ddh
+
+extern "C" {
+
+size_t ddh_backward_workspace_bytes(int n) {
+  if (n != 32 && n != 64 && n != 128 && n != 256) return 0;
+  const size_t M = static_cast<size_t>(n) * n;
+  return sizeof(float) * (4 * M + 5 * M + 3 * M + 256);
+}
+
+}  // extern "C"
+
+int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle, void* stream_v, const void* y,
+                               const float* r_prev, const float* phi_prev, const float* trace, const float* r_new,
+                               const float* r_bar, const float* phi_bar, float* r_prev_bar, float* phi_prev_bar,
+                               float* grads, void* workspace) {
+  using namespace ddh;
+  cudaStream_t st = static_cast<cudaStream_t>(stream_v);
+  const size_t M = static_cast<size_t>(n) * n;
+  BwParams P{};
+  P.n = n;
+  const double d = prm->aperture_diam;
+  P.ap_lim = static_cast<int>(std::floor(d * d));
+  P.tilt_mode = prm->tilt_mode;
+  P.lam1 = static_cast<float>(1.0 - static_cast<double>(prm->lambda));
+  P.lam_alpha = static_cast<float>(static_cast<double>(prm->lambda) * prm->alpha);
+  P.noise_var = prm->noise_var;
+  P.r_floor = prm->r_floor;
+  const double ts = static_cast<double>(prm->prior_T) * prm->prior_sigma;
+  P.w0 = static_cast<float>(std::pow(ts, static_cast<double>(prm->prior_p) - 2.0) *
+                            std::pow(static_cast<double>(prm->prior_sigma), -static_cast<double>(prm->prior_p)));
+  P.inv_tsig = static_cast<float>(1.0 / ts);
+  P.q_minus_p = static_cast<float>(static_cast<double>(prm->prior_q) - prm->prior_p);
+  P.q_over_p = static_cast<float>(static_cast<double>(prm->prior_q) / prm->prior_p);
+  P.q = prm->prior_q;
+  P.p = prm->prior_p;
+  P.sigma = prm->prior_sigma;
+  P.log_t = static_cast<float>(std::log(static_cast<double>(prm->prior_T)));
+  // aperture pair counts of the tip/tilt regression (integer geometry)
+  int64_t px = 0, py = 0;
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      const int64_t dy = 2 * r - (n - 1), dx = 2 * c - (n - 1);
+      if (dx * dx + dy * dy > P.ap_lim) continue;
+      const int64_t dxn = 2 * (c + 1) - (n - 1), dyn = 2 * (r + 1) - (n - 1);
+      if (c + 1 < n && dxn * dxn + dy * dy <= P.ap_lim) ++px;
+      if (r + 1 < n && dx * dx + dyn * dyn <= P.ap_lim) ++py;
+    }
+  P.gx_scale = px > 0 ? static_cast<float>(1.0 / static_cast<double>(px)) : 0.f;
+  P.gy_scale = py > 0 ? static_cast<float>(1.0 / static_cast<double>(py)) : 0.f;
+
+  BwBuffers B{};
+  B.y = static_cast<const float2*>(y);
+  B.r_prev = r_prev;
+  B.phi_prev = phi_prev;
+  B.trace = trace;
+  B.r_new = r_new;
+  B.r_bar = r_bar;
+  B.phi_bar = phi_bar;
+  B.r_prev_bar = r_prev_bar;
+  B.phi_prev_bar = phi_prev_bar;
+  B.grads = grads;
+  float* ws = static_cast<float*>(workspace);
+  B.cbuf1 = reinterpret_cast<float2*>(ws);
+  B.cbuf2 = reinterpret_cast<float2*>(ws + 2 * M);
+  B.abar = ws + 4 * M;
+  B.r0bar = ws + 5 * M;
+  B.sbar = ws + 6 * M;
+  B.cbar = ws + 7 * M;
+  B.wbar = ws + 8 * M;
+  B.pg = ws + 9 * M;
+  B.red = ws + 12 * M;
+  const int blocks = 64;
+  k_bw_phase<<<blocks, kBwThreads, 0, st>>>(P, B);
+  Fft2Args f{};
+  f.in = B.cbuf1;
+  f.out = B.cbuf1;
+  f.tw = static_cast<const float2*>(twiddle);
+  f.inverse = 1;
+  cudaError_t e = launch_fft2(n, f, st);  // mu_bar = F^H z_bar
+  if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
+  for (int c = 3; c >= 0; --c) {
+    k_bw_icd_a<<<blocks, kBwThreads, 0, st>>>(P, B, c);
+    k_bw_icd_b<<<blocks, kBwThreads, 0, st>>>(P, B, c);
+  }
+  k_bw_estep<<<blocks, kBwThreads, 0, st>>>(P, B);
+  f.in = B.cbuf2;
+  f.out = B.cbuf2;
+  f.inverse = 0;
+  e = launch_fft2(n, f, st);  // u_bar = F b_bar
+  if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
+  k_bw_tilt_a<<<blocks, kBwThreads, 0, st>>>(P, B);
+  k_bw_tilt_b<<<1, 1024, 0, st>>>(P, B, blocks);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
+  return DDH_OK;
+}

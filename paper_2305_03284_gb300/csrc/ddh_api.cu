@@ -47,19 +47,19 @@ int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-bool supported_n(int n) { return n == 64 || n == 128 || n == 256; }
-int n_slot(int n) { return n == 64 ? 0 : n == 128 ? 1 : 2; }
+bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
+int n_slot(int n) { return n == 32 ? 3 : n == 64 ? 0 : n == 128 ? 1 : 2; }
 
 std::mutex g_mu;
-bool g_configured[kMaxDevices][3] = {};
-float2* g_twiddle[kMaxDevices][3] = {};
-int g_schedule[kMaxDevices][3] = {};  // FFT radix schedule used for each grid size
+bool g_configured[kMaxDevices][4] = {};
+float2* g_twiddle[kMaxDevices][4] = {};
+int g_schedule[kMaxDevices][4] = {};  // FFT radix schedule used for each grid size
 
 // Library-owned side streams that let the grid-size groups of one batch run concurrently.
 struct SideStreams {
   bool ready = false;
-  cudaStream_t s[3] = {};
-  cudaEvent_t fork = nullptr, join[3] = {};
+  cudaStream_t s[4] = {};
+  cudaEvent_t fork = nullptr, join[4] = {};
 };
 SideStreams g_side[kMaxDevices];
 
@@ -67,7 +67,7 @@ int side_streams(int dev, SideStreams** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   SideStreams& ss = g_side[dev];
   if (!ss.ready) {
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
       DDH_CUDA(cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking));
       DDH_CUDA(cudaEventCreateWithFlags(&ss.join[i], cudaEventDisableTiming));
     }
@@ -205,7 +205,7 @@ int enqueue(ddh_state* s, const void* y, float* trace) {
 // `main`.  Frames come from `ys[i]` or, when `ytab` is set, from ytab[i] on the device.
 int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2* const* ytab, int count,
                   cudaStream_t main, int dev) {
-  const int sizes[3] = {64, 128, 256};
+  const int sizes[4] = {32, 64, 128, 256};
   int groups = 0;
   for (int n : sizes)
     for (int i = 0; i < count; ++i)
@@ -518,6 +518,23 @@ int ddh_batch_run(ddh_batch* b, const void* const* ys) {
   b->run += 1;
   for (ddh_state* s : b->states) s->frame += 1;
   return DDH_OK;
+}
+
+int ddh_step_backward(ddh_state* s, const void* y, const float* r_prev, const float* phi_prev, const float* trace,
+                      const float* r_new, const float* r_bar, const float* phi_bar, float* r_prev_bar,
+                      float* phi_prev_bar, float* grads, void* workspace, size_t workspace_bytes) {
+  if (s == nullptr || y == nullptr || r_prev == nullptr || phi_prev == nullptr || trace == nullptr ||
+      r_new == nullptr || r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr ||
+      phi_prev_bar == nullptr || grads == nullptr || workspace == nullptr)
+    return DDH_EINVAL;
+  if (s->prm.n_k != 1 || s->prm.phase_block != 1) return DDH_EINVAL;
+  if (workspace_bytes < ddh_backward_workspace_bytes(s->prm.n)) return DDH_EINVAL;
+  if (reinterpret_cast<uintptr_t>(y) % 16 != 0 || reinterpret_cast<uintptr_t>(workspace) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(trace) % 8 != 0)
+    return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  return ddh_internal_step_backward(s->prm.n, &s->prm, s->tw, s->stream, y, r_prev, phi_prev, trace, r_new, r_bar,
+                                    phi_bar, r_prev_bar, phi_prev_bar, grads, workspace);
 }
 
 int ddh_fft_schedule_count(int n) { return supported_n(n) ? ddh::schedule_count(n) : 0; }

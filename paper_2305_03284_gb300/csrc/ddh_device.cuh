@@ -126,6 +126,8 @@ __device__ __forceinline__ void stockham_pass(float2* row, const float2* __restr
 template <int N>
 struct FftSchedules;
 template <>
+struct FftSchedules<32> { static constexpr int count = 2; };
+template <>
 struct FftSchedules<64> { static constexpr int count = 2; };
 template <>
 struct FftSchedules<128> { static constexpr int count = 2; };
@@ -135,13 +137,21 @@ template <>
 struct FftSchedules<512> { static constexpr int count = 1; };
 
 // Unscaled length-N DFT of one shared-memory row by one warp (S = -1 forward, +1 inverse),
-// radix schedule V:  64: {8,8} | {4,4,4};  128: {8,4,4} | {2,8,8};
+// radix schedule V:  32: {8,4} | {4,8};  64: {8,8} | {4,4,4};  128: {8,4,4} | {2,8,8};
 // 256: {8,8,4} | {4,4,4,4} | {4,8,8};  512: {8,8,8}.
 template <int N, int S, int V = 0>
 __device__ __forceinline__ void fft_row(float2* row, const float2* __restrict__ tw, int lane) {
-  static_assert(N == 64 || N == 128 || N == 256 || N == 512, "unsupported N");
+  static_assert(N == 32 || N == 64 || N == 128 || N == 256 || N == 512, "unsupported N");
   static_assert(V >= 0 && V < FftSchedules<N>::count, "unknown schedule");
-  if constexpr (N == 64) {
+  if constexpr (N == 32) {
+    if constexpr (V == 0) {
+      stockham_pass<32, 8, 1, S>(row, tw, lane);
+      stockham_pass<32, 4, 8, S>(row, tw, lane);
+    } else {
+      stockham_pass<32, 4, 1, S>(row, tw, lane);
+      stockham_pass<32, 8, 4, S>(row, tw, lane);
+    }
+  } else if constexpr (N == 64) {
     if constexpr (V == 0) {
       stockham_pass<64, 8, 1, S>(row, tw, lane);
       stockham_pass<64, 8, 8, S>(row, tw, lane);

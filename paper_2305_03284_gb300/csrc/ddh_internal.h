@@ -5,3 +5,10 @@
 
 // Record `e` as the library's last CUDA error and map it to DDH_ENOMEM / DDH_ECUDA.
 int ddh_internal_cuda_fail(cudaError_t e);
+
+struct ddh_params;
+// Enqueue the adjoint kernels of one frame step on `stream` (arguments as ddh_step_backward).
+int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle, void* stream, const void* y,
+                               const float* r_prev, const float* phi_prev, const float* trace, const float* r_new,
+                               const float* r_bar, const float* phi_bar, float* r_prev_bar, float* phi_prev_bar,
+                               float* grads, void* workspace);

@@ -200,7 +200,7 @@ int ddh_service_create(ddh_service** out, void* cuda_stream, size_t mem_budget_b
 }
 
 size_t ddh_state_bytes(int n) {
-  if (n != 64 && n != 128 && n != 256) return 0;
+  if (n != 32 && n != 64 && n != 128 && n != 256) return 0;
   const size_t img = sizeof(float) * static_cast<size_t>(n) * n;
   return 4 * img + 512;  // r, phi, 2-image staging buffer, status and scalar words
 }

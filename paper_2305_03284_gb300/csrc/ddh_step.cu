@@ -617,6 +617,7 @@ static cudaError_t configure_n(int* max_active) {
 
 cudaError_t configure(int n, int* max_active) {
   switch (n) {
+    case 32: return configure_n<32>(max_active);
     case 64: return configure_n<64>(max_active);
     case 128: return configure_n<128>(max_active);
     case 256: return configure_n<256>(max_active);
@@ -626,6 +627,7 @@ cudaError_t configure(int n, int* max_active) {
 
 int schedule_count(int n) {
   switch (n) {
+    case 32: return FftSchedules<32>::count;
     case 64: return FftSchedules<64>::count;
     case 128: return FftSchedules<128>::count;
     case 256: return FftSchedules<256>::count;
@@ -635,6 +637,7 @@ int schedule_count(int n) {
 
 size_t step_smem_bytes(int n) {
   switch (n) {
+    case 32: return StepLayout<32>::total;
     case 64: return StepLayout<64>::total;
     case 128: return StepLayout<128>::total;
     case 256: return StepLayout<256>::total;
@@ -657,6 +660,7 @@ static cudaError_t launch_step_n(int v, const StepBatch& b, cudaStream_t st) {
 
 cudaError_t launch_step(int n, int v, const StepBatch& b, cudaStream_t st) {
   switch (n) {
+    case 32: return launch_step_n<32>(v, b, st);
     case 64: return launch_step_n<64>(v, b, st);
     case 128: return launch_step_n<128>(v, b, st);
     case 256: return launch_step_n<256>(v, b, st);
@@ -666,6 +670,7 @@ cudaError_t launch_step(int n, int v, const StepBatch& b, cudaStream_t st) {
 
 cudaError_t launch_strehl(int n, const StrehlArgs& a, cudaStream_t st) {
   switch (n) {
+    case 32: return launch_cluster(k_strehl<32>, StepLayout<32>::C, 1, StepLayout<32>::total, st, a);
     case 64: return launch_cluster(k_strehl<64>, StepLayout<64>::C, 1, StepLayout<64>::total, st, a);
     case 128: return launch_cluster(k_strehl<128>, StepLayout<128>::C, 1, StepLayout<128>::total, st, a);
     case 256: return launch_cluster(k_strehl<256>, StepLayout<256>::C, 1, StepLayout<256>::total, st, a);
@@ -675,6 +680,7 @@ cudaError_t launch_strehl(int n, const StrehlArgs& a, cudaStream_t st) {
 
 cudaError_t launch_fft2(int n, const Fft2Args& a, cudaStream_t st) {
   switch (n) {
+    case 32: return launch_cluster(k_fft2<32>, StepLayout<32>::C, 1, StepLayout<32>::total, st, a);
     case 64: return launch_cluster(k_fft2<64>, StepLayout<64>::C, 1, StepLayout<64>::total, st, a);
     case 128: return launch_cluster(k_fft2<128>, StepLayout<128>::C, 1, StepLayout<128>::total, st, a);
     case 256: return launch_cluster(k_fft2<256>, StepLayout<256>::C, 1, StepLayout<256>::total, st, a);

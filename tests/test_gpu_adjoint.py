@@ -1,0 +1,141 @@
+"""GPU adjoint (ddh_step_backward, the autograd Function) against the FP64 oracle gradient
+and FP64 finite differences."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ddh_adjoint as adj
+from oracle import ddh_oracle as o
+from synth import ddh_synth as sy
+
+pytestmark = pytest.mark.gpu
+
+TOL_FRAME = 1e-3   # one frame: FP32 adjoint vs FP64 adjoint at the same (float32) inputs
+TOL_UNROLLED = 2e-2  # K = 8 frames: trajectories differ by FP32 rounding amplified per frame
+
+
+@pytest.fixture(scope="module")
+def mods():
+    from paper_2305_03284_gb300 import build
+    build.build()
+    from paper_2305_03284_gb300 import adjoint, ddh
+    return ddh, adjoint
+
+
+def _oracle_params(p):
+    return o.Params(n=p.n, aperture_diam=float(p.aperture_diam), lam=float(p.lam), alpha=float(p.alpha),
+                    n_k=p.n_k, noise_var=float(p.noise_var), prior_p=float(p.prior_p), prior_q=float(p.prior_q),
+                    prior_T=float(p.prior_T), prior_sigma=float(p.prior_sigma), r_floor=float(p.r_floor),
+                    tilt_mode=p.tilt_mode, phase_block=p.phase_block)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+@pytest.mark.parametrize("n,tilt", [(32, 1), (64, 1), (64, 0), (256, 1)])
+def test_frame_backward_matches_oracle(mods, n, tilt):
+    ddh, _ = mods
+    cfg = {32: sy.config_adjoint(small=True, streams=1, frames=3)[0], 64: sy.config_single_64(3),
+           256: sy.config_adjoint(streams=1, frames=3)[0]}[n]
+    ys, _ = sy.Stream(cfg).frames(3)
+    p = ddh.default_params(cfg.n, cfg.aperture_diam, cfg.snr, tilt_mode=tilt)
+    prm = _oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    st = o.init_state(cfg.n)
+    for y in ys[:2]:
+        st, _ = o.step(st, y, prm)
+    r32, p32 = st.r.astype(np.float32), st.phi.astype(np.float32)
+    rng = np.random.default_rng(n)
+    rbar = rng.standard_normal((n, n)).astype(np.float32)
+    pbar = np.where(a, rng.standard_normal((n, n)), 0.0).astype(np.float32)
+    ref_r, ref_p, ref_g, _ = adj.frame_backward(r32.astype(np.float64), p32.astype(np.float64), ys[2], prm,
+                                                rbar.astype(np.float64), pbar.astype(np.float64))
+    L = ddh.lib()
+    s = ddh.Stream(p)
+    cu = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    r_prev, phi_prev, y = cu(r32), cu(p32), cu(ys[2])
+    s.set_state(r_prev, phi_prev, 2)
+    tr = torch.zeros(L.ddh_trace_floats(n), dtype=torch.float32, device="cuda")
+    ddh.check(L.ddh_step_trace(s._h, ddh.c_void_p(y.data_ptr()), ddh.c_void_p(tr.data_ptr())))
+    r_new = s.reflectance()
+    ws = torch.empty(L.ddh_backward_workspace_bytes(n) // 4, dtype=torch.float32, device="cuda")
+    g = torch.zeros(3, dtype=torch.float32, device="cuda")
+    out_r, out_p = torch.empty((n, n), device="cuda"), torch.empty((n, n), device="cuda")
+    rb_t, pb_t = cu(rbar), cu(pbar)
+    ptr = lambda t: ddh.c_void_p(t.data_ptr())
+    ddh.check(L.ddh_step_backward(s._h, ptr(y), ptr(r_prev), ptr(phi_prev), ptr(tr), ptr(r_new), ptr(rb_t), ptr(pb_t),
+                                  ptr(out_r), ptr(out_p), ptr(g), ptr(ws), ws.numel() * 4))
+    torch.cuda.synchronize()
+    er, ep = _rel(out_r.cpu().numpy(), ref_r), _rel(out_p.cpu().numpy(), ref_p)
+    eg = np.abs(g.cpu().numpy().astype(np.float64) - ref_g) / np.maximum(np.abs(ref_g), 1e-12)
+    print(f"n={n} tilt={tilt} r_bar {er:.2e} phi_bar {ep:.2e} grads {eg}")
+    assert er < TOL_FRAME and ep < TOL_FRAME and np.all(eg < TOL_FRAME), (er, ep, eg)
+
+
+def test_unrolled_autograd_matches_oracle_and_fd(mods):
+    """K = 8 frames on the 32x32 copy of the differentiation workload, through
+    torch.autograd: gradients in sigma_r, p, sigma^2, phi0 and r0."""
+    ddh, adjoint = mods
+    K = 8
+    cfg = sy.config_adjoint(small=True, streams=1, frames=K)[0]
+    ys, _ = sy.Stream(cfg).frames(K)
+    p = ddh.default_params(32, 16.0, cfg.snr)
+    prm = _oracle_params(p)
+    a = o.aperture(32, 16.0)
+    rng = np.random.default_rng(4)
+    phi0 = np.where(a, 0.3 * rng.standard_normal((32, 32)), 0.0).astype(np.float32)
+    r0 = (0.05 + 0.02 * rng.random((32, 32))).astype(np.float32)
+    c = rng.standard_normal((3, 32, 32))
+    frames = torch.from_numpy(ys).cuda()
+    at = torch.from_numpy(a).cuda()
+    ct = torch.from_numpy(c).cuda()
+    r0t = torch.from_numpy(r0).cuda().requires_grad_(True)
+    p0t = torch.from_numpy(phi0).cuda().requires_grad_(True)
+    sig = torch.tensor(float(p.prior_sigma), dtype=torch.float64, requires_grad=True)
+    pp = torch.tensor(float(p.prior_p), dtype=torch.float64, requires_grad=True)
+    s2 = torch.tensor(float(p.noise_var), dtype=torch.float64, requires_grad=True)
+    rK, phiK = adjoint.unrolled(r0t, p0t, sig, pp, s2, frames, p)
+    loss = (at * (ct[0] * torch.cos(phiK) + ct[1] * torch.sin(phiK))).sum() + (ct[2] * rK).sum()
+    loss.backward()
+    gpu = np.array([sig.grad.item(), pp.grad.item(), s2.grad.item()])
+    # oracle gradient along the oracle's own FP64 trajectory from the same float32 start
+    st = o.State(r=r0.astype(np.float64), phi=phi0.astype(np.float64))
+    for y in ys:
+        st, _ = o.step(st, y, prm)
+    phib = a * (-c[0] * np.sin(st.phi) + c[1] * np.cos(st.phi))
+    rb, pb, g, _ = adj.unrolled_grad(r0.astype(np.float64), phi0.astype(np.float64), ys, prm, c[2], phib)
+    eg = np.abs(gpu - g) / np.abs(g)
+    ephi = _rel(p0t.grad.cpu().numpy(), pb)
+    er = _rel(r0t.grad.cpu().numpy(), rb)
+    print(f"unrolled K=8: grads rel {eg}, phi0 {ephi:.2e}, r0 {er:.2e}")
+    assert np.all(eg < TOL_UNROLLED) and ephi < TOL_UNROLLED and er < TOL_UNROLLED
+    # FP64 central finite difference of the oracle in sigma_r (h = 1e-6)
+    from dataclasses import replace
+
+    def L(prm_):
+        s_ = o.State(r=r0.astype(np.float64), phi=phi0.astype(np.float64))
+        for y in ys:
+            s_, _ = o.step(s_, y, prm_)
+        return float(np.sum(a * (c[0] * np.cos(s_.phi) + c[1] * np.sin(s_.phi))) + np.sum(c[2] * s_.r))
+    h = 1e-6
+    fd = (L(replace(prm, prior_sigma=prm.prior_sigma + h)) - L(replace(prm, prior_sigma=prm.prior_sigma - h))) / (2 * h)
+    assert abs(gpu[0] - fd) < TOL_UNROLLED * abs(fd), (gpu[0], fd)
+
+
+def test_config4_sixteen_streams_256(mods):
+    """16 streams at 256^2, K = 8 unrolled steps each: finite gradients for every stream."""
+    ddh, adjoint = mods
+    cfgs = sy.config_adjoint(streams=16, frames=8)
+    for cfg in cfgs[:16]:
+        ys, _ = sy.Stream(cfg).frames(8)
+        p = ddh.default_params(cfg.n, cfg.aperture_diam, cfg.snr)
+        r0 = torch.zeros((256, 256), device="cuda", requires_grad=True)
+        phi0 = torch.zeros((256, 256), device="cuda", requires_grad=True)
+        sig = torch.tensor(float(p.prior_sigma), dtype=torch.float64, requires_grad=True)
+        pp = torch.tensor(float(p.prior_p), dtype=torch.float64, requires_grad=True)
+        s2 = torch.tensor(float(p.noise_var), dtype=torch.float64, requires_grad=True)
+        rK, phiK = adjoint.unrolled(r0, phi0, sig, pp, s2, torch.from_numpy(ys).cuda(), p)
+        (torch.cos(phiK).sum() + rK.sum()).backward()
+        for t in (sig.grad, pp.grad, s2.grad, r0.grad, phi0.grad):
+            assert torch.isfinite(t).all()
