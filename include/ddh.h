@@ -137,6 +137,22 @@ int ddh_step_backward(ddh_state *s, const void *y_c64_dev, const float *r_prev, 
                       float *r_prev_bar, float *phi_prev_bar, float *grads, void *workspace,
                       size_t workspace_bytes);
 
+/* Allocation-free variant of ddh_step_backward (the paper has no counterpart; this is a
+ * library service).  Same arguments and results without the workspace: the scratch is a
+ * static device array inside the library, 769 KiB, present on every device that loads the
+ * library until the process exits, sized for grids up to 128 x 128 (larger grids return
+ * DDH_EINVAL with a message in ddh_last_cuda_error).  It is meant for callers that must not
+ * allocate device memory while they run, such as a real-time control loop where cudaMalloc's
+ * unbounded latency and possible device-wide synchronisation would break the frame deadline,
+ * or a host whose device memory is fully budgeted up front.  The call itself never calls
+ * cudaMalloc or cudaFree.  The first call on a device looks up the array's device address
+ * (with that device current) and caches it; make that first call before any stream capture.
+ * Every call shares the one array, and each call initialises what it reads; calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it, so serialise them. */
+int ddh_step_backward_noalloc(ddh_state *s, const void *y_c64_dev, const float *r_prev, const float *phi_prev,
+                              const float *trace, const float *r_new, const float *r_bar, const float *phi_bar,
+                              float *r_prev_bar, float *phi_prev_bar, float *grads);
+
 /* ---- streaming service: native continuous-batching scheduler -------------------------------
  * Sensors are admitted against a device-memory budget and keep their state resident; frames
  * are queued per sensor; a scheduler (a library thread after ddh_service_start, or each

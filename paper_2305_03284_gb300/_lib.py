@@ -84,6 +84,8 @@ _SIGS = {
     "ddh_backward_workspace_bytes": (c_size_t, [c_int]),
     "ddh_step_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_size_t]),
+    "ddh_step_backward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_void_p, c_void_p]),
     "ddh_fft_schedule_count": (c_int, [c_int]),
     "ddh_set_fft_schedule": (c_int, [c_int, c_int]),
     "ddh_get_fft_schedule": (c_int, [c_int]),

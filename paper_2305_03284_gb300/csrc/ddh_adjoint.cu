@@ -13,6 +13,7 @@
 // in a fixed order (deterministic).  The caller provides every buffer, workspace included.
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -420,4 +421,56 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
   e = cudaGetLastError();
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
   return DDH_OK;
+}
+
+// ---- allocation-free variant -----------------------------------------------------------------
+// Scratch for ddh_step_backward_noalloc: a file-scope device array, present on every device
+// that loads the library until the process exits.  It holds the backward workspace of grids up
+// to 128 x 128 (12 N^2 + 256 floats = 769 KiB).  Host code must not pass the array's name to a
+// kernel (on the host it is only a stand-in); its device address is looked up once per device.
+namespace {
+constexpr int kNoAllocMaxN = 128;
+constexpr size_t kNoAllocScratchFloats = 12 * static_cast<size_t>(kNoAllocMaxN) * kNoAllocMaxN + 256;
+static __device__ __align__(256) float g_backward_scratch[kNoAllocScratchFloats];
+std::mutex g_scratch_mu;
+void* g_scratch_addr[64] = {};
+}  // namespace
+
+extern "C" int ddh_step_backward_noalloc(ddh_state* s, const void* y, const float* r_prev, const float* phi_prev,
+                                         const float* trace, const float* r_new, const float* r_bar,
+                                         const float* phi_bar, float* r_prev_bar, float* phi_prev_bar,
+                                         float* grads) {
+  const ddh_params* prm = nullptr;
+  const void* tw = nullptr;
+  void* stream = nullptr;
+  int dev = 0;
+  if (ddh_internal_state_info(s, &prm, &tw, &stream, &dev) != DDH_OK) return DDH_EINVAL;
+  if (y == nullptr || r_prev == nullptr || phi_prev == nullptr || trace == nullptr || r_new == nullptr ||
+      r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr || phi_prev_bar == nullptr || grads == nullptr)
+    return DDH_EINVAL;
+  if (prm->n > kNoAllocMaxN) {
+    ddh_internal_set_error("ddh_step_backward_noalloc: grid larger than 128 x 128 (its static scratch is 769 KiB); "
+                           "use ddh_step_backward with a caller workspace");
+    return DDH_EINVAL;
+  }
+  if (prm->n_k != 1 || prm->phase_block != 1) return DDH_EINVAL;
+  if (reinterpret_cast<uintptr_t>(y) % 16 != 0 || reinterpret_cast<uintptr_t>(trace) % 8 != 0) return DDH_EINVAL;
+  if (dev < 0 || dev >= 64) return DDH_EINVAL;
+  cudaError_t e = cudaSetDevice(dev);
+  if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (g_scratch_addr[dev] == nullptr) {
+      // first call on this device (with it current): the array's device address
+      e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_backward_scratch);
+      if (e != cudaSuccess) {
+        g_scratch_addr[dev] = nullptr;
+        return ddh_internal_cuda_fail(e);
+      }
+    }
+    scratch = g_scratch_addr[dev];
+  }
+  return ddh_internal_step_backward(prm->n, prm, tw, stream, y, r_prev, phi_prev, trace, r_new, r_bar, phi_bar,
+                                    r_prev_bar, phi_prev_bar, grads, scratch);
 }

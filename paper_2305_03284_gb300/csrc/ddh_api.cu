@@ -267,6 +267,18 @@ constexpr uint32_t kMagic = 0x31484444u;  // "DDH1"
 
 int ddh_internal_cuda_fail(cudaError_t e) { return cuda_fail(e); }
 
+int ddh_internal_state_info(const ddh_state* s, const ddh_params** prm, const void** twiddle, void** stream,
+                            int* device) {
+  if (s == nullptr) return DDH_EINVAL;
+  *prm = &s->prm;
+  *twiddle = s->tw;
+  *stream = s->stream;
+  *device = s->device;
+  return DDH_OK;
+}
+
+void ddh_internal_set_error(const char* msg) { std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", msg); }
+
 extern "C" {
 
 int ddh_version(void) { return kVersion; }

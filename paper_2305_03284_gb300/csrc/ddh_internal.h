@@ -12,3 +12,10 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
                                const float* r_prev, const float* phi_prev, const float* trace, const float* r_new,
                                const float* r_bar, const float* phi_bar, float* r_prev_bar, float* phi_prev_bar,
                                float* grads, void* workspace);
+
+struct ddh_state;
+// Read-only view of a state's parameters, twiddle table, stream and device.
+int ddh_internal_state_info(const ddh_state* s, const ddh_params** prm, const void** twiddle, void** stream,
+                            int* device);
+// Set the library's last error message (returned by ddh_last_cuda_error).
+void ddh_internal_set_error(const char* msg);
