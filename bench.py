@@ -204,18 +204,19 @@ def run_reference(args):
 
 
 def batched_measure(ddh, peak_gbs, timesteps=200, ring=10, warm=5):
-    """Many independent streams of mixed grid size (the <= 256^2 part of the 64-stream mix):
+    """Many independent streams of mixed grid size (the 64-stream mix of 128^2, 256^2, 512^2):
     one launch per stream per time step ("plain") against one captured graph per time step."""
     import torch
     from synth import ddh_synth as sy
-    cfgs = [c for c in sy.config_batched(frames=timesteps) if c.n <= 256]
+    cfgs = sy.config_batched(frames=timesteps)
     rings = []
     for c in cfgs:
         ys, _ = sy.Stream(c).frames(ring)
         rings.append(torch.from_numpy(ys).cuda())
     stream = torch.cuda.Stream()
     out = {"workload": f"{len(cfgs)} independent streams: "
-                       f"{sum(c.n == 128 for c in cfgs)} x 128^2 + {sum(c.n == 256 for c in cfgs)} x 256^2, "
+                       f"{sum(c.n == 128 for c in cfgs)} x 128^2 + {sum(c.n == 256 for c in cfgs)} x 256^2 + "
+                       f"{sum(c.n == 512 for c in cfgs)} x 512^2, "
                        "pupil = grid/2, seeded D/r0 and wind per stream, 1 EM iteration per frame",
            "timesteps": timesteps, "frames_ring_per_stream": ring,
            "ring_bytes": int(sum(r.numel() * 8 for r in rings))}
@@ -279,7 +280,7 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
     import torch
     from paper_2305_03284_gb300 import serve
     from synth import ddh_synth as sy
-    cfgs = [c for c in sy.config_service(frames_total=total_frames) if c.n <= 256]
+    cfgs = sy.config_service(frames_total=total_frames)
     rates = np.array([c.rate_khz * 1e3 for c in cfgs])
     horizon = total_frames / rates.sum()
     rng = np.random.default_rng(seed)
@@ -295,7 +296,8 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
             k += 1
     arrivals.sort(key=lambda a: a[0])
     out = {"workload": f"{len(cfgs)} sensors ({sum(c.n == 128 for c in cfgs)} x 128^2, "
-                       f"{sum(c.n == 256 for c in cfgs)} x 256^2), Poisson arrivals at 0.5-5 kHz per sensor, "
+                       f"{sum(c.n == 256 for c in cfgs)} x 256^2, {sum(c.n == 512 for c in cfgs)} x 512^2), "
+                       "Poisson arrivals at 0.5-5 kHz per sensor, "
                        f"{len(arrivals)} frames over {horizon * 1e3:.1f} ms",
            "offered_frames_per_s": len(arrivals) / horizon}
 

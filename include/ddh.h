@@ -37,7 +37,7 @@ extern "C" {
 
 /* ---- parameters (Fig. 1 arguments lambda, alpha, N_k; Sec. 5.B values) -------------------- */
 typedef struct ddh_params {
-  int n;                /* grid side N: 32, 64, 128 or 256 */
+  int n;                /* grid side N: 32, 64, 128, 256 (cluster kernel) or 512 (L2-staged kernels) */
   float aperture_diam;  /* pupil diameter in px, 0 < d <= N */
   float lambda;         /* Eq. 3 weight of the back-projection term (paper: 0.45) */
   float alpha;          /* Eq. 3 scale of |A^H y|^2 (paper: 0.025) */
@@ -72,7 +72,7 @@ int ddh_init(ddh_state **out, const ddh_params *p, void *cuda_stream);
  * reported later (DDH_ENONFINITE) and leaves r and phi unchanged. */
 int ddh_step(ddh_state *s, const void *y_c64_dev);
 
-/* Same step, also writing the frame's intermediates into `trace_dev` (device, float32,
+/* Same step, also writing the frame's intermediates into `trace_dev` (N <= 256) (device, float32,
  * ddh_trace_floats(N) entries): b = A^H y (complex, N*N), mu (complex, N*N), z = F mu
  * (complex, N*N), r-init (N*N), s = E|g|^2 (N*N), then 8 scalars (mean re, mean im, scale,
  * t_x, t_y, 0, 0, 0).  Complex fields are interleaved; all images row-major. */
@@ -94,7 +94,7 @@ int ddh_reflectance(const ddh_state *s, float *out);
 int ddh_set_state(ddh_state *s, const float *r, const float *phi, int64_t frame_index);
 int64_t ddh_frame_index(const ddh_state *s);
 
-/* Peak Strehl ratio of the current phase estimate against `phi_true_dev` (N*N float32,
+/* Peak Strehl ratio (N <= 256) of the current phase estimate against `phi_true_dev` (N*N float32,
  * device): max |F^H(a exp(j(phi_true - phi)))|^2 / max |F^H a|^2 (Sec. 5.B).  Synchronous:
  * the value lands in *out.  Evaluation only, never part of a step. */
 int ddh_strehl(ddh_state *s, const float *phi_true_dev, float *out);
@@ -120,7 +120,7 @@ int ddh_batch_free(ddh_batch *b);
 
 /* ---- adjoint of one frame step (reverse mode through the EM iteration) -------------------
  * The paper defines no derivative; this is the chain rule through the step of ddh_step
- * (one EM iteration per frame, per-pixel phase: n_k 1 and phase_block 1, else DDH_EINVAL).
+ * (one EM iteration per frame, per-pixel phase, N <= 256: otherwise DDH_EINVAL).
  * Inputs (device, N*N float32 unless noted): the frame `y` (complex64, 16-byte aligned); the
  * state entering the frame (`r_prev`, `phi_prev`); the frame's ddh_step_trace output `trace`
  * recorded from that same state; the frame's output reflectance `r_new`; the gradients of a
@@ -203,7 +203,7 @@ int ddh_set_fft_schedule(int n, int schedule);
 int ddh_get_fft_schedule(int n);
 
 /* Unitary 2D DFT (Sec. 2, F) or its inverse (inverse != 0) of one N x N complex64 image,
- * device in/out (may alias), on `cuda_stream`.  N as for ddh_params. */
+ * device in/out (may alias), on `cuda_stream`.  N = 32 ... 256. */
 int ddh_fft2(const void *in_c64_dev, void *out_c64_dev, int n, int inverse, void *cuda_stream);
 
 /* Wait for the state's stream; return and clear any latched device error. */

@@ -26,6 +26,7 @@ struct ddh_state {
   unsigned* status;
   float2* ystage;
   float* scalar;
+  void* l2scratch;  // working images of the L2-staged kernels (512 x 512 grids only)
   const float2* tw;
   int64_t frame;
   int64_t ap_count;
@@ -47,19 +48,20 @@ int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
-int n_slot(int n) { return n == 32 ? 3 : n == 64 ? 0 : n == 128 ? 1 : 2; }
+bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
+bool cluster_n(int n) { return n != 512; }  // 512 uses the L2-staged kernels
+int n_slot(int n) { return n == 32 ? 3 : n == 64 ? 0 : n == 128 ? 1 : n == 256 ? 2 : 4; }
 
 std::mutex g_mu;
-bool g_configured[kMaxDevices][4] = {};
-float2* g_twiddle[kMaxDevices][4] = {};
-int g_schedule[kMaxDevices][4] = {};  // FFT radix schedule used for each grid size
+bool g_configured[kMaxDevices][5] = {};
+float2* g_twiddle[kMaxDevices][5] = {};
+int g_schedule[kMaxDevices][5] = {};  // FFT radix schedule used for each grid size
 
 // Library-owned side streams that let the grid-size groups of one batch run concurrently.
 struct SideStreams {
   bool ready = false;
-  cudaStream_t s[4] = {};
-  cudaEvent_t fork = nullptr, join[4] = {};
+  cudaStream_t s[5] = {};
+  cudaEvent_t fork = nullptr, join[5] = {};
 };
 SideStreams g_side[kMaxDevices];
 
@@ -67,7 +69,7 @@ int side_streams(int dev, SideStreams** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   SideStreams& ss = g_side[dev];
   if (!ss.ready) {
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 5; ++i) {
       DDH_CUDA(cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking));
       DDH_CUDA(cudaEventCreateWithFlags(&ss.join[i], cudaEventDisableTiming));
     }
@@ -85,8 +87,9 @@ int device_setup(int dev, int n, const float2** tw) {
   std::lock_guard<std::mutex> lock(g_mu);
   const int s = n_slot(n);
   if (!g_configured[dev][s]) {
-    int active = 0;
-    DDH_CUDA(ddh::configure(n, &active));
+    int active = 1;
+    if (cluster_n(n)) DDH_CUDA(ddh::configure(n, &active));
+    else DDH_CUDA(ddh::configure_l2(n));
     if (active < 1) {
       std::snprintf(g_cuda_err, sizeof(g_cuda_err), "no resident cluster of %d CTAs x %zu B shared memory", n / 16,
                     ddh::step_smem_bytes(n));
@@ -186,10 +189,30 @@ ddh::FrameArgs frame_args(ddh_state* s, const void* y, float* trace) {
   return f;
 }
 
+ddh::L2Stream l2_view(ddh_state* s, const void* y) {
+  ddh::L2Stream v = ddh::l2_stream_view(s->l2scratch, s->prm.n);
+  v.y = static_cast<const float2*>(y);
+  v.r = s->r;
+  v.phi = s->phi;
+  v.status = s->status;
+  return v;
+}
+
 int enqueue(ddh_state* s, const void* y, float* trace) {
   if (s == nullptr || y == nullptr) return DDH_EINVAL;
   if (reinterpret_cast<uintptr_t>(y) % 16 != 0) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(s->device));
+  if (!cluster_n(s->prm.n)) {
+    if (trace != nullptr) return DDH_EINVAL;  // no trace output on the L2-staged path
+    ddh::L2Batch lb{};
+    lb.prm[0] = s->kp;
+    lb.st[0] = l2_view(s, y);
+    lb.tw = s->tw;
+    lb.count = 1;
+    DDH_CUDA(ddh::launch_step_l2(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], lb, s->kp.n_k, s->stream));
+    s->frame += 1;
+    return DDH_OK;
+  }
   ddh::StepBatch b{};
   b.prm[0] = s->kp;
   b.fa[0] = frame_args(s, y, trace);
@@ -205,7 +228,7 @@ int enqueue(ddh_state* s, const void* y, float* trace) {
 // `main`.  Frames come from `ys[i]` or, when `ytab` is set, from ytab[i] on the device.
 int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2* const* ytab, int count,
                   cudaStream_t main, int dev) {
-  const int sizes[4] = {32, 64, 128, 256};
+  const int sizes[5] = {512, 32, 64, 128, 256};
   int groups = 0;
   for (int n : sizes)
     for (int i = 0; i < count; ++i)
@@ -230,6 +253,36 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
       DDH_CUDA(cudaStreamWaitEvent(st, ss->fork, 0));
     }
     const int sched = g_schedule[dev][n_slot(n)];
+    if (!cluster_n(n)) {
+      ddh::L2Batch lb{};
+      lb.ytab = ytab;
+      lb.count = 0;
+      for (int i = 0; i < count; ++i) {
+        ddh_state* s = states[i];
+        if (s->prm.n != n) continue;
+        if (lb.count > 0 && s->kp.n_k != lb.prm[0].n_k) {  // one EM-iteration count per launch
+          DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
+          lb.count = 0;
+        }
+        if (lb.count == 0) lb.ytab_base = i;
+        lb.prm[lb.count] = s->kp;
+        lb.st[lb.count] = l2_view(s, ys != nullptr ? ys[i] : nullptr);
+        lb.tw = s->tw;
+        ++lb.count;
+        const bool next_same = i + 1 < count && states[i + 1]->prm.n == n;
+        if (lb.count == ddh::kMaxBatchL2 || (ytab != nullptr && !next_same)) {
+          DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
+          lb.count = 0;
+        }
+      }
+      if (lb.count > 0) DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
+      if (ss != nullptr) {
+        DDH_CUDA(cudaEventRecord(ss->join[g], st));
+        DDH_CUDA(cudaStreamWaitEvent(main, ss->join[g], 0));
+      }
+      ++g;
+      continue;
+    }
     b.count = 0;
     for (int i = 0; i < count; ++i) {
       ddh_state* s = states[i];
@@ -342,6 +395,7 @@ int ddh_init(ddh_state** out, const ddh_params* p, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaMalloc(&s->status, 256);
   if (e == cudaSuccess) e = cudaMalloc(&s->ystage, 2 * img);
   if (e == cudaSuccess) e = cudaMalloc(&s->scalar, 256);
+  if (e == cudaSuccess && !cluster_n(p->n)) e = cudaMalloc(&s->l2scratch, ddh::l2_scratch_bytes(p->n));
   if (e == cudaSuccess) e = cudaMemsetAsync(s->r, 0, img, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->phi, 0, img, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->status, 0, 256, s->stream);
@@ -400,7 +454,7 @@ int ddh_set_state(ddh_state* s, const float* r, const float* phi, int64_t frame_
 int64_t ddh_frame_index(const ddh_state* s) { return s ? s->frame : -1; }
 
 int ddh_strehl(ddh_state* s, const float* phi_true_dev, float* out) {
-  if (s == nullptr || phi_true_dev == nullptr || out == nullptr) return DDH_EINVAL;
+  if (s == nullptr || phi_true_dev == nullptr || out == nullptr || !cluster_n(s->prm.n)) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(s->device));
   ddh::StrehlArgs a{};
   a.phi_est = s->phi;
@@ -539,7 +593,7 @@ int ddh_step_backward(ddh_state* s, const void* y, const float* r_prev, const fl
       r_new == nullptr || r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr ||
       phi_prev_bar == nullptr || grads == nullptr || workspace == nullptr)
     return DDH_EINVAL;
-  if (s->prm.n_k != 1 || s->prm.phase_block != 1) return DDH_EINVAL;
+  if (s->prm.n_k != 1 || s->prm.phase_block != 1 || !cluster_n(s->prm.n)) return DDH_EINVAL;
   if (workspace_bytes < ddh_backward_workspace_bytes(s->prm.n)) return DDH_EINVAL;
   if (reinterpret_cast<uintptr_t>(y) % 16 != 0 || reinterpret_cast<uintptr_t>(workspace) % 16 != 0 ||
       reinterpret_cast<uintptr_t>(trace) % 8 != 0)
@@ -569,7 +623,7 @@ int ddh_get_fft_schedule(int n) {
 }
 
 int ddh_fft2(const void* in, void* out, int n, int inverse, void* cuda_stream) {
-  if (in == nullptr || out == nullptr || !supported_n(n)) return DDH_EINVAL;
+  if (in == nullptr || out == nullptr || !supported_n(n) || !cluster_n(n)) return DDH_EINVAL;
   int dev = 0;
   DDH_CUDA(cudaGetDevice(&dev));
   const float2* tw = nullptr;
@@ -639,6 +693,7 @@ int ddh_free(ddh_state* s) {
   cudaFree(s->status);
   cudaFree(s->ystage);
   cudaFree(s->scalar);
+  cudaFree(s->l2scratch);
   delete s;
   return DDH_OK;
 }

@@ -48,6 +48,38 @@ struct StepBatch {
   int count;
 };
 
+// L2-staged path (grids beyond a cluster's shared memory): per-stream views of the global
+// scratch the stages exchange data through.
+constexpr int kMaxBatchL2 = 16;
+
+struct L2Stream {
+  const float2* y;
+  float* r;
+  float* phi;
+  unsigned* status;
+  float2* fa;     // row-major complex image (z rows for the phase step)
+  float2* fb;     // column-major complex image (back-projection columns)
+  float* r0;      // r-init (entry values of the ICD sweep)
+  float* s;       // E|g|^2
+  float* beta;    // 4 images of pair weights: E, S, SE, SW
+  float* part;    // row-block statistics, then the combined statistics
+  int* flag;      // frame dropped (non-finite or zero variance)
+};
+
+struct L2Batch {
+  KParams prm[kMaxBatchL2];
+  L2Stream st[kMaxBatchL2];
+  const float2* tw;
+  const float2* const* ytab;
+  int ytab_base;
+  int count;
+};
+
+size_t l2_scratch_bytes(int n);                    // per stream; 0 when n uses the cluster kernel
+L2Stream l2_stream_view(void* scratch, int n);     // y, r, phi, status left for the caller
+cudaError_t configure_l2(int n);
+cudaError_t launch_step_l2(int n, int schedule, const L2Batch& b, int n_k, cudaStream_t st);
+
 struct StrehlArgs {
   const float* phi_est;
   const float* phi_true;

@@ -21,6 +21,7 @@
 
 #include "../../include/ddh.h"
 #include "ddh_internal.h"
+#include "ddh_kernels.cuh"
 
 namespace {
 
@@ -200,9 +201,10 @@ int ddh_service_create(ddh_service** out, void* cuda_stream, size_t mem_budget_b
 }
 
 size_t ddh_state_bytes(int n) {
-  if (n != 32 && n != 64 && n != 128 && n != 256) return 0;
+  if (n != 32 && n != 64 && n != 128 && n != 256 && n != 512) return 0;
   const size_t img = sizeof(float) * static_cast<size_t>(n) * n;
-  return 4 * img + 512;  // r, phi, 2-image staging buffer, status and scalar words
+  // r, phi, 2-image staging buffer, status and scalar words (+ L2-staged working images)
+  return 4 * img + 512 + ddh::l2_scratch_bytes(n);
 }
 
 int ddh_service_admit(ddh_service* s, int sensor_id, const ddh_params* p) {

@@ -627,6 +627,7 @@ cudaError_t configure(int n, int* max_active) {
 
 int schedule_count(int n) {
   switch (n) {
+    case 512: return FftSchedules<512>::count;
     case 32: return FftSchedules<32>::count;
     case 64: return FftSchedules<64>::count;
     case 128: return FftSchedules<128>::count;

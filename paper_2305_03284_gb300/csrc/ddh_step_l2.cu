@@ -1,0 +1,410 @@
+// L2-staged frame step for grids whose working set exceeds a thread-block cluster's shared
+// memory (512 x 512: about 10 MB per stream).  The same stages as the cluster kernel, as a
+// sequence of batched kernels (blockIdx.y = stream of the batch) over per-stream global
+// scratch that stays resident in the 129 MB L2 between stages:
+//   s1 row statistics (Normalize, Eq. 4) and tip/tilt sums        (16 rows per block)
+//   s2 combine; RemoveTipTilt, prologue a e^{-j phi'} y~, row IFFT; transposed store
+//   s3 column IFFT, r-init (Eq. 3) + E-step, column FFT of mu; transposed store (16 cols/block)
+//   s4 row FFT and phase M-step (tile sums when the phase is tiled)
+//   s5 surrogate weights of the E, S, SE, SW pairs; s6 one ICD colour (launched 4 times)
+// Each 1-D DFT is the warp-per-row shared-memory Stockham FFT of the cluster kernel; the
+// transposes go through a 16-row shared-memory tile so that global stores are 128-byte runs.
+#include "ddh_device.cuh"
+#include "ddh_kernels.cuh"
+
+namespace ddh {
+
+namespace {
+
+constexpr int kT = 16;  // rows (or columns) per block
+
+__device__ __forceinline__ bool frame_dropped(const L2Stream& S) { return *S.flag != 0; }
+
+// ---- s1: per-row statistics and tip/tilt partial sums ---------------------------------------
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_l2_stats(const __grid_constant__ L2Batch b) {
+  const L2Stream& S = b.st[blockIdx.y];
+  const KParams& P = b.prm[blockIdx.y];
+  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
+  __shared__ float red[16][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rho = kT * blockIdx.x + warp;
+  constexpr int PER = N / 32;
+  float2 v[PER];
+  float sre = 0.f, sim = 0.f;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    v[j] = y[static_cast<size_t>(rho) * N + lane + 32 * j];
+    sre += v[j].x;
+    sim += v[j].y;
+  }
+  sre = warp_sum(sre);
+  sim = warp_sum(sim);
+  const float invN = 1.f / static_cast<float>(N);
+  const float2 m = make_float2(sre * invN, sim * invN);
+  float q = 0.f;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) q += c_abs2(c_sub(v[j], m));
+  q = warp_sum(q);
+  float txs = 0.f, txc = 0.f, tys = 0.f, tyc = 0.f;
+  if (P.tilt_mode) {
+    const float* pr = S.phi + static_cast<size_t>(rho) * N;
+    const int dy2 = ap_dist2(rho, N);
+    const int dy2n = rho + 1 < N ? ap_dist2(rho + 1, N) : (1 << 30);
+    for (int x = lane; x < N; x += 32) {
+      const int dx2 = ap_dist2(x, N);
+      if (dx2 + dy2 > P.ap_lim) continue;
+      if (x + 1 < N && ap_dist2(x + 1, N) + dy2 <= P.ap_lim) { txs += wrap_pi(pr[x + 1] - pr[x]); txc += 1.f; }
+      if (dx2 + dy2n <= P.ap_lim) { tys += wrap_pi(pr[x + N] - pr[x]); tyc += 1.f; }
+    }
+    txs = warp_sum(txs); txc = warp_sum(txc); tys = warp_sum(tys); tyc = warp_sum(tyc);
+  }
+  if (lane == 0) {
+    red[warp][0] = m.x; red[warp][1] = m.y; red[warp][2] = q;
+    red[warp][3] = txs; red[warp][4] = txc; red[warp][5] = tys; red[warp][6] = tyc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float n_a = static_cast<float>(N), q_a = red[0][2];
+    float2 m_a = make_float2(red[0][0], red[0][1]);
+    float t0 = red[0][3], t1 = red[0][4], t2 = red[0][5], t3 = red[0][6];
+    for (int w = 1; w < kT; ++w) {
+      const float n_b = static_cast<float>(N);
+      const float nn = n_a + n_b;
+      const float2 d = make_float2(red[w][0] - m_a.x, red[w][1] - m_a.y);
+      const float f = n_b / nn;
+      m_a = make_float2(fmaf(d.x, f, m_a.x), fmaf(d.y, f, m_a.y));
+      q_a = q_a + red[w][2] + c_abs2(d) * (n_a * f);
+      n_a = nn;
+      t0 += red[w][3]; t1 += red[w][4]; t2 += red[w][5]; t3 += red[w][6];
+    }
+    float* o = S.part + 8 * blockIdx.x;
+    o[0] = m_a.x; o[1] = m_a.y; o[2] = q_a; o[3] = t0; o[4] = t1; o[5] = t2; o[6] = t3; o[7] = 0.f;
+    if (blockIdx.x == 0) *S.flag = 0;
+  }
+}
+
+// combine the row-block partials in rank order (identical in every block)
+template <int N>
+__device__ void l2_combine(const L2Stream& S, const KParams& P, float* g) {
+  constexpr int B = N / kT;
+  const float nb = static_cast<float>(kT * N);
+  float n_a = nb, q_a = S.part[2];
+  float2 m_a = make_float2(S.part[0], S.part[1]);
+  float t0 = S.part[3], t1 = S.part[4], t2 = S.part[5], t3 = S.part[6];
+  for (int k = 1; k < B; ++k) {
+    const float* o = S.part + 8 * k;
+    const float nn = n_a + nb;
+    const float2 d = make_float2(o[0] - m_a.x, o[1] - m_a.y);
+    const float f = nb / nn;
+    m_a = make_float2(fmaf(d.x, f, m_a.x), fmaf(d.y, f, m_a.y));
+    q_a = q_a + o[2] + c_abs2(d) * (n_a * f);
+    n_a = nn;
+    t0 += o[3]; t1 += o[4]; t2 += o[5]; t3 += o[6];
+  }
+  const float scale = sqrtf(static_cast<float>(N) * static_cast<float>(N) / q_a);
+  const bool finite = isfinite(m_a.x) && isfinite(m_a.y) && isfinite(q_a) && q_a > 0.f && isfinite(scale);
+  g[0] = m_a.x;
+  g[1] = m_a.y;
+  g[2] = scale;
+  g[3] = (P.tilt_mode && t1 > 0.f) ? t0 / t1 : 0.f;
+  g[4] = (P.tilt_mode && t3 > 0.f) ? t2 / t3 : 0.f;
+  g[5] = finite ? 0.f : 1.f;
+}
+
+// ---- s2: prologue and row IFFT of the pupil rows; transposed store into fb ------------------
+template <int N, int V>
+__global__ void __launch_bounds__(kThreads) k_l2_rows_inv(const __grid_constant__ L2Batch b, int first) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const L2Stream& S = b.st[blockIdx.y];
+  const KParams& P = b.prm[blockIdx.y];
+  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float2* rows = tw + N;  // kT rows x (N + 1)
+  __shared__ float g[8];
+  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = b.tw[i];
+  if (threadIdx.x == 0) {
+    if (first) {
+      l2_combine<N>(S, P, g);
+      if (blockIdx.x == 0) {
+        float* st = S.part + 8 * (N / kT);  // combined statistics for the later stages
+        for (int k = 0; k < 6; ++k) st[k] = g[k];
+        if (g[5] != 0.f) {
+          *S.flag = 1;
+          if (S.status != nullptr) atomicOr(S.status, kStatusNonFinite);
+        }
+      }
+    } else {
+      const float* st = S.part + 8 * (N / kT);
+      for (int k = 0; k < 6; ++k) g[k] = st[k];
+    }
+  }
+  __syncthreads();
+  if (g[5] != 0.f) return;
+  const float2 ymean = make_float2(g[0], g[1]);
+  const float scale = g[2], tx = g[3], ty = g[4];
+  const float cc = 0.5f * static_cast<float>(N - 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rho = kT * blockIdx.x + warp;
+  const int dy2 = ap_dist2(rho, N);
+  float2* rb = rows + warp * (N + 1);
+  float* pr = S.phi + static_cast<size_t>(rho) * N;
+  if (dy2 <= P.ap_lim) {
+    const float tyr = ty * (static_cast<float>(rho) - cc);
+    for (int x = lane; x < N; x += 32) {
+      float2 u = make_float2(0.f, 0.f);
+      float ph = 0.f;
+      if (ap_dist2(x, N) + dy2 <= P.ap_lim) {
+        ph = pr[x];
+        if (first && P.tilt_mode) ph = wrap_pi(ph - fmaf(tx, static_cast<float>(x) - cc, tyr));
+        const float2 yt = c_scale(c_sub(y[static_cast<size_t>(rho) * N + x], ymean), scale);
+        float sn, cs;
+        __sincosf(ph, &sn, &cs);
+        u = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
+      }
+      pr[x] = ph;  // the state keeps phi' (tip/tilt removed) until the phase step
+      rb[x] = u;
+    }
+    __syncwarp();
+    fft_row<N, +1, V>(rb, tw, lane);
+  } else {
+    for (int x = lane; x < N; x += 32) {
+      rb[x] = make_float2(0.f, 0.f);
+      pr[x] = 0.f;
+    }
+  }
+  __syncthreads();
+  // fb is column-major: fb[x N + rho]; 16 threads write the 16 rows of one column
+  for (int i = threadIdx.x; i < kT * N; i += kThreads) {
+    const int x = i / kT, r = i - x * kT;
+    S.fb[static_cast<size_t>(x) * N + kT * blockIdx.x + r] = rows[r * (N + 1) + x];
+  }
+}
+
+// ---- s3: column IFFT, r-init + E-step, column FFT of mu; transposed store into fa ----------
+template <int N, int V>
+__global__ void __launch_bounds__(kThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const L2Stream& S = b.st[blockIdx.y];
+  const KParams& P = b.prm[blockIdx.y];
+  if (frame_dropped(S)) return;
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float2* cols = tw + N;                                        // kT columns x (N + 1)
+  float* rt = reinterpret_cast<float*>(cols + kT * (N + 1));    // kT x (N + 1): r, then r-init
+  float* stile = rt + kT * (N + 1);                             // kT x (N + 1): s
+  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = b.tw[i];
+  const int x0 = kT * blockIdx.x;
+  for (int i = threadIdx.x; i < kT * N; i += kThreads) {
+    const int c = i / N, rho = i - c * N;
+    cols[c * (N + 1) + rho] = S.fb[static_cast<size_t>(x0 + c) * N + rho];
+  }
+  for (int i = threadIdx.x; i < kT * N; i += kThreads) {  // coalesced 64-byte row segments
+    const int rho = i / kT, c = i - rho * kT;
+    rt[c * (N + 1) + rho] = S.r[static_cast<size_t>(rho) * N + x0 + c];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* cb = cols + warp * (N + 1);
+  float* rc = rt + warp * (N + 1);
+  float* sc = stile + warp * (N + 1);
+  fft_row<N, +1, V>(cb, tw, lane);
+  const float invN = 1.f / static_cast<float>(N);
+  for (int rho = lane; rho < N; rho += 32) {
+    const float2 bb = c_scale(cb[rho], invN);
+    const float rp = rc[rho];
+    const float ri = first ? fmaxf(fmaf(P.lam1, rp, P.lam_alpha * c_abs2(bb)), P.r_floor) : rp;
+    const float w = ri / (ri + P.noise_var);
+    const float2 mu = c_scale(bb, w);
+    cb[rho] = mu;
+    rc[rho] = ri;
+    sc[rho] = fmaf(P.noise_var, w, c_abs2(mu));
+  }
+  __syncwarp();
+  fft_row<N, -1, V>(cb, tw, lane);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kT * N; i += kThreads) {
+    const int rho = i / kT, c = i - rho * kT;
+    const size_t gi = static_cast<size_t>(rho) * N + x0 + c;
+    const float ri = rt[c * (N + 1) + rho];
+    S.r0[gi] = ri;
+    S.r[gi] = ri;  // the ICD sweep starts from r-init
+    S.s[gi] = stile[c * (N + 1) + rho];
+    if (ap_dist2(rho, N) <= P.ap_lim) S.fa[gi] = cols[c * (N + 1) + rho];
+  }
+}
+
+// ---- s4: row FFT of mu and phase M-step ------------------------------------------------------
+template <int N, int V>
+__global__ void __launch_bounds__(kThreads) k_l2_rows_fwd(const __grid_constant__ L2Batch b) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const L2Stream& S = b.st[blockIdx.y];
+  const KParams& P = b.prm[blockIdx.y];
+  if (frame_dropped(S)) return;
+  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
+  float2* tw = reinterpret_cast<float2*>(smem);
+  float2* rows = tw + N;
+  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = b.tw[i];
+  const float* st = S.part + 8 * (N / kT);
+  const float2 ymean = make_float2(st[0], st[1]);
+  const float scale = st[2];
+  const int gs = P.g_shift, G = 1 << gs;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rho = kT * blockIdx.x + warp;
+  const int dy2 = ap_dist2(rho, N);
+  const bool row_ap = dy2 <= P.ap_lim;
+  float2* rb = rows + warp * (N + 1);
+  if (row_ap)
+    for (int x = lane; x < N; x += 32) rb[x] = S.fa[static_cast<size_t>(rho) * N + x];
+  __syncthreads();
+  if (row_ap) fft_row<N, -1, V>(rb, tw, lane);
+  const float invN = 1.f / static_cast<float>(N);
+  for (int x = lane; x < N; x += 32) {
+    float2 v = make_float2(0.f, 0.f);
+    if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
+      const float2 z = c_scale(rb[x], invN);
+      const float2 yt = c_scale(c_sub(y[static_cast<size_t>(rho) * N + x], ymean), scale);
+      v = make_float2(fmaf(yt.x, z.x, yt.y * z.y), fmaf(yt.y, z.x, -yt.x * z.y));
+    }
+    for (int o = 1; o < G; o <<= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    rb[x] = v;
+  }
+  __syncthreads();
+  const int l0 = warp & ~(G - 1);
+  float* pr = S.phi + static_cast<size_t>(rho) * N;
+  for (int x = lane; x < N; x += 32) {
+    if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
+      float2 v = rows[l0 * (N + 1) + x];
+      for (int j = 1; j < G; ++j) v = c_add(v, rows[(l0 + j) * (N + 1) + x]);
+      if (v.x != 0.f || v.y != 0.f) pr[x] = atan2f(v.y, v.x);  // else phi' is kept
+    }
+  }
+}
+
+// ---- s5: surrogate pair weights at the sweep's entry values ---------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) k_l2_weights(const __grid_constant__ L2Batch b) {
+  const L2Stream& S = b.st[blockIdx.y];
+  const KParams& P = b.prm[blockIdx.y];
+  if (frame_dropped(S)) return;
+  constexpr int M = N * N;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int rho = i / N, x = i - rho * N;
+    const float a = S.r0[i];
+    const bool rt = x + 1 < N, dn = rho + 1 < N, lf = x > 0;
+    auto wgt = [&](float d) { return prior_weight_fast(d, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p); };
+    S.beta[i] = rt ? kBnn * wgt(a - S.r0[i + 1]) : 0.f;
+    S.beta[M + i] = dn ? kBnn * wgt(a - S.r0[i + N]) : 0.f;
+    S.beta[2 * M + i] = (rt && dn) ? kBdiag * wgt(a - S.r0[i + N + 1]) : 0.f;
+    S.beta[3 * M + i] = (lf && dn) ? kBdiag * wgt(a - S.r0[i + N - 1]) : 0.f;
+  }
+}
+
+// ---- s6: one ICD colour ---------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Batch b, int c) {
+  const L2Stream& S = b.st[blockIdx.y];
+  const KParams& P = b.prm[blockIdx.y];
+  if (frame_dropped(S)) return;
+  constexpr int M = N * N;
+  const int cx = c & 1, cy = c >> 1;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M / 4; k += gridDim.x * blockDim.x) {
+    const int rho = cy + 2 * (k / (N / 2)), x = cx + 2 * (k % (N / 2));
+    const int i = rho * N + x;
+    const bool up = rho > 0, dn = rho + 1 < N, lf = x > 0, rt = x + 1 < N;
+    const float* bE = S.beta;
+    const float* bS = S.beta + M;
+    const float* bSE = S.beta + 2 * M;
+    const float* bSW = S.beta + 3 * M;
+    const float* r = S.r;
+    const float wE = bE[i], wS = bS[i], wSE = bSE[i], wSW = bSW[i];
+    const float wW = lf ? bE[i - 1] : 0.f;
+    const float wN = up ? bS[i - N] : 0.f;
+    const float wNW = (up && lf) ? bSE[i - N - 1] : 0.f;
+    const float wNE = (up && rt) ? bSW[i - N + 1] : 0.f;
+    const float rW = lf ? r[i - 1] : 0.f, rE = rt ? r[i + 1] : 0.f;
+    const float rN = up ? r[i - N] : 0.f, rSo = dn ? r[i + N] : 0.f;
+    const float rNW = (up && lf) ? r[i - N - 1] : 0.f, rNE = (up && rt) ? r[i - N + 1] : 0.f;
+    const float rSW = (dn && lf) ? r[i + N - 1] : 0.f, rSE = (dn && rt) ? r[i + N + 1] : 0.f;
+    const float Wsum = ((wN + wS) + (wW + wE)) + ((wNW + wNE) + (wSW + wSE));
+    float Csum = wN * rN;
+    Csum = fmaf(wS, rSo, Csum);
+    Csum = fmaf(wW, rW, Csum);
+    Csum = fmaf(wE, rE, Csum);
+    Csum = fmaf(wNW, rNW, Csum);
+    Csum = fmaf(wNE, rNE, Csum);
+    Csum = fmaf(wSW, rSW, Csum);
+    Csum = fmaf(wSE, rSE, Csum);
+    S.r[i] = fmaxf(icd_root_from(Wsum, Csum, S.s[i], S.r0[i]), P.r_floor);
+  }
+}
+
+template <int N>
+constexpr size_t rows_smem() { return sizeof(float2) * (N + kT * (N + 1)); }
+template <int N>
+constexpr size_t cols_smem() { return sizeof(float2) * (N + kT * (N + 1)) + 2 * sizeof(float) * kT * (N + 1); }
+
+template <int N, int V>
+cudaError_t l2_step(const L2Batch& b, int n_k, cudaStream_t st) {
+  const dim3 grid(N / kT, b.count), blk(kThreads);
+  const dim3 pgrid(64, b.count);
+  k_l2_stats<N><<<grid, blk, 0, st>>>(b);
+  for (int it = 0; it < n_k; ++it) {
+    k_l2_rows_inv<N, V><<<grid, blk, rows_smem<N>(), st>>>(b, it == 0 ? 1 : 0);
+    k_l2_cols<N, V><<<grid, blk, cols_smem<N>(), st>>>(b, it == 0 ? 1 : 0);
+    k_l2_rows_fwd<N, V><<<grid, blk, rows_smem<N>(), st>>>(b);
+    k_l2_weights<N><<<pgrid, 256, 0, st>>>(b);
+    for (int c = 0; c < 4; ++c) k_l2_colour<N><<<pgrid, 256, 0, st>>>(b, c);
+  }
+  return cudaGetLastError();
+}
+
+template <int N, int V>
+cudaError_t l2_configure() {
+  cudaError_t e = cudaFuncSetAttribute(k_l2_rows_inv<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(rows_smem<N>()));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_l2_cols<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(cols_smem<N>()));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_l2_rows_fwd<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(rows_smem<N>()));
+  return e;
+}
+
+}  // namespace
+
+size_t l2_scratch_bytes(int n) {
+  if (n != 512) return 0;
+  const size_t M = static_cast<size_t>(n) * n;
+  // fa, fb (complex), r-init, s, 4 weight images, row-block partials + combined stats, flag
+  return 2 * M * sizeof(float2) + 6 * M * sizeof(float) + (8 * (n / kT) + 16) * sizeof(float) + 256;
+}
+
+L2Stream l2_stream_view(void* scratch, int n) {
+  const size_t M = static_cast<size_t>(n) * n;
+  char* p = static_cast<char*>(scratch);
+  L2Stream s{};
+  s.fa = reinterpret_cast<float2*>(p);
+  s.fb = s.fa + M;
+  s.r0 = reinterpret_cast<float*>(s.fb + M);
+  s.s = s.r0 + M;
+  s.beta = s.s + M;
+  s.part = s.beta + 4 * M;
+  s.flag = reinterpret_cast<int*>(s.part + 8 * (n / kT) + 16);
+  return s;
+}
+
+cudaError_t configure_l2(int n) {
+  if (n != 512) return cudaErrorInvalidValue;
+  return l2_configure<512, 0>();
+}
+
+cudaError_t launch_step_l2(int n, int schedule, const L2Batch& b, int n_k, cudaStream_t st) {
+  if (n != 512 || schedule != 0) return cudaErrorInvalidValue;
+  return l2_step<512, 0>(b, n_k, st);
+}
+
+}  // namespace ddh

@@ -23,8 +23,8 @@ def ddh():
 def _cfgs():
     b = sy.config_batched(4)
     # interleaved grid sizes, so that equal sizes are not adjacent
-    return [sy.config_single_64(4), b[0], sy.config_single_256(4), b[1], sy.config_single_64(4).__class__(
-        **{**sy.config_single_64(4).__dict__, "stream_id": 7}), b[33]]
+    return [sy.config_single_64(4), b[0], sy.config_single_256(4), b[57], b[1], sy.config_single_64(4).__class__(
+        **{**sy.config_single_64(4).__dict__, "stream_id": 7}), b[33], b[58]]
 
 
 def _data(ddh, cfgs, frames):

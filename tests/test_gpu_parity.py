@@ -354,3 +354,33 @@ def test_argument_errors(ddh):
         q = ddh.default_params(64, 32.0, 10.0, **bad)
         with pytest.raises(ddh.DdhError):
             ddh.Stream(q)
+
+
+# -------------------------------------------------------------- 512 x 512 (L2-staged path)
+@pytest.mark.parametrize("over", [{}, {"phase_block": 2}, {"n_k": 2}])
+def test_parity_512_l2_staged(ddh, over):
+    cfg = sy.config_batched(frames=3)[56]  # a 512^2 stream of the 64-stream workload
+    assert cfg.n == 512
+    st, ys, ph, p = make(ddh, cfg, 3 if not over else 2, **over)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    gphi, gr, _ = _run_free(ddh, p, ys, ph, with_strehl=False)
+    ophi, orr, _ = _run_oracle(prm, ys, ph)
+    assert rel_l2_phase(gphi[-1], ophi[-1], a) < TOL
+    assert rel_l2(gr[-1], orr[-1]) < TOL
+    assert np.all(gphi[-1][~a] == 0.0)
+
+
+def test_512_rejects_nonfinite_frame(ddh):
+    cfg = sy.config_batched(frames=2)[56]
+    st, ys, ph, p = make(ddh, cfg, 2)
+    s = ddh.Stream(p)
+    s.step(cu(ys[0]))
+    s.sync()
+    phi0 = s.phase().clone()
+    bad = ys[1].copy()
+    bad[3, 5] = np.inf
+    s.step(cu(bad))
+    with pytest.raises(ddh.DdhError):
+        s.sync()
+    assert torch.equal(s.phase(), phi0)
