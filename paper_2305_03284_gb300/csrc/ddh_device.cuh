@@ -80,10 +80,15 @@ __device__ __forceinline__ void dft_r(float2* x) {
   else dft8<S>(x);
 }
 
+// Shared-memory placement of element i of a row: the low four bits are XORed with the next
+// four, so that the strided stores of the early Stockham passes (stride 4 or 32 elements)
+// spread over all banks.  Every reader and writer of a row buffer uses this placement.
+__device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15); }
+
 // ------------------------------------------------------------------------------- row FFT
-// One Stockham radix-R pass over a length-N row owned by one warp.  Group i (0 <= i < N/R)
-// reads x_m = row[i + m N/R], multiplies by exp(S 2 pi i m k /(P R)) with k = i mod P, takes
-// the R-point DFT and writes y_q to row[(i - k) R + k + q P].  All reads of the warp finish
+// One Stockham radix-R pass over a length-N row owned by one warp (element e at row[swz(e)]).
+// Group i (0 <= i < N/R) reads x_m = element i + m N/R, multiplies by exp(S 2 pi i m k /(P R)) with k = i mod P, takes
+// the R-point DFT and writes y_q to element (i - k) R + k + q P.  All reads of the warp finish
 // before any write, so the pass runs in place.  `tw[t] = exp(-2 pi i t / N)`.
 template <int N, int R, int P, int S>
 __device__ __forceinline__ void stockham_pass(float2* row, const float2* __restrict__ tw, int lane) {
@@ -95,7 +100,7 @@ __device__ __forceinline__ void stockham_pass(float2* row, const float2* __restr
     const int i = lane + 32 * g;
     if (G % 32 == 0 || i < G) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) v[g][m] = row[i + m * G];
+      for (int m = 0; m < R; ++m) v[g][m] = row[swz(i + m * G)];
     }
   }
   __syncwarp();
@@ -115,7 +120,7 @@ __device__ __forceinline__ void stockham_pass(float2* row, const float2* __restr
       dft_r<R, S>(v[g]);
       const int j = (i - k) * R + k;
 #pragma unroll
-      for (int q = 0; q < R; ++q) row[j + q * P] = v[g][q];
+      for (int q = 0; q < R; ++q) row[swz(j + q * P)] = v[g][q];
     }
   }
   __syncwarp();
@@ -228,14 +233,27 @@ __device__ __forceinline__ float prior_weight(float delta, float w0, float inv_t
   return w0 * (q_over_p + u) / (d * d);
 }
 
-// Same weight with the power taken through the hardware log2 / exp2 (relative error of the
-// weight a few 1e-7, far inside the FP32-vs-FP64 tolerance of the step).
+// Hardware approximations (PTX ex2.approx / rcp.approx: a few ulp) used where the result
+// feeds a quantity compared against FP64 at 2e-5.
+__device__ __forceinline__ float hw_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float hw_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Same weight with the power taken through the hardware log2 / exp2 and one reciprocal
+// (relative error of the weight a few 1e-7, far inside the step's FP32-vs-FP64 tolerance).
 __device__ __forceinline__ float prior_weight_fast(float delta, float w0, float inv_tsig, float q_minus_p,
                                                    float q_over_p) {
   const float t = fabsf(delta) * inv_tsig;
-  const float u = t > 0.f ? exp2f(q_minus_p * __log2f(t)) : 0.f;
+  const float u = t > 0.f ? hw_exp2(q_minus_p * __log2f(t)) : 0.f;
   const float d = 1.f + u;
-  return w0 * __fdividef(q_over_p + u, d * d);
+  return (w0 * (q_over_p + u)) * hw_rcp(d * d);
 }
 
 // ICD pixel update: the positive real root of f(r) = W r^3 - C r^2 + r - s minimising

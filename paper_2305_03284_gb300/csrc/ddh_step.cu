@@ -34,12 +34,13 @@ struct StepLayout {
   static constexpr size_t phib = al(ybuf + size_t(R) * N * 8);
   static constexpr size_t phin = al(phib + size_t(R) * N * 4);  // phi of row rho + 1
   static constexpr size_t rS = al(phin + size_t(R) * N * 4);
-  static constexpr size_t r0S = al(rS + size_t(W) * CS * 4);
-  static constexpr size_t sS = al(r0S + size_t(W) * CS * 4);
-  static constexpr size_t halo = al(sS + size_t(W) * CS * 4);  // 3 x N halo-pair weights
+  static constexpr size_t sS = al(rS + size_t(W) * CS * 4);
+  static constexpr size_t hl = al(sS + size_t(W) * CS * 4);    // r of the left slab's last column
+  static constexpr size_t hr = al(hl + size_t(N) * 4);         // r of the right slab's first column
+  static constexpr size_t halo = al(hr + size_t(N) * 4);       // 3 x N halo-pair weights
   static constexpr size_t red = al(halo + size_t(3) * N * 4);  // 16 warps x 8 floats
-  static constexpr size_t pub = al(red + 16 * 8 * 4);         // 8 published floats
-  static constexpr size_t glob = al(pub + 8 * 4);             // 8 combined floats
+  static constexpr size_t pub = al(red + 16 * 8 * 4);         // 8 floats from each of the C CTAs
+  static constexpr size_t glob = al(pub + 16 * 8 * 4);        // 8 combined floats
   static constexpr size_t mbar = al(glob + 8 * 4);
   static constexpr size_t total = al(mbar + 16);
 };
@@ -88,8 +89,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   float* phib = reinterpret_cast<float*>(smem + L::phib);
   float* phin = reinterpret_cast<float*>(smem + L::phin);
   float* rS = reinterpret_cast<float*>(smem + L::rS);
-  float* r0S = reinterpret_cast<float*>(smem + L::r0S);
   float* sS = reinterpret_cast<float*>(smem + L::sS);
+  float* hl = reinterpret_cast<float*>(smem + L::hl);
+  float* hr = reinterpret_cast<float*>(smem + L::hr);
   float* halo = reinterpret_cast<float*>(smem + L::halo);
   float* red = reinterpret_cast<float*>(smem + L::red);
   float* pub = reinterpret_cast<float*>(smem + L::pub);
@@ -186,8 +188,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       chan_combine(n_a, m_a, q_a, static_cast<float>(N), make_float2(o[0], o[1]), o[2]);
       t0 += o[3]; t1 += o[4]; t2 += o[5]; t3 += o[6]; bad += o[7];
     }
-    pub[0] = m_a.x; pub[1] = m_a.y; pub[2] = q_a; pub[3] = t0; pub[4] = t1; pub[5] = t2; pub[6] = t3;
-    pub[7] = bad;
+    red[0] = m_a.x; red[1] = m_a.y; red[2] = q_a; red[3] = t0; red[4] = t1; red[5] = t2; red[6] = t3;
+    red[7] = bad;
+  }
+  __syncthreads();
+  // push this CTA's partials into slot k of every CTA of the cluster (read locally after B1)
+  if (tid < C) {
+    const float4* srcv = reinterpret_cast<const float4*>(red);
+    float4* dst = reinterpret_cast<float4*>(cluster.map_shared_rank(pub, tid) + 8 * k);
+    dst[0] = srcv[0];
+    dst[1] = srcv[1];
   }
   cluster.sync();  // B1
   if (warp == 0) {
@@ -197,9 +207,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
 #pragma unroll
     for (int j = 0; j < 8; ++j) o[j] = 0.f;
     if (lane < C) {
-      const float* src = cluster.map_shared_rank(pub, lane);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) o[j] = src[j];
+      const float4* src = reinterpret_cast<const float4*>(pub + 8 * lane);
+      const float4 a = src[0], b = src[1];
+      o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+      o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
     }
     const float nb = static_cast<float>(R * N);
     float n_a = nb, q_a = 0.f;
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       // the scatter below writes only aperture rows of colbuf; clear the others again
       for (int i = tid; i < W * N; i += kThreads) {
         const int cl = i / N, rho = i - cl * N;
-        if (ap_dist2(rho, N) > P.ap_lim) colbuf[cl * CS + rho] = make_float2(0.f, 0.f);
+        if (ap_dist2(rho, N) > P.ap_lim) colbuf[cl * CS + swz(rho)] = make_float2(0.f, 0.f);
       }
     }
     {
@@ -271,9 +282,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
             const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
             float sn, cs;
             __sincosf(ph, &sn, &cs);  // |ph| <= pi: absolute error ~ 5e-7
-            rb[x] = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
+            rb[swz(x)] = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
           } else {
-            rb[x] = make_float2(0.f, 0.f);
+            rb[swz(x)] = make_float2(0.f, 0.f);
             pr[x] = 0.f;
           }
         }
@@ -281,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
         fft_row<N, +1, V>(rb, tw, lane);
         for (int x = lane; x < N; x += 32) {
           float2* dst = cluster.map_shared_rank(colbuf, x / W);
-          dst[(x % W) * CS + rho] = rb[x];
+          dst[(x % W) * CS + swz(rho)] = rb[swz(x)];
         }
       } else {
         for (int x = lane; x < N; x += 32) pr[x] = 0.f;
@@ -294,16 +305,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       float2* cb = colbuf + cl * CS;
       fft_row<N, +1, V>(cb, tw, lane);
       for (int rho = lane; rho < N; rho += 32) {
-        const float2 b = c_scale(cb[rho], invN);
+        const float2 b = c_scale(cb[swz(rho)], invN);
         const float rp = rS[cl * CS + rho];
         const float ri = first ? fmaxf(fmaf(P.lam1, rp, P.lam_alpha * c_abs2(b)), P.r_floor) : rp;
-        const float wgt = ri / (ri + P.noise_var);
+        const float wgt = ri * hw_rcp(ri + P.noise_var);
         const float2 mu = c_scale(b, wgt);
         const float s = fmaf(P.noise_var, wgt, c_abs2(mu));
-        cb[rho] = mu;
+        cb[swz(rho)] = mu;
         rS[cl * CS + rho] = ri;
-        r0S[cl * CS + rho] = ri;
         sS[cl * CS + rho] = s;
+        // slab-edge values go to the neighbouring slabs' halo columns (read after B3)
+        if (cl == 0 && k > 0) cluster.map_shared_rank(hr, k - 1)[rho] = ri;
+        if (cl == W - 1 && k < C - 1) cluster.map_shared_rank(hl, k + 1)[rho] = ri;
         if (trace != nullptr) {
           const size_t gi = static_cast<size_t>(rho) * N + W * k + cl;
           const size_t M = static_cast<size_t>(N) * N;
@@ -318,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       for (int rho = lane; rho < N; rho += 32) {
         if (ap_dist2(rho, N) <= P.ap_lim) {
           float2* dst = cluster.map_shared_rank(rowbuf, row_owner<C>(rho, P.g_shift));
-          dst[row_local<C>(rho, P.g_shift) * CS + W * k + cl] = cb[rho];
+          dst[row_local<C>(rho, P.g_shift) * CS + swz(W * k + cl)] = cb[swz(rho)];
         }
       }
     }
@@ -336,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       for (int x = lane; x < N; x += 32) {
         float2 v = make_float2(0.f, 0.f);
         if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
-          const float2 z = c_scale(rb[x], invN);
+          const float2 z = c_scale(rb[swz(x)], invN);
           const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
           v = make_float2(fmaf(yt.x, z.x, yt.y * z.y), fmaf(yt.y, z.x, -yt.x * z.y));
           if (trace != nullptr) {
@@ -348,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
           v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
         }
-        rb[x] = v;
+        rb[swz(x)] = v;
       }
     }
     if (P.g_shift > 0) __syncthreads();  // tile rows are other warps of this CTA
@@ -362,8 +375,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       for (int x = lane; x < N; x += 32) {
         float out = 0.f;
         if (dy2 <= P.ap_lim && ap_dist2(x, N) + dy2 <= P.ap_lim) {
-          float2 v = rowbuf[l0 * CS + x];
-          for (int j = 1; j < G; ++j) v = c_add(v, rowbuf[(l0 + j) * CS + x]);
+          float2 v = rowbuf[l0 * CS + swz(x)];
+          for (int j = 1; j < G; ++j) v = c_add(v, rowbuf[(l0 + j) * CS + swz(x)]);
           out = (v.x != 0.f || v.y != 0.f) ? atan2f(v.y, v.x) : pr[x];
           pr[x] = out;
         }
@@ -381,33 +394,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       float* bS = bE + W * CS;
       float* bSE = reinterpret_cast<float*>(rowbuf);
       float* bSW = bSE + W * CS;
-      const float* r0L = k > 0 ? cluster.map_shared_rank(r0S, k - 1) : r0S;
-      const float* r0R = k < C - 1 ? cluster.map_shared_rank(r0S, k + 1) : r0S;
+      // before colour 0 the slab holds r-init, and hl / hr hold the neighbours' edge columns
       auto wgt = [&](float d) { return prior_weight_fast(d, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p); };
+#pragma unroll 4
       for (int i = tid; i < W * N; i += kThreads) {
         const int cl = i / N, rho = i - cl * N;
         const int x = W * k + cl;
-        const float r0i = r0S[cl * CS + rho];
+        const float r0i = rS[cl * CS + rho];
         const bool dn = rho + 1 < N;
-        // right / lower neighbours (the right column of the slab lives in CTA k+1)
-        const float rE = cl + 1 < W ? r0S[(cl + 1) * CS + rho] : (x + 1 < N ? r0R[rho] : 0.f);
+        const float rE = cl + 1 < W ? rS[(cl + 1) * CS + rho] : hr[rho];
         bE[cl * CS + rho] = x + 1 < N ? kBnn * wgt(r0i - rE) : 0.f;
-        bS[cl * CS + rho] = dn ? kBnn * wgt(r0i - r0S[cl * CS + rho + 1]) : 0.f;
-        const float rSE = cl + 1 < W ? (dn ? r0S[(cl + 1) * CS + rho + 1] : 0.f) : (x + 1 < N && dn ? r0R[rho + 1] : 0.f);
+        bS[cl * CS + rho] = dn ? kBnn * wgt(r0i - rS[cl * CS + rho + 1]) : 0.f;
+        const float rSE = !dn ? 0.f : (cl + 1 < W ? rS[(cl + 1) * CS + rho + 1] : hr[rho + 1]);
         bSE[cl * CS + rho] = (x + 1 < N && dn) ? kBdiag * wgt(r0i - rSE) : 0.f;
-        const float rSW = cl > 0 ? (dn ? r0S[(cl - 1) * CS + rho + 1] : 0.f) : (x > 0 && dn ? r0L[(W - 1) * CS + rho + 1] : 0.f);
+        const float rSW = !dn ? 0.f : (cl > 0 ? rS[(cl - 1) * CS + rho + 1] : hl[rho + 1]);
         bSW[cl * CS + rho] = (x > 0 && dn) ? kBdiag * wgt(r0i - rSW) : 0.f;
       }
       for (int rho = tid; rho < N; rho += kThreads) {
         // hW: pair (rho, x0-1)-(rho, x0); hNW: (rho-1, x0-1)-(rho, x0); hNE: (rho-1, x1+1)-(rho, x1)
-        const float a0 = r0S[rho], a1 = r0S[(W - 1) * CS + rho];
-        halo[rho] = k > 0 ? kBnn * wgt(a0 - r0L[(W - 1) * CS + rho]) : 0.f;
-        halo[N + rho] = (k > 0 && rho > 0) ? kBdiag * wgt(a0 - r0L[(W - 1) * CS + rho - 1]) : 0.f;
-        halo[2 * N + rho] = (k < C - 1 && rho > 0) ? kBdiag * wgt(a1 - r0R[rho - 1]) : 0.f;
+        const float a0 = rS[rho], a1 = rS[(W - 1) * CS + rho];
+        halo[rho] = k > 0 ? kBnn * wgt(a0 - hl[rho]) : 0.f;
+        halo[N + rho] = (k > 0 && rho > 0) ? kBdiag * wgt(a0 - hl[rho - 1]) : 0.f;
+        halo[2 * N + rho] = (k < C - 1 && rho > 0) ? kBdiag * wgt(a1 - hr[rho - 1]) : 0.f;
       }
       __syncthreads();
-      const float* rL = k > 0 ? cluster.map_shared_rank(rS, k - 1) : rS;
-      const float* rR = k < C - 1 ? cluster.map_shared_rank(rS, k + 1) : rS;
+      float* hr_left = k > 0 ? cluster.map_shared_rank(hr, k - 1) : hr;
+      float* hl_right = k < C - 1 ? cluster.map_shared_rank(hl, k + 1) : hl;
       for (int c = 0; c < 4; ++c) {
         const int cx = c & 1, cy = c >> 1;  // colours (0,0), (1,0), (0,1), (1,1)
         for (int idx = tid; idx < 4 * N; idx += kThreads) {
@@ -416,14 +428,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           const int o = cl * CS + rho;
           const bool up = rho > 0, dn = rho + 1 < N;
           // neighbour values: current r (earlier colours already updated)
-          const float rW = cl > 0 ? rS[o - CS] : rL[(W - 1) * CS + rho];
-          const float rE = cl + 1 < W ? rS[o + CS] : rR[rho];
+          const float rW = cl > 0 ? rS[o - CS] : hl[rho];
+          const float rE = cl + 1 < W ? rS[o + CS] : hr[rho];
           const float rN = up ? rS[o - 1] : 0.f;
           const float rSo = dn ? rS[o + 1] : 0.f;
-          const float rNW = !up ? 0.f : (cl > 0 ? rS[o - CS - 1] : rL[(W - 1) * CS + rho - 1]);
-          const float rNE = !up ? 0.f : (cl + 1 < W ? rS[o + CS - 1] : rR[rho - 1]);
-          const float rSW = !dn ? 0.f : (cl > 0 ? rS[o - CS + 1] : rL[(W - 1) * CS + rho + 1]);
-          const float rSE = !dn ? 0.f : (cl + 1 < W ? rS[o + CS + 1] : rR[rho + 1]);
+          const float rNW = !up ? 0.f : (cl > 0 ? rS[o - CS - 1] : hl[rho - 1]);
+          const float rNE = !up ? 0.f : (cl + 1 < W ? rS[o + CS - 1] : hr[rho - 1]);
+          const float rSW = !dn ? 0.f : (cl > 0 ? rS[o - CS + 1] : hl[rho + 1]);
+          const float rSE = !dn ? 0.f : (cl + 1 < W ? rS[o + CS + 1] : hr[rho + 1]);
           // pair weights (zero where the neighbour is off the grid)
           const float wE = bE[o], wS = bS[o], wSE = bSE[o], wSW = bSW[o];
           const float wW = cl > 0 ? bE[o - CS] : halo[rho];
@@ -439,8 +451,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           Csum = fmaf(wNE, rNE, Csum);
           Csum = fmaf(wSW, rSW, Csum);
           Csum = fmaf(wSE, rSE, Csum);
-          const float root = icd_root_from(Wsum, Csum, sS[o], r0S[o]);
-          rS[o] = fmaxf(root, P.r_floor);
+          const float rn = fmaxf(icd_root_from(Wsum, Csum, sS[o], rS[o]), P.r_floor);
+          rS[o] = rn;
+          // edge pixels of this colour are read by the neighbouring slab in the next colours
+          if (cl == 0 && k > 0) hr_left[rho] = rn;
+          if (cl == W - 1 && k < C - 1) hl_right[rho] = rn;
         }
         cluster.sync();  // B4..B7
       }
@@ -484,11 +499,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_strehl(const __grid_constant__ 
           sincosf(a.phi_true[gi] - a.phi_est[gi], &sn, &cs);
           v = make_float2(cs, sn);
         }
-        rb[x] = v;
+        rb[swz(x)] = v;
       }
       __syncwarp();
       fft_row<N, +1>(rb, tw, lane);
-      for (int x = lane; x < N; x += 32) cluster.map_shared_rank(colbuf, x / W)[(x % W) * CS + rho] = rb[x];
+      for (int x = lane; x < N; x += 32) cluster.map_shared_rank(colbuf, x / W)[(x % W) * CS + swz(rho)] = rb[swz(x)];
     }
   }
   cluster.sync();
@@ -496,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_strehl(const __grid_constant__ 
   {
     float2* cb = colbuf + warp * CS;
     fft_row<N, +1>(cb, tw, lane);
-    for (int rho = lane; rho < N; rho += 32) m = fmaxf(m, c_abs2(cb[rho]));
+    for (int rho = lane; rho < N; rho += 32) m = fmaxf(m, c_abs2(cb[swz(rho)]));
     m = warp_max(m);
   }
   if (lane == 0) red[warp] = m;
@@ -531,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fft2(const __grid_constant__ Ff
   for (int i = tid; i < N; i += kThreads) tw[i] = a.tw[i];
   for (int i = tid; i < R * N; i += kThreads) {
     const int l = i / N, x = i - l * N;
-    rowbuf[i] = a.in[static_cast<size_t>(k + C * l) * N + x];
+    rowbuf[l * N + swz(x)] = a.in[static_cast<size_t>(k + C * l) * N + x];
   }
   __syncthreads();
   cluster.sync();  // every read of `in` precedes every write of `out`
@@ -540,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fft2(const __grid_constant__ Ff
     float2* rb = rowbuf + l * N;
     if (a.inverse) fft_row<N, +1>(rb, tw, lane);
     else fft_row<N, -1>(rb, tw, lane);
-    for (int x = lane; x < N; x += 32) cluster.map_shared_rank(colbuf, x / W)[(x % W) * CS + rho] = rb[x];
+    for (int x = lane; x < N; x += 32) cluster.map_shared_rank(colbuf, x / W)[(x % W) * CS + swz(rho)] = rb[swz(x)];
   }
   cluster.sync();
   {
@@ -552,7 +567,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fft2(const __grid_constant__ Ff
   const float invN = 1.f / static_cast<float>(N);
   for (int i = tid; i < N * W; i += kThreads) {
     const int rho = i / W, cl = i - rho * W;
-    a.out[static_cast<size_t>(rho) * N + W * k + cl] = c_scale(colbuf[cl * CS + rho], invN);
+    a.out[static_cast<size_t>(rho) * N + W * k + cl] = c_scale(colbuf[cl * CS + swz(rho)], invN);
   }
   cluster.sync();
 }

@@ -163,13 +163,13 @@ __global__ void __launch_bounds__(kThreads) k_l2_rows_inv(const __grid_constant_
         u = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
       }
       pr[x] = ph;  // the state keeps phi' (tip/tilt removed) until the phase step
-      rb[x] = u;
+      rb[swz(x)] = u;
     }
     __syncwarp();
     fft_row<N, +1, V>(rb, tw, lane);
   } else {
     for (int x = lane; x < N; x += 32) {
-      rb[x] = make_float2(0.f, 0.f);
+      rb[swz(x)] = make_float2(0.f, 0.f);
       pr[x] = 0.f;
     }
   }
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_rows_inv(const __grid_constant_
   // fb is column-major: fb[x N + rho]; 16 threads write the 16 rows of one column
   for (int i = threadIdx.x; i < kT * N; i += kThreads) {
     const int x = i / kT, r = i - x * kT;
-    S.fb[static_cast<size_t>(x) * N + kT * blockIdx.x + r] = rows[r * (N + 1) + x];
+    S.fb[static_cast<size_t>(x) * N + kT * blockIdx.x + r] = rows[r * (N + 1) + swz(x)];
   }
 }
 
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_cols(const __grid_constant__ L2
   const int x0 = kT * blockIdx.x;
   for (int i = threadIdx.x; i < kT * N; i += kThreads) {
     const int c = i / N, rho = i - c * N;
-    cols[c * (N + 1) + rho] = S.fb[static_cast<size_t>(x0 + c) * N + rho];
+    cols[c * (N + 1) + swz(rho)] = S.fb[static_cast<size_t>(x0 + c) * N + rho];
   }
   for (int i = threadIdx.x; i < kT * N; i += kThreads) {  // coalesced 64-byte row segments
     const int rho = i / kT, c = i - rho * kT;
@@ -210,12 +210,12 @@ __global__ void __launch_bounds__(kThreads) k_l2_cols(const __grid_constant__ L2
   fft_row<N, +1, V>(cb, tw, lane);
   const float invN = 1.f / static_cast<float>(N);
   for (int rho = lane; rho < N; rho += 32) {
-    const float2 bb = c_scale(cb[rho], invN);
+    const float2 bb = c_scale(cb[swz(rho)], invN);
     const float rp = rc[rho];
     const float ri = first ? fmaxf(fmaf(P.lam1, rp, P.lam_alpha * c_abs2(bb)), P.r_floor) : rp;
     const float w = ri / (ri + P.noise_var);
     const float2 mu = c_scale(bb, w);
-    cb[rho] = mu;
+    cb[swz(rho)] = mu;
     rc[rho] = ri;
     sc[rho] = fmaf(P.noise_var, w, c_abs2(mu));
   }
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_cols(const __grid_constant__ L2
     S.r0[gi] = ri;
     S.r[gi] = ri;  // the ICD sweep starts from r-init
     S.s[gi] = stile[c * (N + 1) + rho];
-    if (ap_dist2(rho, N) <= P.ap_lim) S.fa[gi] = cols[c * (N + 1) + rho];
+    if (ap_dist2(rho, N) <= P.ap_lim) S.fa[gi] = cols[c * (N + 1) + swz(rho)];
   }
 }
 
@@ -254,14 +254,14 @@ __global__ void __launch_bounds__(kThreads) k_l2_rows_fwd(const __grid_constant_
   const bool row_ap = dy2 <= P.ap_lim;
   float2* rb = rows + warp * (N + 1);
   if (row_ap)
-    for (int x = lane; x < N; x += 32) rb[x] = S.fa[static_cast<size_t>(rho) * N + x];
+    for (int x = lane; x < N; x += 32) rb[swz(x)] = S.fa[static_cast<size_t>(rho) * N + x];
   __syncthreads();
   if (row_ap) fft_row<N, -1, V>(rb, tw, lane);
   const float invN = 1.f / static_cast<float>(N);
   for (int x = lane; x < N; x += 32) {
     float2 v = make_float2(0.f, 0.f);
     if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
-      const float2 z = c_scale(rb[x], invN);
+      const float2 z = c_scale(rb[swz(x)], invN);
       const float2 yt = c_scale(c_sub(y[static_cast<size_t>(rho) * N + x], ymean), scale);
       v = make_float2(fmaf(yt.x, z.x, yt.y * z.y), fmaf(yt.y, z.x, -yt.x * z.y));
     }
@@ -269,15 +269,15 @@ __global__ void __launch_bounds__(kThreads) k_l2_rows_fwd(const __grid_constant_
       v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
       v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
     }
-    rb[x] = v;
+    rb[swz(x)] = v;
   }
   __syncthreads();
   const int l0 = warp & ~(G - 1);
   float* pr = S.phi + static_cast<size_t>(rho) * N;
   for (int x = lane; x < N; x += 32) {
     if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
-      float2 v = rows[l0 * (N + 1) + x];
-      for (int j = 1; j < G; ++j) v = c_add(v, rows[(l0 + j) * (N + 1) + x]);
+      float2 v = rows[l0 * (N + 1) + swz(x)];
+      for (int j = 1; j < G; ++j) v = c_add(v, rows[(l0 + j) * (N + 1) + swz(x)]);
       if (v.x != 0.f || v.y != 0.f) pr[x] = atan2f(v.y, v.x);  // else phi' is kept
     }
   }
