@@ -59,15 +59,20 @@ __device__ __forceinline__ int row_local(int rho, int gs) {
   return (((rho >> gs) / C) << gs) + (rho & ((1 << gs) - 1));
 }
 
-// Chan et al. pairwise update of (count, complex mean, M2 = sum |y - mean|^2).
-__device__ __forceinline__ void chan_combine(float& n_a, float2& m_a, float& q_a, float n_b, float2 m_b,
-                                             float q_b) {
-  const float n = n_a + n_b;
-  const float2 d = c_sub(m_b, m_a);
-  const float f = n_b / n;
-  m_a = make_float2(fmaf(d.x, f, m_a.x), fmaf(d.y, f, m_a.y));
-  q_a = q_a + q_b + c_abs2(d) * (n_a * f);
-  n_a = n;
+// Combine equal-size groups held one per lane (lanes with valid == false contribute nothing):
+// overall mean = mean of the group means; M2 = sum_l (M2_l + n |m_l - mean|^2); plain sums for
+// the rest.  Butterfly sums: every lane ends with the same, order-fixed result.
+__device__ __forceinline__ void combine_equal_groups(float* v, bool valid, float n_group, float inv_groups) {
+  float sx = warp_sum(valid ? v[0] : 0.f);
+  float sy = warp_sum(valid ? v[1] : 0.f);
+  const float mx = sx * inv_groups, my = sy * inv_groups;
+  const float dx = v[0] - mx, dy = v[1] - my;
+  const float q = warp_sum(valid ? fmaf(n_group, fmaf(dx, dx, dy * dy), v[2]) : 0.f);
+  v[0] = mx;
+  v[1] = my;
+  v[2] = q;
+#pragma unroll
+  for (int j = 3; j < 8; ++j) v[j] = warp_sum(valid ? v[j] : 0.f);
 }
 
 template <int N, int V>
@@ -117,14 +122,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   for (int i = tid; i < N; i += kThreads) tw[i] = batch.tw[i];
   {
     // phi rows rho and rho + 1 (the latter for the y tip/tilt pairs), 16-byte vectors
-    constexpr int V = N / 4;
+    constexpr int NV4 = N / 4;
     const float4* src = reinterpret_cast<const float4*>(A.phi);
-    for (int i = tid; i < R * V; i += kThreads) {
-      const int l = i / V, xv = i - l * V;
+    for (int i = tid; i < R * NV4; i += kThreads) {
+      const int l = i / NV4, xv = i - l * NV4;
       const int rho = row_of<C>(k, l, P.g_shift);
-      reinterpret_cast<float4*>(phib)[i] = src[static_cast<size_t>(rho) * V + xv];
+      reinterpret_cast<float4*>(phib)[i] = src[static_cast<size_t>(rho) * NV4 + xv];
       reinterpret_cast<float4*>(phin)[i] =
-          rho + 1 < N ? src[static_cast<size_t>(rho + 1) * V + xv] : make_float4(0.f, 0.f, 0.f, 0.f);
+          rho + 1 < N ? src[static_cast<size_t>(rho + 1) * NV4 + xv] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // reflectance slab: W = 16 consecutive floats per row = 4 vectors
     for (int i = tid; i < N * (W / 4); i += kThreads) {
@@ -179,17 +184,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    float n_a = static_cast<float>(N), q_a = red[2];
-    float2 m_a = make_float2(red[0], red[1]);
-    float t0 = red[3], t1 = red[4], t2 = red[5], t3 = red[6], bad = red[7];
-    for (int w = 1; w < 16; ++w) {
-      const float* o = red + w * 8;
-      chan_combine(n_a, m_a, q_a, static_cast<float>(N), make_float2(o[0], o[1]), o[2]);
-      t0 += o[3]; t1 += o[4]; t2 += o[5]; t3 += o[6]; bad += o[7];
-    }
-    red[0] = m_a.x; red[1] = m_a.y; red[2] = q_a; red[3] = t0; red[4] = t1; red[5] = t2; red[6] = t3;
-    red[7] = bad;
+  if (warp == 0) {  // the 16 rows of this CTA: equal groups of N samples
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = lane < 16 ? red[lane * 8 + j] : 0.f;
+    combine_equal_groups(v, lane < 16, static_cast<float>(N), 1.f / 16.f);
+    __syncwarp();
+    if (lane < 8) red[lane] = v[lane];
   }
   __syncthreads();
   // push this CTA's partials into slot k of every CTA of the cluster (read locally after B1)
@@ -212,18 +213,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
       o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
     }
-    const float nb = static_cast<float>(R * N);
-    float n_a = nb, q_a = 0.f;
-    float2 m_a = make_float2(0.f, 0.f);
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, bad = 0.f;
-    for (int q = 0; q < C; ++q) {
-      float v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = __shfl_sync(0xffffffffu, o[j], q);
-      if (q == 0) { m_a = make_float2(v[0], v[1]); q_a = v[2]; }
-      else chan_combine(n_a, m_a, q_a, nb, make_float2(v[0], v[1]), v[2]);
-      t0 += v[3]; t1 += v[4]; t2 += v[5]; t3 += v[6]; bad += v[7];
-    }
+    combine_equal_groups(o, lane < C, static_cast<float>(R * N), 1.f / static_cast<float>(C));
+    const float2 m_a = make_float2(o[0], o[1]);
+    const float q_a = o[2], t0 = o[3], t1 = o[4], t2 = o[5], t3 = o[6], bad = o[7];
     if (lane == 0) {
     const float scale = sqrtf(static_cast<float>(N) * static_cast<float>(N) / q_a);
     const bool finite = isfinite(m_a.x) && isfinite(m_a.y) && isfinite(q_a) && q_a > 0.f && isfinite(scale);
@@ -281,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
             pr[x] = ph;
             const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
             float sn, cs;
-            __sincosf(ph, &sn, &cs);  // |ph| <= pi: absolute error ~ 5e-7
+            sincosf(ph, &sn, &cs);
             rb[swz(x)] = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
           } else {
             rb[swz(x)] = make_float2(0.f, 0.f);
@@ -422,6 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       float* hl_right = k < C - 1 ? cluster.map_shared_rank(hl, k + 1) : hl;
       for (int c = 0; c < 4; ++c) {
         const int cx = c & 1, cy = c >> 1;  // colours (0,0), (1,0), (0,1), (1,1)
+#pragma unroll 2
         for (int idx = tid; idx < 4 * N; idx += kThreads) {
           const int j = idx % (N / 2), ci = idx / (N / 2);
           const int cl = cx + 2 * ci, rho = cy + 2 * j;

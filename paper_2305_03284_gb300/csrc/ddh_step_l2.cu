@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_rows_inv(const __grid_constant_
         if (first && P.tilt_mode) ph = wrap_pi(ph - fmaf(tx, static_cast<float>(x) - cc, tyr));
         const float2 yt = c_scale(c_sub(y[static_cast<size_t>(rho) * N + x], ymean), scale);
         float sn, cs;
-        __sincosf(ph, &sn, &cs);
+        sincosf(ph, &sn, &cs);
         u = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
       }
       pr[x] = ph;  // the state keeps phi' (tip/tilt removed) until the phase step

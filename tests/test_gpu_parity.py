@@ -140,9 +140,9 @@ def test_free_running_parity_64_100_frames_tiled_phase(ddh):
     a = o.aperture(cfg.n, cfg.aperture_diam)
     gphi, gr, gS = _run_free(ddh, p, ys, ph)
     ophi, orr, oS = _run_oracle(prm, ys, ph)
-    assert rel_l2_phase(gphi[-1], ophi[-1], a) < TOL
-    assert rel_l2(gr[-1], orr[-1]) < TOL
-    assert rel_l2(gS, oS) < TOL
+    e = (rel_l2_phase(gphi[-1], ophi[-1], a), rel_l2(gr[-1], orr[-1]), rel_l2(gS, oS))
+    print(f"100 frames, tiled phase: phi {e[0]:.2e}, r {e[1]:.2e}, Strehl trace {e[2]:.2e}")
+    assert e[0] < TOL and e[1] < TOL and e[2] < TOL, e
     assert np.all(gphi[:, ~a] == 0.0)
 
 
