@@ -218,7 +218,7 @@ int enqueue(ddh_state* s, const void* y, float* trace) {
   b.fa[0] = frame_args(s, y, trace);
   b.tw = s->tw;
   b.count = 1;
-  DDH_CUDA(ddh::launch_step(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], b, s->stream));
+  DDH_CUDA(ddh::launch_step(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], b, s->stream, /*pdl=*/true));
   s->frame += 1;
   return DDH_OK;
 }

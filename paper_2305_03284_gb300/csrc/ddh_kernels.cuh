@@ -97,7 +97,9 @@ struct Fft2Args {
 };
 
 // Launchers (return the CUDA error of the launch).  `n` selects the template instance.
-cudaError_t launch_step(int n, int schedule, const StepBatch& b, cudaStream_t st);
+// `pdl`: launch with programmatic stream serialization, so that the kernel's prologue (frame
+// TMA, twiddles, frame statistics) overlaps the tail of the previous kernel on `st`.
+cudaError_t launch_step(int n, int schedule, const StepBatch& b, cudaStream_t st, bool pdl = false);
 cudaError_t launch_strehl(int n, const StrehlArgs& a, cudaStream_t st);
 cudaError_t launch_fft2(int n, const Fft2Args& a, cudaStream_t st);
 // One-time per-device function attributes (shared memory size, cluster size); also checks

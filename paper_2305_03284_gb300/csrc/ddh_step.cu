@@ -6,11 +6,15 @@
 //   * the column slab x = 16 k .. 16 k + 15 of the image plane: a column buffer (one column
 //     per warp, contiguous), r, the r-init copy and s = E|g|^2.
 // The 2-D DFT is a row pass (one warp per row), a transpose through distributed shared
-// memory (remote stores into the owner CTA's buffer), and a column pass.  Cluster barriers
+// memory (16-byte remote stores of each row's 16-column segments into the column owner's
+// row-major staging buffer; 8-byte remote stores on the way back), and a column pass.  Cluster barriers
 // separate the frame's global dependencies:
 //   B1 Normalize / tip-tilt statistics   B2 row IFFT -> columns   B3 r-init + column FFT -> rows
 //   B4..B7 the four ICD colours (the last also guards shared memory until every reader is done).
 // Per frame the kernel reads y (8 B/px), phi and r (4 B/px each) and writes phi and r.
+// Everything before `grid_dep_wait` (frame TMA, twiddles, frame statistics) is independent of
+// the previous frame, so under programmatic dependent launch it overlaps the previous frame's
+// kernel on the same stream; the state (phi, r) is read only after the wait.
 #include <cooperative_groups.h>
 
 #include "ddh_device.cuh"
@@ -35,7 +39,9 @@ struct StepLayout {
   static constexpr size_t phin = al(phib + size_t(R) * N * 4);  // phi of row rho + 1
   static constexpr size_t rS = al(phin + size_t(R) * N * 4);
   static constexpr size_t sS = al(rS + size_t(W) * CS * 4);
-  static constexpr size_t hl = al(sS + size_t(W) * CS * 4);    // r of the left slab's last column
+  // row-major staging of the row pass for this slab: 16 columns (8 chunks of 2) per row
+  static constexpr size_t stage = al(sS + size_t(W) * CS * 4);
+  static constexpr size_t hl = al(stage + size_t(N) * 16 * 8);  // r of the left slab's last column
   static constexpr size_t hr = al(hl + size_t(N) * 4);         // r of the right slab's first column
   static constexpr size_t halo = al(hr + size_t(N) * 4);       // 3 x N halo-pair weights
   static constexpr size_t red = al(halo + size_t(3) * N * 4);  // 16 warps x 8 floats
@@ -95,6 +101,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   float* phin = reinterpret_cast<float*>(smem + L::phin);
   float* rS = reinterpret_cast<float*>(smem + L::rS);
   float* sS = reinterpret_cast<float*>(smem + L::sS);
+  float4* stage = reinterpret_cast<float4*>(smem + L::stage);
   float* hl = reinterpret_cast<float*>(smem + L::hl);
   float* hr = reinterpret_cast<float*>(smem + L::hr);
   float* halo = reinterpret_cast<float*>(smem + L::halo);
@@ -105,7 +112,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   const float cc = 0.5f * static_cast<float>(N - 1);
   const float invN = 1.f / static_cast<float>(N);
 
-  // ---- phase 0: stage y rows by TMA; phi rows, r slab, twiddles by plain loads ----------
+  // ---- phase 0: stage y rows by TMA and twiddles (independent of the previous frame) ------
+  grid_dep_launch();  // the next frame's kernel may start its own prologue now
   if (tid == 0) {
     mbar_init(mbar, 1);
     fence_mbar_init();
@@ -120,6 +128,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     }
   }
   for (int i = tid; i < N; i += kThreads) tw[i] = batch.tw[i];
+  // bounded wait: on expiry the frame is dropped (flag carried into the B1 statistics)
+  const bool loaded = mbar_wait_bounded(mbar, 0, 1u << 22);
+  __syncthreads();
+
+  // ---- phase 1a: per-row statistics of the frame (Normalize, Eq. 4) ----------------------
+  const int rho1 = row_of<C>(k, warp, P.g_shift);
+  float2 mrow;
+  float q = 0.f;
+  {
+    const float2* yr = ybuf + warp * N;
+    float sre = 0.f, sim = 0.f;
+    for (int x = lane; x < N; x += 32) { sre += yr[x].x; sim += yr[x].y; }
+    sre = warp_sum(sre);
+    sim = warp_sum(sim);
+    mrow = make_float2(sre * invN, sim * invN);
+    for (int x = lane; x < N; x += 32) q += c_abs2(c_sub(yr[x], mrow));
+    q = warp_sum(q);
+  }
+
+  // ---- phase 0b: the state written by the previous frame: phi rows, r slab ----------------
+  grid_dep_wait();
   {
     // phi rows rho and rho + 1 (the latter for the y tip/tilt pairs), 16-byte vectors
     constexpr int NV4 = N / 4;
@@ -141,23 +170,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       rS[(4 * cv + 3) * CS + rho] = v.w;
     }
   }
-  for (int i = tid; i < W * CS; i += kThreads) colbuf[i] = make_float2(0.f, 0.f);
-  // bounded wait: on expiry the frame is dropped (flag carried into the B1 statistics)
-  const bool loaded = mbar_wait_bounded(mbar, 0, 1u << 22);
   __syncthreads();
 
-  // ---- phase 1: per-row statistics (Normalize, Eq. 4) and tip/tilt sums (Sec. 4) --------
+  // ---- phase 1b: tip/tilt sums (Sec. 4) ------------------------------------------------
   {
-    const int l = warp, rho = row_of<C>(k, l, P.g_shift);
-    const float2* yr = ybuf + l * N;
-    float sre = 0.f, sim = 0.f;
-    for (int x = lane; x < N; x += 32) { sre += yr[x].x; sim += yr[x].y; }
-    sre = warp_sum(sre);
-    sim = warp_sum(sim);
-    const float2 mrow = make_float2(sre * invN, sim * invN);
-    float q = 0.f;
-    for (int x = lane; x < N; x += 32) q += c_abs2(c_sub(yr[x], mrow));
-    q = warp_sum(q);
+    const int l = warp, rho = rho1;
     float txs = 0.f, txc = 0.f, tys = 0.f, tyc = 0.f;
     if (P.tilt_mode) {
       const float* pr = phib + l * N;
@@ -251,13 +268,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     const bool first = (it == 0);
     float* trace = first ? A.trace : nullptr;
     // ---- phase 2: back-projection prologue a e^{-j phi} y~ and row IFFT (aperture rows) --
-    if (!first) {
-      // the scatter below writes only aperture rows of colbuf; clear the others again
-      for (int i = tid; i < W * N; i += kThreads) {
-        const int cl = i / N, rho = i - cl * N;
-        if (ap_dist2(rho, N) > P.ap_lim) colbuf[cl * CS + swz(rho)] = make_float2(0.f, 0.f);
-      }
-    }
     {
       const int l = warp, rho = row_of<C>(k, l, P.g_shift);
       const int dy2 = ap_dist2(rho, N);
@@ -282,9 +292,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
         }
         __syncwarp();
         fft_row<N, +1, V>(rb, tw, lane);
-        for (int x = lane; x < N; x += 32) {
-          float2* dst = cluster.map_shared_rank(colbuf, x / W);
-          dst[(x % W) * CS + swz(rho)] = rb[swz(x)];
+        // transpose: CTA j receives columns 16 j .. 16 j + 15 of this row as 8 chunks of two
+        // (16-byte remote stores), chunk m at slot m ^ (rho & 7) of stage row rho, its two
+        // values swapped when bit 3 of rho is set (the column reads below are conflict-free)
+        const int sw = rho & 7, sp = (rho >> 3) & 1;
+        for (int g = lane; g < N / 2; g += 32) {
+          const int j = g >> 3, m = g & 7;
+          const float2 a = rb[16 * j + ((2 * m) ^ j)];      // swz(16 j + o) = 16 j + (o ^ j)
+          const float2 b = rb[16 * j + ((2 * m + 1) ^ j)];
+          const float4 v = sp ? make_float4(b.x, b.y, a.x, a.y) : make_float4(a.x, a.y, b.x, b.y);
+          cluster.map_shared_rank(stage, j)[rho * 8 + (m ^ sw)] = v;
         }
       } else {
         for (int x = lane; x < N; x += 32) pr[x] = 0.f;
@@ -295,6 +312,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     {
       const int cl = warp;
       float2* cb = colbuf + cl * CS;
+      {
+        const float2* st2 = reinterpret_cast<const float2*>(stage);
+        for (int rho = lane; rho < N; rho += 32) {
+          float2 v = make_float2(0.f, 0.f);
+          if (ap_dist2(rho, N) <= P.ap_lim)
+            v = st2[rho * 16 + 2 * ((cl >> 1) ^ (rho & 7)) + ((cl & 1) ^ ((rho >> 3) & 1))];
+          cb[swz(rho)] = v;
+        }
+      }
+      __syncwarp();
       fft_row<N, +1, V>(cb, tw, lane);
       for (int rho = lane; rho < N; rho += 32) {
         const float2 b = c_scale(cb[swz(rho)], invN);
@@ -567,19 +594,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_fft2(const __grid_constant__ Ff
 
 // ------------------------------------------------------------------------------ launchers
 template <typename Kern, typename Arg>
-static cudaError_t launch_cluster(Kern kern, int c, int clusters, size_t smem, cudaStream_t st, const Arg& arg) {
+static cudaError_t launch_cluster(Kern kern, int c, int clusters, size_t smem, cudaStream_t st, const Arg& arg,
+                                  bool pdl = false) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(c * clusters), 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = static_cast<unsigned>(c);
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, kern, arg);
 }
 
@@ -655,24 +685,24 @@ size_t step_smem_bytes(int n) {
 }
 
 template <int N>
-static cudaError_t launch_step_n(int v, const StepBatch& b, cudaStream_t st) {
+static cudaError_t launch_step_n(int v, const StepBatch& b, cudaStream_t st, bool pdl) {
   using L = StepLayout<N>;
-  if (v == 0) return launch_cluster(k_ddh_step<N, 0>, L::C, b.count, L::total, st, b);
+  if (v == 0) return launch_cluster(k_ddh_step<N, 0>, L::C, b.count, L::total, st, b, pdl);
   if constexpr (FftSchedules<N>::count > 1) {
-    if (v == 1) return launch_cluster(k_ddh_step<N, 1>, L::C, b.count, L::total, st, b);
+    if (v == 1) return launch_cluster(k_ddh_step<N, 1>, L::C, b.count, L::total, st, b, pdl);
   }
   if constexpr (FftSchedules<N>::count > 2) {
-    if (v == 2) return launch_cluster(k_ddh_step<N, 2>, L::C, b.count, L::total, st, b);
+    if (v == 2) return launch_cluster(k_ddh_step<N, 2>, L::C, b.count, L::total, st, b, pdl);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step(int n, int v, const StepBatch& b, cudaStream_t st) {
+cudaError_t launch_step(int n, int v, const StepBatch& b, cudaStream_t st, bool pdl) {
   switch (n) {
-    case 32: return launch_step_n<32>(v, b, st);
-    case 64: return launch_step_n<64>(v, b, st);
-    case 128: return launch_step_n<128>(v, b, st);
-    case 256: return launch_step_n<256>(v, b, st);
+    case 32: return launch_step_n<32>(v, b, st, pdl);
+    case 64: return launch_step_n<64>(v, b, st, pdl);
+    case 128: return launch_step_n<128>(v, b, st, pdl);
+    case 256: return launch_step_n<256>(v, b, st, pdl);
     default: return cudaErrorInvalidValue;
   }
 }
