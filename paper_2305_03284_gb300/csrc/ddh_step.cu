@@ -30,10 +30,11 @@ struct StepLayout {
   static constexpr int R = kRowsPerCta;        // local rows
   static constexpr int W = kRowsPerCta;        // slab columns
   static constexpr int CS = N + 1;             // padded column stride (floats / float2)
+  static constexpr int RS = N + 2;             // row-buffer stride (float2): 16-byte aligned rows
   static constexpr size_t al(size_t v) { return (v + 127) & ~size_t(127); }
   static constexpr size_t tw = 0;
   static constexpr size_t rowbuf = al(tw + N * 8);
-  static constexpr size_t colbuf = al(rowbuf + size_t(R) * CS * 8);
+  static constexpr size_t colbuf = al(rowbuf + size_t(R) * RS * 8);
   static constexpr size_t ybuf = al(colbuf + size_t(W) * CS * 8);
   static constexpr size_t phib = al(ybuf + size_t(R) * N * 8);
   static constexpr size_t phin = al(phib + size_t(R) * N * 4);  // phi of row rho + 1
@@ -84,7 +85,7 @@ __device__ __forceinline__ void combine_equal_groups(float* v, bool valid, float
 template <int N, int V>
 __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant__ StepBatch batch) {
   using L = StepLayout<N>;
-  constexpr int C = L::C, R = L::R, W = L::W, CS = L::CS;
+  constexpr int C = L::C, R = L::R, W = L::W, CS = L::CS, RS = L::RS;
   extern __shared__ __align__(128) unsigned char smem[];
   cg::cluster_group cluster = cg::this_cluster();
   const int k = static_cast<int>(cluster.block_rank());
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     {
       const int l = warp, rho = row_of<C>(k, l, P.g_shift);
       const int dy2 = ap_dist2(rho, N);
-      float2* rb = rowbuf + l * CS;
+      float2* rb = rowbuf + l * RS;
       float* pr = phib + l * N;
       const float2* yr = ybuf + l * N;
       if (dy2 <= P.ap_lim) {
@@ -347,12 +348,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       }
       __syncwarp();
       fft_row<N, -1, V>(cb, tw, lane);
-      for (int rho = lane; rho < N; rho += 32) {
-        if (ap_dist2(rho, N) <= P.ap_lim) {
-          float2* dst = cluster.map_shared_rank(rowbuf, row_owner<C>(rho, P.g_shift));
-          dst[row_local<C>(rho, P.g_shift) * CS + swz(W * k + cl)] = cb[swz(rho)];
-        }
-      }
+    }
+    __syncthreads();  // every column of the slab is transformed
+    // transpose back: the 16 slab values of aperture row rho go to the row owner as 8 chunks
+    // of two (16-byte remote stores); chunk m covers positions 16 k + 2m, 16 k + 2m + 1 of the
+    // owner's swizzled row, which hold columns (2m) ^ k and (2m + 1) ^ k of this slab
+    for (int f = tid; f < N * 8; f += kThreads) {
+      const int rho = f >> 3, m = f & 7;
+      if (ap_dist2(rho, N) > P.ap_lim) continue;
+      const float2 a = colbuf[((2 * m) ^ k) * CS + swz(rho)];
+      const float2 b = colbuf[((2 * m + 1) ^ k) * CS + swz(rho)];
+      float2* row = cluster.map_shared_rank(rowbuf, row_owner<C>(rho, P.g_shift)) + row_local<C>(rho, P.g_shift) * RS;
+      reinterpret_cast<float4*>(row + W * k)[m] = make_float4(a.x, a.y, b.x, b.y);
     }
     cluster.sync();  // B3
     // ---- phase 4: row FFT of mu (aperture rows) and phase M-step ------------------------
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       const int l = warp, rho = row_of<C>(k, l, gs);
       const int dy2 = ap_dist2(rho, N);
       const bool row_ap = dy2 <= P.ap_lim;
-      float2* rb = rowbuf + l * CS;
+      float2* rb = rowbuf + l * RS;
       const float2* yr = ybuf + l * N;
       if (row_ap) fft_row<N, -1, V>(rb, tw, lane);
       for (int x = lane; x < N; x += 32) {
@@ -394,8 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       for (int x = lane; x < N; x += 32) {
         float out = 0.f;
         if (dy2 <= P.ap_lim && ap_dist2(x, N) + dy2 <= P.ap_lim) {
-          float2 v = rowbuf[l0 * CS + swz(x)];
-          for (int j = 1; j < G; ++j) v = c_add(v, rowbuf[(l0 + j) * CS + swz(x)]);
+          float2 v = rowbuf[l0 * RS + swz(x)];
+          for (int j = 1; j < G; ++j) v = c_add(v, rowbuf[(l0 + j) * RS + swz(x)]);
           out = (v.x != 0.f || v.y != 0.f) ? atan2f(v.y, v.x) : pr[x];
           pr[x] = out;
         }
