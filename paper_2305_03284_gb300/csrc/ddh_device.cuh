@@ -240,6 +240,12 @@ __device__ __forceinline__ float hw_exp2(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+// log2 on the MUFU unit, subnormal inputs flushed to zero (log2 -> -inf).
+__device__ __forceinline__ float hw_log2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float hw_rcp(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -251,7 +257,7 @@ __device__ __forceinline__ float hw_rcp(float x) {
 __device__ __forceinline__ float prior_weight_fast(float delta, float w0, float inv_tsig, float q_minus_p,
                                                    float q_over_p) {
   const float t = fabsf(delta) * inv_tsig;
-  const float u = t > 0.f ? hw_exp2(q_minus_p * __log2f(t)) : 0.f;
+  const float u = t > 0.f ? hw_exp2(q_minus_p * hw_log2(t)) : 0.f;
   const float d = 1.f + u;
   return (w0 * (q_over_p + u)) * hw_rcp(d * d);
 }
@@ -311,14 +317,16 @@ __device__ __forceinline__ float icd_root(float W, float C, float s) {
 
 // Same root, solved first by Newton from `r_start` (the pixel's entry value, close to the
 // update) when f is monotone (C^2 <= 3W: a single real root, so Newton cannot pick another
-// one).  Accepted when the last step changed r by less than 2^-20 relative; otherwise, and
-// whenever f is not monotone, the closed form above decides.
+// one).  Six steps: starts within a factor 0.7 of the root need five, and a warp pays for
+// the closed form if any one of its lanes falls back.  Accepted when the last step changed r
+// by less than 2^-20 relative; otherwise, and whenever f is not monotone, the closed form
+// above decides.
 __device__ __forceinline__ float icd_root_from(float W, float C, float s, float r_start) {
   if (W > 0.f && C * C <= 3.f * W && r_start > 0.f) {
     float r = r_start;
     float step = 0.f;
 #pragma unroll
-    for (int it = 0; it < 4; ++it) {
+    for (int it = 0; it < 6; ++it) {
       const float f = fmaf(fmaf(fmaf(W, r, -C), r, 1.f), r, -s);
       const float fp = fmaf(fmaf(3.f * W, r, -2.f * C), r, 1.f);  // >= 1 - C^2/(3W) >= 0
       step = __fdividef(f, fp);

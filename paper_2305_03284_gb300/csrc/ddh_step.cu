@@ -422,19 +422,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       float* bSW = bSE + W * CS;
       // before colour 0 the slab holds r-init, and hl / hr hold the neighbours' edge columns
       auto wgt = [&](float d) { return prior_weight_fast(d, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p); };
-#pragma unroll 4
-      for (int i = tid; i < W * N; i += kThreads) {
-        const int cl = i / N, rho = i - cl * N;
-        const int x = W * k + cl;
-        const float r0i = rS[cl * CS + rho];
-        const bool dn = rho + 1 < N;
-        const float rE = cl + 1 < W ? rS[(cl + 1) * CS + rho] : hr[rho];
-        bE[cl * CS + rho] = x + 1 < N ? kBnn * wgt(r0i - rE) : 0.f;
-        bS[cl * CS + rho] = dn ? kBnn * wgt(r0i - rS[cl * CS + rho + 1]) : 0.f;
-        const float rSE = !dn ? 0.f : (cl + 1 < W ? rS[(cl + 1) * CS + rho + 1] : hr[rho + 1]);
-        bSE[cl * CS + rho] = (x + 1 < N && dn) ? kBdiag * wgt(r0i - rSE) : 0.f;
-        const float rSW = !dn ? 0.f : (cl > 0 ? rS[(cl - 1) * CS + rho + 1] : hl[rho + 1]);
-        bSW[cl * CS + rho] = (x > 0 && dn) ? kBdiag * wgt(r0i - rSW) : 0.f;
+      // every load of a batch precedes its stores (the weight arrays alias other buffers, so
+      // a load after a store could not be moved above it), which keeps 4 pixels x 4 weights
+      // of MUFU work in flight per thread
+      constexpr int kPx = W * N / kThreads;  // pixels per thread (N / 32)
+      constexpr int kB = kPx < 4 ? kPx : 4;
+#pragma unroll
+      for (int u0 = 0; u0 < kPx; u0 += kB) {
+        float dd[kB][4];
+        bool ok[kB][4];
+        int oo[kB];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          const int i = tid + kThreads * (u0 + b);
+          const int cl = i / N, rho = i - cl * N;
+          const int x = W * k + cl;
+          const int o = cl * CS + rho;
+          const bool dn = rho + 1 < N;
+          const float r0i = rS[o];
+          const float rE = cl + 1 < W ? rS[o + CS] : hr[rho];
+          const float rSo = dn ? rS[o + 1] : 0.f;
+          const float rSE = !dn ? 0.f : (cl + 1 < W ? rS[o + CS + 1] : hr[rho + 1]);
+          const float rSW = !dn ? 0.f : (cl > 0 ? rS[o - CS + 1] : hl[rho + 1]);
+          dd[b][0] = r0i - rE;  dd[b][1] = r0i - rSo;  dd[b][2] = r0i - rSE;  dd[b][3] = r0i - rSW;
+          ok[b][0] = x + 1 < N;  ok[b][1] = dn;  ok[b][2] = x + 1 < N && dn;  ok[b][3] = x > 0 && dn;
+          oo[b] = o;
+        }
+        float ww[kB][4];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ww[b][e] = ok[b][e] ? (e < 2 ? kBnn : kBdiag) * wgt(dd[b][e]) : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          bE[oo[b]] = ww[b][0];
+          bS[oo[b]] = ww[b][1];
+          bSE[oo[b]] = ww[b][2];
+          bSW[oo[b]] = ww[b][3];
+        }
       }
       for (int rho = tid; rho < N; rho += kThreads) {
         // hW: pair (rho, x0-1)-(rho, x0); hNW: (rho-1, x0-1)-(rho, x0); hNE: (rho-1, x1+1)-(rho, x1)
@@ -448,8 +474,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       float* hl_right = k < C - 1 ? cluster.map_shared_rank(hl, k + 1) : hl;
       for (int c = 0; c < 4; ++c) {
         const int cx = c & 1, cy = c >> 1;  // colours (0,0), (1,0), (0,1), (1,1)
-#pragma unroll 2
-        for (int idx = tid; idx < 4 * N; idx += kThreads) {
+        // the pixels of one colour are not neighbours of each other: every thread loads the
+        // inputs of all its pixels, solves, then stores (kCp = 4N / 512 pixels per thread)
+        constexpr int kCp = (4 * N + kThreads - 1) / kThreads;
+        float Wv[kCp], Cv[kCp], sv[kCp], rv[kCp];
+        int ov[kCp], cv[kCp], hv[kCp];
+#pragma unroll
+        for (int u = 0; u < kCp; ++u) {
+          const int idx = tid + kThreads * u;
+          ov[u] = -1;
+          if (4 * N % kThreads != 0 && idx >= 4 * N) continue;
           const int j = idx % (N / 2), ci = idx / (N / 2);
           const int cl = cx + 2 * ci, rho = cy + 2 * j;
           const int o = cl * CS + rho;
@@ -469,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           const float wN = up ? bS[o - 1] : 0.f;
           const float wNW = !up ? 0.f : (cl > 0 ? bSE[o - CS - 1] : halo[N + rho]);
           const float wNE = !up ? 0.f : (cl + 1 < W ? bSW[o + CS - 1] : halo[2 * N + rho]);
-          const float Wsum = ((wN + wS) + (wW + wE)) + ((wNW + wNE) + (wSW + wSE));
+          Wv[u] = ((wN + wS) + (wW + wE)) + ((wNW + wNE) + (wSW + wSE));
           float Csum = wN * rN;
           Csum = fmaf(wS, rSo, Csum);
           Csum = fmaf(wW, rW, Csum);
@@ -478,11 +512,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           Csum = fmaf(wNE, rNE, Csum);
           Csum = fmaf(wSW, rSW, Csum);
           Csum = fmaf(wSE, rSE, Csum);
-          const float rn = fmaxf(icd_root_from(Wsum, Csum, sS[o], rS[o]), P.r_floor);
-          rS[o] = rn;
+          Cv[u] = Csum;
+          sv[u] = sS[o];
+          rv[u] = rS[o];
+          ov[u] = o;
+          cv[u] = cl;
+          hv[u] = rho;
+        }
+#pragma unroll
+        for (int u = 0; u < kCp; ++u) {
+          if (ov[u] < 0) continue;
+          const float rn = fmaxf(icd_root_from(Wv[u], Cv[u], sv[u], rv[u]), P.r_floor);
+          rS[ov[u]] = rn;
           // edge pixels of this colour are read by the neighbouring slab in the next colours
-          if (cl == 0 && k > 0) hr_left[rho] = rn;
-          if (cl == W - 1 && k < C - 1) hl_right[rho] = rn;
+          if (cv[u] == 0 && k > 0) hr_left[hv[u]] = rn;
+          if (cv[u] == W - 1 && k < C - 1) hl_right[hv[u]] = rn;
         }
         cluster.sync();  // B4..B7
       }
