@@ -93,6 +93,9 @@ int ddh_reflectance(const ddh_state *s, float *out);
  * used to resume from a checkpoint and by teacher-forced comparisons. */
 int ddh_set_state(ddh_state *s, const float *r, const float *phi, int64_t frame_index);
 int64_t ddh_frame_index(const ddh_state *s);
+/* The cudaStream_t the state's work is ordered on (the one given to ddh_init, or the service's
+ * stream for a state admitted by ddh_service_admit); NULL if s is NULL. */
+void *ddh_state_stream(const ddh_state *s);
 
 /* Peak Strehl ratio (N <= 256) of the current phase estimate against `phi_true_dev` (N*N float32,
  * device): max |F^H(a exp(j(phi_true - phi)))|^2 / max |F^H a|^2 (Sec. 5.B).  Synchronous:
@@ -156,10 +159,13 @@ int ddh_step_backward_noalloc(ddh_state *s, const void *y_c64_dev, const float *
 /* ---- streaming service: native continuous-batching scheduler -------------------------------
  * Sensors are admitted against a device-memory budget and keep their state resident; frames
  * are queued per sensor; a scheduler (a library thread after ddh_service_start, or each
- * ddh_service_poll call otherwise) resolves finished batches and launches the next frame of
- * every sensor that has one queued and none on the device, as one ddh_step_batch, without
- * waiting for batches still running (at most `max_in_flight`).  A sensor's results do not
- * depend on which other sensors share its launches.  The paper has a frame loop per sensor
+ * ddh_service_poll call otherwise) resolves finished batches and launches the next queued
+ * frame of every sensor that has one, as one ddh_step_batch, without waiting for batches still
+ * running (at most `max_in_flight`; 1 gives continuous batching: each batch takes every frame
+ * that arrived while the previous one ran).  A batch holds at most one frame per sensor; a
+ * sensor's next frame may go into a later batch while its previous one still runs, since
+ * batches execute in order on the service's stream.  A sensor's results do not depend on which
+ * other sensors share its launches.  The paper has a frame loop per sensor
  * (Fig. 1); the multi-sensor service around it is this library's. */
 #define DDH_SERVICE_PER_FRAME_LAUNCH 1u /* comparison mode: one ddh_step launch per frame */
 typedef struct ddh_service ddh_service;
@@ -185,7 +191,7 @@ ddh_state *ddh_service_state(ddh_service *s, int sensor_id);
 /* Queue one frame (device pointer, caller-owned, valid until its completion is returned).
  * arrival_s < 0 stamps the current time. */
 int ddh_service_submit(ddh_service *s, int sensor_id, const void *y_c64_dev, double arrival_s, uint64_t tag);
-/* Return up to max_out completions in arrival order of their batches; drives one scheduler
+/* Return up to max_out completions in the order of their batches; drives one scheduler
  * iteration first when no library thread runs.  Returns a latched scheduler error if any. */
 int ddh_service_poll(ddh_service *s, ddh_completion *out, int max_out, int *n_out);
 int64_t ddh_service_pending(ddh_service *s); /* queued + running + unreturned frames */

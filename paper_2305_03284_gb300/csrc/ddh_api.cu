@@ -452,6 +452,7 @@ int ddh_set_state(ddh_state* s, const float* r, const float* phi, int64_t frame_
 }
 
 int64_t ddh_frame_index(const ddh_state* s) { return s ? s->frame : -1; }
+void* ddh_state_stream(const ddh_state* s) { return s ? static_cast<void*>(s->stream) : nullptr; }
 
 int ddh_strehl(ddh_state* s, const float* phi_true_dev, float* out) {
   if (s == nullptr || phi_true_dev == nullptr || out == nullptr || !cluster_n(s->prm.n)) return DDH_EINVAL;

@@ -4,8 +4,13 @@
 // budget) own FIFOs of submitted frames.  The thread loops: (1) resolve the oldest in-flight
 // batches whose completion event has fired (completion timestamp, latency from arrival);
 // (2) if fewer than `max_in_flight` batches are on the device, launch one batch holding the
-// next frame of every sensor that has one queued and none on the device (frames n and n+1 of a
-// sensor are dependent).  Host code only: the batch itself is enqueue_batch() of ddh_api.cu.
+// next queued frame of every sensor that has one.  A batch holds at most one frame per sensor;
+// frames n and n+1 of a sensor are dependent, and they may sit in consecutive batches on the
+// device at the same time because every batch runs in order on the service's one stream (a
+// batch's side-stream branches fork from and join back into it).  With max_in_flight = 1 every
+// batch takes all frames that arrived while the previous one ran (continuous batching); a
+// larger value lets small batches slip in behind a large one, which spends a full launch
+// sequence on a few frames.  Host code only: the batch itself is enqueue_batch() of ddh_api.cu.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -41,7 +46,7 @@ struct Sensor {
   ddh_state* state;
   size_t bytes;
   std::deque<Pending> queue;
-  bool in_flight = false;
+  int in_flight = 0;  // frames of this sensor in batches on the device
   bool closing = false;
   int64_t done = 0;
 };
@@ -79,7 +84,7 @@ namespace {
 void reap_locked(ddh_service* s) {
   for (auto it = s->sensors.begin(); it != s->sensors.end();) {
     Sensor* se = it->second;
-    if (se->closing && se->queue.empty() && !se->in_flight) {
+    if (se->closing && se->queue.empty() && se->in_flight == 0) {
       ddh_free(se->state);
       s->used -= se->bytes;
       delete se;
@@ -101,7 +106,7 @@ int service_step(ddh_service* s) {
     const double t = now_s();
     for (auto& it : b.items) {
       Sensor* se = it.first;
-      se->in_flight = false;
+      se->in_flight -= 1;
       se->done += 1;
       ddh_completion c{};
       c.tag = it.second.tag;
@@ -121,10 +126,10 @@ int service_step(ddh_service* s) {
   Batch b;
   for (auto& kv : s->sensors) {
     Sensor* se = kv.second;
-    if (se->in_flight || se->queue.empty()) continue;
+    if (se->queue.empty()) continue;
     Pending p = se->queue.front();
     se->queue.pop_front();
-    se->in_flight = true;
+    se->in_flight += 1;
     s->scratch_states.push_back(se->state);
     s->scratch_ys.push_back(p.y);
     b.items.emplace_back(se, p);
@@ -275,7 +280,7 @@ int64_t ddh_service_pending(ddh_service* s) {
   if (s == nullptr) return -1;
   std::lock_guard<std::mutex> lock(s->mu);
   int64_t n = static_cast<int64_t>(s->completed.size());
-  for (auto& kv : s->sensors) n += static_cast<int64_t>(kv.second->queue.size()) + (kv.second->in_flight ? 1 : 0);
+  for (auto& kv : s->sensors) n += static_cast<int64_t>(kv.second->queue.size()) + kv.second->in_flight;
   return n;
 }
 

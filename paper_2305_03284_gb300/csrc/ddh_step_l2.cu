@@ -3,12 +3,19 @@
 // sequence of batched kernels (blockIdx.y = stream of the batch) over per-stream global
 // scratch that stays resident in the 129 MB L2 between stages:
 //   s1 row statistics (Normalize, Eq. 4) and tip/tilt sums        (16 rows per block)
-//   s2 combine; RemoveTipTilt, prologue a e^{-j phi'} y~, row IFFT; transposed store
-//   s3 column IFFT, r-init (Eq. 3) + E-step, column FFT of mu; transposed store (16 cols/block)
-//   s4 row FFT and phase M-step (tile sums when the phase is tiled)
+//   s2 combine; RemoveTipTilt, prologue a e^{-j phi'} y~, row IFFT; transposed store (8 rows)
+//   s3 column IFFT, r-init (Eq. 3) + E-step, column FFT of mu; transposed store (8 cols/block)
+//   s4 row FFT and phase M-step (tile sums when the phase is tiled)  (8 rows per block)
 //   s5 surrogate weights of the E, S, SE, SW pairs; s6 one ICD colour (launched 4 times)
 // Each 1-D DFT is the warp-per-row shared-memory Stockham FFT of the cluster kernel; the
-// transposes go through a 16-row shared-memory tile so that global stores are 128-byte runs.
+// transposes go through an 8-row or 8-column shared-memory tile, so that global accesses are
+// 32- or 64-byte runs.
+// The stages are launched with programmatic stream serialization: each kernel lets its
+// successor launch as soon as all its blocks run, and waits (`griddepcontrol.wait`, every
+// thread, before any read of another stage's output and before any early return) until its
+// predecessor has completed, so that the completion of one stage implies that of all earlier ones.
+#include <utility>
+
 #include "ddh_device.cuh"
 #include "ddh_kernels.cuh"
 
@@ -16,7 +23,11 @@ namespace ddh {
 
 namespace {
 
-constexpr int kT = 16;  // rows (or columns) per block
+constexpr int kT = 16;  // rows per statistics block
+constexpr int kTc = 8;  // columns per column-pass block (one warp per column)
+constexpr int kColThreads = 32 * kTc;
+constexpr int kTr = 8;  // rows per row-pass block (one warp per row)
+constexpr int kRowThreads = 32 * kTr;
 
 __device__ __forceinline__ bool frame_dropped(const L2Stream& S) { return *S.flag != 0; }
 
@@ -27,6 +38,8 @@ __global__ void __launch_bounds__(kThreads) k_l2_stats(const __grid_constant__ L
   const KParams& P = b.prm[blockIdx.y];
   const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
   __shared__ float red[16][8];
+  grid_dep_launch();
+  grid_dep_wait();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rho = kT * blockIdx.x + warp;
   constexpr int PER = N / 32;
@@ -114,15 +127,17 @@ __device__ void l2_combine(const L2Stream& S, const KParams& P, float* g) {
 
 // ---- s2: prologue and row IFFT of the pupil rows; transposed store into fb ------------------
 template <int N, int V>
-__global__ void __launch_bounds__(kThreads) k_l2_rows_inv(const __grid_constant__ L2Batch b, int first) {
+__global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_constant__ L2Batch b, int first) {
   extern __shared__ __align__(128) unsigned char smem[];
   const L2Stream& S = b.st[blockIdx.y];
   const KParams& P = b.prm[blockIdx.y];
   const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* rows = tw + N;  // kT rows x (N + 1)
+  float2* rows = tw + N;  // kTr rows x (N + 1)
   __shared__ float g[8];
-  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = b.tw[i];
+  for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = b.tw[i];
+  grid_dep_launch();
+  grid_dep_wait();
   if (threadIdx.x == 0) {
     if (first) {
       l2_combine<N>(S, P, g);
@@ -145,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_l2_rows_inv(const __grid_constant_
   const float scale = g[2], tx = g[3], ty = g[4];
   const float cc = 0.5f * static_cast<float>(N - 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rho = kT * blockIdx.x + warp;
+  const int rho = kTr * blockIdx.x + warp;
   const int dy2 = ap_dist2(rho, N);
   float2* rb = rows + warp * (N + 1);
   float* pr = S.phi + static_cast<size_t>(rho) * N;
@@ -174,32 +189,34 @@ __global__ void __launch_bounds__(kThreads) k_l2_rows_inv(const __grid_constant_
     }
   }
   __syncthreads();
-  // fb is column-major: fb[x N + rho]; 16 threads write the 16 rows of one column
-  for (int i = threadIdx.x; i < kT * N; i += kThreads) {
-    const int x = i / kT, r = i - x * kT;
-    S.fb[static_cast<size_t>(x) * N + kT * blockIdx.x + r] = rows[r * (N + 1) + swz(x)];
+  // fb is column-major: fb[x N + rho]; 8 threads write the 8 rows of one column
+  for (int i = threadIdx.x; i < kTr * N; i += kRowThreads) {
+    const int x = i / kTr, r = i - x * kTr;
+    S.fb[static_cast<size_t>(x) * N + kTr * blockIdx.x + r] = rows[r * (N + 1) + swz(x)];
   }
 }
 
 // ---- s3: column IFFT, r-init + E-step, column FFT of mu; transposed store into fa ----------
 template <int N, int V>
-__global__ void __launch_bounds__(kThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first) {
+__global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first) {
   extern __shared__ __align__(128) unsigned char smem[];
   const L2Stream& S = b.st[blockIdx.y];
   const KParams& P = b.prm[blockIdx.y];
+  grid_dep_launch();
+  grid_dep_wait();
   if (frame_dropped(S)) return;
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* cols = tw + N;                                        // kT columns x (N + 1)
-  float* rt = reinterpret_cast<float*>(cols + kT * (N + 1));    // kT x (N + 1): r, then r-init
-  float* stile = rt + kT * (N + 1);                             // kT x (N + 1): s
-  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = b.tw[i];
-  const int x0 = kT * blockIdx.x;
-  for (int i = threadIdx.x; i < kT * N; i += kThreads) {
+  float2* cols = tw + N;                                        // kTc columns x (N + 1)
+  float* rt = reinterpret_cast<float*>(cols + kTc * (N + 1));    // kTc x (N + 1): r, then r-init
+  float* stile = rt + kTc * (N + 1);                             // kTc x (N + 1): s
+  for (int i = threadIdx.x; i < N; i += kColThreads) tw[i] = b.tw[i];
+  const int x0 = kTc * blockIdx.x;
+  for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {
     const int c = i / N, rho = i - c * N;
     cols[c * (N + 1) + swz(rho)] = S.fb[static_cast<size_t>(x0 + c) * N + rho];
   }
-  for (int i = threadIdx.x; i < kT * N; i += kThreads) {  // coalesced 64-byte row segments
-    const int rho = i / kT, c = i - rho * kT;
+  for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {  // coalesced 32-byte row segments
+    const int rho = i / kTc, c = i - rho * kTc;
     rt[c * (N + 1) + rho] = S.r[static_cast<size_t>(rho) * N + x0 + c];
   }
   __syncthreads();
@@ -222,8 +239,8 @@ __global__ void __launch_bounds__(kThreads) k_l2_cols(const __grid_constant__ L2
   __syncwarp();
   fft_row<N, -1, V>(cb, tw, lane);
   __syncthreads();
-  for (int i = threadIdx.x; i < kT * N; i += kThreads) {
-    const int rho = i / kT, c = i - rho * kT;
+  for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {
+    const int rho = i / kTc, c = i - rho * kTc;
     const size_t gi = static_cast<size_t>(rho) * N + x0 + c;
     const float ri = rt[c * (N + 1) + rho];
     S.r0[gi] = ri;
@@ -235,21 +252,23 @@ __global__ void __launch_bounds__(kThreads) k_l2_cols(const __grid_constant__ L2
 
 // ---- s4: row FFT of mu and phase M-step ------------------------------------------------------
 template <int N, int V>
-__global__ void __launch_bounds__(kThreads) k_l2_rows_fwd(const __grid_constant__ L2Batch b) {
+__global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_constant__ L2Batch b) {
   extern __shared__ __align__(128) unsigned char smem[];
   const L2Stream& S = b.st[blockIdx.y];
   const KParams& P = b.prm[blockIdx.y];
+  grid_dep_launch();
+  grid_dep_wait();
   if (frame_dropped(S)) return;
   const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
   float2* tw = reinterpret_cast<float2*>(smem);
   float2* rows = tw + N;
-  for (int i = threadIdx.x; i < N; i += kThreads) tw[i] = b.tw[i];
+  for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = b.tw[i];
   const float* st = S.part + 8 * (N / kT);
   const float2 ymean = make_float2(st[0], st[1]);
   const float scale = st[2];
   const int gs = P.g_shift, G = 1 << gs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rho = kT * blockIdx.x + warp;
+  const int rho = kTr * blockIdx.x + warp;
   const int dy2 = ap_dist2(rho, N);
   const bool row_ap = dy2 <= P.ap_lim;
   float2* rb = rows + warp * (N + 1);
@@ -288,6 +307,8 @@ template <int N>
 __global__ void __launch_bounds__(256) k_l2_weights(const __grid_constant__ L2Batch b) {
   const L2Stream& S = b.st[blockIdx.y];
   const KParams& P = b.prm[blockIdx.y];
+  grid_dep_launch();
+  grid_dep_wait();
   if (frame_dropped(S)) return;
   constexpr int M = N * N;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
@@ -307,6 +328,8 @@ template <int N>
 __global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Batch b, int c) {
   const L2Stream& S = b.st[blockIdx.y];
   const KParams& P = b.prm[blockIdx.y];
+  grid_dep_launch();
+  grid_dep_wait();
   if (frame_dropped(S)) return;
   constexpr int M = N * N;
   const int cx = c & 1, cy = c >> 1;
@@ -342,23 +365,44 @@ __global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Bat
 }
 
 template <int N>
-constexpr size_t rows_smem() { return sizeof(float2) * (N + kT * (N + 1)); }
+constexpr size_t rows_smem() { return sizeof(float2) * (N + kTr * (N + 1)); }
 template <int N>
-constexpr size_t cols_smem() { return sizeof(float2) * (N + kT * (N + 1)) + 2 * sizeof(float) * kT * (N + 1); }
+constexpr size_t cols_smem() { return sizeof(float2) * (N + kTc * (N + 1)) + 2 * sizeof(float) * kTc * (N + 1); }
+
+// launch with programmatic stream serialization (the kernel waits for its predecessor itself)
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 template <int N, int V>
 cudaError_t l2_step(const L2Batch& b, int n_k, cudaStream_t st) {
   const dim3 grid(N / kT, b.count), blk(kThreads);
-  const dim3 pgrid(64, b.count);
-  k_l2_stats<N><<<grid, blk, 0, st>>>(b);
-  for (int it = 0; it < n_k; ++it) {
-    k_l2_rows_inv<N, V><<<grid, blk, rows_smem<N>(), st>>>(b, it == 0 ? 1 : 0);
-    k_l2_cols<N, V><<<grid, blk, cols_smem<N>(), st>>>(b, it == 0 ? 1 : 0);
-    k_l2_rows_fwd<N, V><<<grid, blk, rows_smem<N>(), st>>>(b);
-    k_l2_weights<N><<<pgrid, 256, 0, st>>>(b);
-    for (int c = 0; c < 4; ++c) k_l2_colour<N><<<pgrid, 256, 0, st>>>(b, c);
+  const dim3 rgrid(N / kTr, b.count), rblk(kRowThreads);
+  const dim3 cgrid2(N / kTc, b.count), cblk(kColThreads);
+  // pixel kernels: two pixels per thread for the weights, one per thread for a colour
+  const dim3 wgrid(N * N / (2 * 256), b.count), cgrid(N * N / (4 * 256), b.count);
+  cudaError_t e = launch_pdl(k_l2_stats<N>, grid, blk, 0, st, b);
+  for (int it = 0; it < n_k && e == cudaSuccess; ++it) {
+    const int first = it == 0 ? 1 : 0;
+    e = launch_pdl(k_l2_rows_inv<N, V>, rgrid, rblk, rows_smem<N>(), st, b, first);
+    if (e == cudaSuccess) e = launch_pdl(k_l2_cols<N, V>, cgrid2, cblk, cols_smem<N>(), st, b, first);
+    if (e == cudaSuccess) e = launch_pdl(k_l2_rows_fwd<N, V>, rgrid, rblk, rows_smem<N>(), st, b);
+    if (e == cudaSuccess) e = launch_pdl(k_l2_weights<N>, wgrid, dim3(256), 0, st, b);
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c) e = launch_pdl(k_l2_colour<N>, cgrid, dim3(256), 0, st, b, c);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 template <int N, int V>

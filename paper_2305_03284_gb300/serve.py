@@ -5,10 +5,14 @@ caller sets); each keeps its state ``(n, r, phi)`` resident on the device.  Fram
 any time into per-sensor FIFOs.  The scheduler loop repeatedly
 
 1. resolves finished batches (an event per batch), delivering each frame's phase and latency;
-2. forms a batch from every sensor whose next frame has arrived and whose previous frame is not
-   still on the device (frames n and n+1 of one sensor depend on each other), and launches it
-   with ``ddh_step_batch`` without waiting for batches already in flight (up to
-   ``max_in_flight``), so frames that arrive while the GPU works join the next launch.
+2. forms a batch from the next queued frame of every sensor that has one (at most one frame per
+   sensor per batch) and launches it with ``ddh_step_batch`` without waiting for batches
+   already in flight (up to ``max_in_flight``), so frames that arrive while the GPU works join
+   the next launch.  Frames n and n+1 of one sensor depend on each other; they may sit in
+   consecutive batches on the device at once because the batches execute in order on one
+   stream (a backend must keep that order).  The default ``max_in_flight = 1`` is continuous
+   batching proper: each batch takes every frame that arrived while the previous one ran,
+   whereas more slots let small batches slip in behind a large one.
 
 Each sensor's result is independent of which other sensors share its launches (one cluster per
 stream, no cross-stream arithmetic), so a frame's output is the same alone and in the mix.
@@ -47,8 +51,9 @@ class _Sensor:
     params: object
     nbytes: int
     queue: collections.deque = field(default_factory=collections.deque)
-    in_flight: bool = False
+    in_flight: int = 0        # frames in batches on the device
     frames_done: int = 0
+    frames_launched: int = 0
     out_ring: list = field(default_factory=list)
     closing: bool = False
 
@@ -108,7 +113,7 @@ class PerFrameLaunchBackend(LibddhBackend):
 
 class Service:
     def __init__(self, backend=None, mem_budget_bytes: int | None = None, reserve_bytes: int = 1 << 30,
-                 max_in_flight: int = 2, deliver_phase: bool = True, clock=time.perf_counter):
+                 max_in_flight: int = 1, deliver_phase: bool = True, clock=time.perf_counter):
         self.backend = backend if backend is not None else LibddhBackend()
         self.max_in_flight = max_in_flight
         self.deliver_phase = deliver_phase
@@ -181,14 +186,14 @@ class Service:
                 _, items = self._in_flight.popleft()
                 now = self.clock()
                 for s, fut, arrival, slot in items:
-                    s.in_flight = False
+                    s.in_flight -= 1
                     s.frames_done += 1
                     out = s.out_ring[slot] if slot is not None else None
                     fut.set_result(FrameResult(s.sid, s.frames_done, now - arrival, out))
             self._reap()
             if len(self._in_flight) >= self.max_in_flight:
                 return 0
-            ready = [s for s in self._sensors.values() if s.queue and not s.in_flight]
+            ready = [s for s in self._sensors.values() if s.queue]
             if not ready:
                 return 0
             frames, states, items = [], [], []
@@ -196,21 +201,23 @@ class Service:
                 frame, arrival, fut = s.queue.popleft()
                 frames.append(frame)
                 states.append(s.state)
-                s.in_flight = True
+                s.in_flight += 1
                 items.append((s, fut, arrival, None))
             self.backend.step_batch(states, frames)
             if self.deliver_phase:
                 for i, (s, fut, arrival, _) in enumerate(items):
-                    slot = s.frames_done % len(s.out_ring)
+                    slot = s.frames_launched % len(s.out_ring)
                     self.backend.phase(s.state, s.out_ring[slot])
                     items[i] = (s, fut, arrival, slot)
+            for s, *_ in items:
+                s.frames_launched += 1
             self._in_flight.append((self.backend.record(), items))
             self.batches_launched += 1
             self.batch_sizes.append(len(items))
             return len(items)
 
     def _reap(self) -> None:
-        for sid in [k for k, s in self._sensors.items() if s.closing and not s.queue and not s.in_flight]:
+        for sid in [k for k, s in self._sensors.items() if s.closing and not s.queue and s.in_flight == 0]:
             s = self._sensors.pop(sid)
             self.backend.close_state(s.state)
             self._used -= s.nbytes
@@ -263,7 +270,7 @@ class NativeService:
     ``poll``.  ``per_frame_launch=True`` is the comparison mode that launches every frame alone.
     """
 
-    def __init__(self, cuda_stream=None, mem_budget_bytes: int = 0, max_in_flight: int = 2,
+    def __init__(self, cuda_stream=None, mem_budget_bytes: int = 0, max_in_flight: int = 1,
                  per_frame_launch: bool = False):
         import ctypes
         import torch
@@ -298,15 +305,22 @@ class NativeService:
         n = self._sizes[int(sid)]
         out = out if out is not None else self.torch.empty((n, n), dtype=self.torch.float32, device="cuda")
         self._L.check(self._L.lib().ddh_phase(self._ct.c_void_p(st), self._ct.c_void_p(out.data_ptr())))
-        self.torch.cuda.current_stream().wait_stream(self.stream)
+        self._join_state(st)
         return out
+
+    def _join_state(self, st) -> None:
+        # the copy runs on the sensor's stream: order torch's current stream after it
+        sst = self._L.lib().ddh_state_stream(self._ct.c_void_p(st))
+        self.torch.cuda.current_stream().wait_stream(self.torch.cuda.ExternalStream(sst))
 
     def reflectance(self, sid: int, out=None):
         st = self._L.lib().ddh_service_state(self._h, int(sid))
+        if not st:
+            raise KeyError(sid)
         n = self._sizes[int(sid)]
         out = out if out is not None else self.torch.empty((n, n), dtype=self.torch.float32, device="cuda")
         self._L.check(self._L.lib().ddh_reflectance(self._ct.c_void_p(st), self._ct.c_void_p(out.data_ptr())))
-        self.torch.cuda.current_stream().wait_stream(self.stream)
+        self._join_state(st)
         return out
 
     def submit(self, sid: int, frame, arrival_s: float = -1.0, tag: int = 0) -> None:

@@ -63,7 +63,7 @@ def make(**kw):
     return be, svc
 
 
-def test_fifo_per_sensor_and_one_frame_in_flight():
+def test_fifo_per_sensor_and_one_frame_per_sensor_per_batch():
     be, svc = make(latency_polls=3)
     svc.admit("a", Params(64))
     svc.admit("b", Params(128))
@@ -89,9 +89,28 @@ def test_frames_arriving_while_a_batch_runs_join_the_next_launch():
     svc.submit("c", "c0")
     assert svc.poll() == 2            # batch 2 launched while batch 1 still runs: {b, c}
     svc.submit("a", "a1")
-    assert svc.poll() == 0            # a is in flight, and two batches are in flight
+    assert svc.poll() == 0            # two batches are in flight
     svc.drain()
     assert be.batches == [["a0"], ["b0", "c0"], ["a1"]]
+
+
+def test_next_frame_of_a_sensor_joins_the_next_batch_while_its_previous_runs():
+    be, svc = make(latency_polls=5, max_in_flight=3)
+    svc.admit("a", Params(64))
+    svc.admit("b", Params(64))
+    fa = [svc.submit("a", "a0"), svc.submit("a", "a1")]
+    assert svc.poll() == 1            # {a0}: one frame per sensor per batch
+    assert svc.poll() == 1            # {a1} launched while a0 still runs (batches run in order)
+    fb = svc.submit("b", "b0")
+    fa.append(svc.submit("a", "a2"))
+    assert svc.poll() == 2            # {a2, b0}
+    assert svc.poll() == 0            # three batches in flight
+    svc.drain()
+    assert be.batches == [["a0"], ["a1"], ["a2", "b0"]]
+    assert svc.state("a").frames == ["a0", "a1", "a2"]
+    assert [f.result().frame_index for f in fa] == [1, 2, 3]
+    assert [f.result().phase for f in fa] == ["out0", "out1", "out2"]
+    assert fb.result().frame_index == 1
 
 
 def test_admission_by_budget_and_release():
