@@ -161,10 +161,10 @@ int ddh_step_backward_noalloc(ddh_state *s, const void *y_c64_dev, const float *
  * are queued per sensor; a scheduler (a library thread after ddh_service_start, or each
  * ddh_service_poll call otherwise) resolves finished batches and launches the next queued
  * frame of every sensor that has one, as one ddh_step_batch, without waiting for batches still
- * running (at most `max_in_flight`; 1 gives continuous batching: each batch takes every frame
- * that arrived while the previous one ran).  A batch holds at most one frame per sensor; a
- * sensor's next frame may go into a later batch while its previous one still runs, since
- * batches execute in order on the service's stream.  A sensor's results do not depend on which
+ * running (at most `max_in_flight`; a batch starts behind a running one only if it holds at
+ * least half of the admitted sensors).  A batch holds at most one frame per sensor; a sensor's
+ * next frame may go into a later batch while its previous one still runs, since batches
+ * execute in order on the service's stream.  A sensor's results do not depend on which
  * other sensors share its launches.  The paper has a frame loop per sensor
  * (Fig. 1); the multi-sensor service around it is this library's. */
 #define DDH_SERVICE_PER_FRAME_LAUNCH 1u /* comparison mode: one ddh_step launch per frame */

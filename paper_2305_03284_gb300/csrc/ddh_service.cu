@@ -7,10 +7,12 @@
 // next queued frame of every sensor that has one.  A batch holds at most one frame per sensor;
 // frames n and n+1 of a sensor are dependent, and they may sit in consecutive batches on the
 // device at the same time because every batch runs in order on the service's one stream (a
-// batch's side-stream branches fork from and join back into it).  With max_in_flight = 1 every
-// batch takes all frames that arrived while the previous one ran (continuous batching); a
-// larger value lets small batches slip in behind a large one, which spends a full launch
-// sequence on a few frames.  Host code only: the batch itself is enqueue_batch() of ddh_api.cu.
+// batch's side-stream branches fork from and join back into it).  A batch may start behind a
+// running one only if it holds at least half of the sensors: under a backlog the device then
+// never idles between batches, while light traffic still collects every frame that arrived
+// during the running batch into the next one (small batches behind a large one would each
+// spend a full launch sequence on a few frames).  Host code only: the batch itself is
+// enqueue_batch() of ddh_api.cu.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -121,6 +123,13 @@ int service_step(ddh_service* s) {
   }
   reap_locked(s);
   if (static_cast<int>(s->in_flight.size()) >= s->max_in_flight) return 0;
+  int ready = 0;
+  for (auto& kv : s->sensors) ready += kv.second->queue.empty() ? 0 : 1;
+  if (ready == 0) return 0;
+  // behind a running batch only a batch of at least half of the sensors goes out: under a
+  // backlog the device never waits for the scheduler, and no launch sequence is spent on a
+  // few frames that would otherwise join the next full batch
+  if (!s->in_flight.empty() && 2 * ready < static_cast<int>(s->sensors.size())) return 0;
   s->scratch_states.clear();
   s->scratch_ys.clear();
   Batch b;

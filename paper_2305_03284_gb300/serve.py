@@ -10,9 +10,9 @@ any time into per-sensor FIFOs.  The scheduler loop repeatedly
    already in flight (up to ``max_in_flight``), so frames that arrive while the GPU works join
    the next launch.  Frames n and n+1 of one sensor depend on each other; they may sit in
    consecutive batches on the device at once because the batches execute in order on one
-   stream (a backend must keep that order).  The default ``max_in_flight = 1`` is continuous
-   batching proper: each batch takes every frame that arrived while the previous one ran,
-   whereas more slots let small batches slip in behind a large one.
+   stream (a backend must keep that order).  A batch starts behind a running one only if it
+   holds at least half of the sensors, so that a backlog keeps the device busy while light
+   traffic still gathers into full batches.
 
 Each sensor's result is independent of which other sensors share its launches (one cluster per
 stream, no cross-stream arithmetic), so a frame's output is the same alone and in the mix.
@@ -113,7 +113,7 @@ class PerFrameLaunchBackend(LibddhBackend):
 
 class Service:
     def __init__(self, backend=None, mem_budget_bytes: int | None = None, reserve_bytes: int = 1 << 30,
-                 max_in_flight: int = 1, deliver_phase: bool = True, clock=time.perf_counter):
+                 max_in_flight: int = 2, deliver_phase: bool = True, clock=time.perf_counter):
         self.backend = backend if backend is not None else LibddhBackend()
         self.max_in_flight = max_in_flight
         self.deliver_phase = deliver_phase
@@ -196,6 +196,8 @@ class Service:
             ready = [s for s in self._sensors.values() if s.queue]
             if not ready:
                 return 0
+            if self._in_flight and 2 * len(ready) < len(self._sensors):
+                return 0          # behind a running batch only a batch of half the sensors
             frames, states, items = [], [], []
             for s in ready:
                 frame, arrival, fut = s.queue.popleft()
@@ -270,7 +272,7 @@ class NativeService:
     ``poll``.  ``per_frame_launch=True`` is the comparison mode that launches every frame alone.
     """
 
-    def __init__(self, cuda_stream=None, mem_budget_bytes: int = 0, max_in_flight: int = 1,
+    def __init__(self, cuda_stream=None, mem_budget_bytes: int = 0, max_in_flight: int = 2,
                  per_frame_launch: bool = False):
         import ctypes
         import torch

@@ -148,3 +148,17 @@ def test_drive_replays_arrivals_and_reports_latency():
     for s in range(4):
         assert svc.state(s).frames == [(s, k) for k in range(5)]
     assert max(svc.batch_sizes) > 1   # frames of different sensors shared launches
+
+
+def test_a_batch_behind_a_running_one_needs_half_of_the_sensors():
+    be, svc = make(latency_polls=5, max_in_flight=2)
+    for x in "abcd":
+        svc.admit(x, Params(64))
+    svc.submit("a", "a0")
+    assert svc.poll() == 1            # nothing in flight: any batch goes
+    svc.submit("a", "a1")
+    assert svc.poll() == 0            # 1 of 4 sensors ready behind a running batch: wait
+    svc.submit("b", "b0")
+    assert svc.poll() == 2            # 2 of 4: {a1, b0}
+    svc.drain()
+    assert be.batches == [["a0"], ["a1", "b0"]]
