@@ -57,6 +57,23 @@ def dist_info():
 
 
 # ----------------------------------------------------------------------------- helpers
+def max_over_ranks(values, device):
+    """Element-wise maximum of `values` over all ranks: the job takes as long as its slowest
+    rank (one process per GPU; a plain barrier-and-reduce, no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_throughput(steps_per_rank, world, max_ms):
+    """Frames per second of the whole job: every rank advances its own stream by
+    `steps_per_rank` frames (weak scaling), timed by the slowest rank."""
+    return steps_per_rank * world / (max_ms * 1e-3)
+
+
 def measured_peak_gbs():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -398,14 +415,10 @@ def run_ours(args):
         t_e2e = time.perf_counter() - t0
         barrier()
 
-    tmax = torch.tensor([ms, t_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-    ms, t_e2e = float(tmax[0]), float(tmax[1])
+    ms, t_e2e = max_over_ranks([ms, t_e2e], "cuda")
     if rank != 0:
         return
-    frames = args.steps * world
-    value = frames / (ms * 1e-3)
+    value = job_throughput(args.steps, world, ms)
     lat.sort()
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
