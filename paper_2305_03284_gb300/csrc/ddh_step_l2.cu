@@ -39,7 +39,6 @@ __global__ void __launch_bounds__(kThreads) k_l2_stats(const __grid_constant__ L
   const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
   __shared__ float red[16][8];
   grid_dep_launch();
-  grid_dep_wait();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rho = kT * blockIdx.x + warp;
   constexpr int PER = N / 32;
@@ -59,6 +58,9 @@ __global__ void __launch_bounds__(kThreads) k_l2_stats(const __grid_constant__ L
 #pragma unroll
   for (int j = 0; j < PER; ++j) q += c_abs2(c_sub(v[j], m));
   q = warp_sum(q);
+  // the frame's statistics above do not depend on the previous stage; phi and the
+  // statistics buffers below do
+  grid_dep_wait();
   float txs = 0.f, txc = 0.f, tys = 0.f, tyc = 0.f;
   if (P.tilt_mode) {
     const float* pr = S.phi + static_cast<size_t>(rho) * N;
@@ -189,10 +191,12 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
     }
   }
   __syncthreads();
-  // fb is column-major: fb[x N + rho]; 8 threads write the 8 rows of one column
+  // fb is column-major: fb[x N + rho]; 8 threads write the 8 rows of one column.  Rows outside
+  // the aperture are zero and are not stored: the column pass fills them in itself.
   for (int i = threadIdx.x; i < kTr * N; i += kRowThreads) {
     const int x = i / kTr, r = i - x * kTr;
-    S.fb[static_cast<size_t>(x) * N + kTr * blockIdx.x + r] = rows[r * (N + 1) + swz(x)];
+    if (ap_dist2(kTr * blockIdx.x + r, N) <= P.ap_lim)
+      S.fb[static_cast<size_t>(x) * N + kTr * blockIdx.x + r] = rows[r * (N + 1) + swz(x)];
   }
 }
 
@@ -213,7 +217,8 @@ __global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__
   const int x0 = kTc * blockIdx.x;
   for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {
     const int c = i / N, rho = i - c * N;
-    cols[c * (N + 1) + swz(rho)] = S.fb[static_cast<size_t>(x0 + c) * N + rho];
+    cols[c * (N + 1) + swz(rho)] =
+        ap_dist2(rho, N) <= P.ap_lim ? S.fb[static_cast<size_t>(x0 + c) * N + rho] : make_float2(0.f, 0.f);
   }
   for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {  // coalesced 32-byte row segments
     const int rho = i / kTc, c = i - rho * kTc;
