@@ -135,7 +135,10 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
   const KParams& P = b.prm[blockIdx.y];
   const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* rows = tw + N;  // kTr rows x (N + 1)
+  // row tile with stride N + 4: the transposed accesses (8 rows x 4 columns per warp) hit
+  // 16 bank pairs
+  constexpr int RW = N + 4;
+  float2* rows = tw + N;  // kTr rows x RW
   __shared__ float g[8];
   for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = b.tw[i];
   grid_dep_launch();
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rho = kTr * blockIdx.x + warp;
   const int dy2 = ap_dist2(rho, N);
-  float2* rb = rows + warp * (N + 1);
+  float2* rb = rows + warp * RW;
   float* pr = S.phi + static_cast<size_t>(rho) * N;
   if (dy2 <= P.ap_lim) {
     const float tyr = ty * (static_cast<float>(rho) - cc);
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
   for (int i = threadIdx.x; i < kTr * N; i += kRowThreads) {
     const int x = i / kTr, r = i - x * kTr;
     if (ap_dist2(kTr * blockIdx.x + r, N) <= P.ap_lim)
-      S.fb[static_cast<size_t>(x) * N + kTr * blockIdx.x + r] = rows[r * (N + 1) + swz(x)];
+      S.fb[static_cast<size_t>(x) * N + kTr * blockIdx.x + r] = rows[r * RW + swz(x)];
   }
 }
 
@@ -210,25 +213,28 @@ __global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__
   grid_dep_wait();
   if (frame_dropped(S)) return;
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* cols = tw + N;                                        // kTc columns x (N + 1)
-  float* rt = reinterpret_cast<float*>(cols + kTc * (N + 1));    // kTc x (N + 1): r, then r-init
-  float* stile = rt + kTc * (N + 1);                             // kTc x (N + 1): s
+  // column tiles with stride N + 4: the transposed accesses (8 columns x 4 rows per warp) hit
+  // 32 distinct banks (16 bank pairs for the complex tile)
+  constexpr int CW = N + 4;
+  float2* cols = tw + N;                                    // kTc columns x CW
+  float* rt = reinterpret_cast<float*>(cols + kTc * CW);    // kTc x CW: r, then r-init
+  float* stile = rt + kTc * CW;                             // kTc x CW: s
   for (int i = threadIdx.x; i < N; i += kColThreads) tw[i] = b.tw[i];
   const int x0 = kTc * blockIdx.x;
   for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {
     const int c = i / N, rho = i - c * N;
-    cols[c * (N + 1) + swz(rho)] =
+    cols[c * CW + swz(rho)] =
         ap_dist2(rho, N) <= P.ap_lim ? S.fb[static_cast<size_t>(x0 + c) * N + rho] : make_float2(0.f, 0.f);
   }
   for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {  // coalesced 32-byte row segments
     const int rho = i / kTc, c = i - rho * kTc;
-    rt[c * (N + 1) + rho] = S.r[static_cast<size_t>(rho) * N + x0 + c];
+    rt[c * CW + rho] = S.r[static_cast<size_t>(rho) * N + x0 + c];
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* cb = cols + warp * (N + 1);
-  float* rc = rt + warp * (N + 1);
-  float* sc = stile + warp * (N + 1);
+  float2* cb = cols + warp * CW;
+  float* rc = rt + warp * CW;
+  float* sc = stile + warp * CW;
   fft_row<N, +1, V>(cb, tw, lane);
   const float invN = 1.f / static_cast<float>(N);
   for (int rho = lane; rho < N; rho += 32) {
@@ -247,11 +253,11 @@ __global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__
   for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {
     const int rho = i / kTc, c = i - rho * kTc;
     const size_t gi = static_cast<size_t>(rho) * N + x0 + c;
-    const float ri = rt[c * (N + 1) + rho];
+    const float ri = rt[c * CW + rho];
     S.r0[gi] = ri;
     S.r[gi] = ri;  // the ICD sweep starts from r-init
-    S.s[gi] = stile[c * (N + 1) + rho];
-    if (ap_dist2(rho, N) <= P.ap_lim) S.fa[gi] = cols[c * (N + 1) + swz(rho)];
+    S.s[gi] = stile[c * CW + rho];
+    if (ap_dist2(rho, N) <= P.ap_lim) S.fa[gi] = cols[c * CW + swz(rho)];
   }
 }
 
@@ -266,7 +272,10 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_consta
   if (frame_dropped(S)) return;
   const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
   float2* tw = reinterpret_cast<float2*>(smem);
-  float2* rows = tw + N;
+  // row tile with stride N + 4: the transposed accesses (8 rows x 4 columns per warp) hit
+  // 16 bank pairs
+  constexpr int RW = N + 4;
+  float2* rows = tw + N;  // kTr rows x RW
   for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = b.tw[i];
   const float* st = S.part + 8 * (N / kT);
   const float2 ymean = make_float2(st[0], st[1]);
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_consta
   const int rho = kTr * blockIdx.x + warp;
   const int dy2 = ap_dist2(rho, N);
   const bool row_ap = dy2 <= P.ap_lim;
-  float2* rb = rows + warp * (N + 1);
+  float2* rb = rows + warp * RW;
   if (row_ap)
     for (int x = lane; x < N; x += 32) rb[swz(x)] = S.fa[static_cast<size_t>(rho) * N + x];
   __syncthreads();
@@ -300,8 +309,8 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_consta
   float* pr = S.phi + static_cast<size_t>(rho) * N;
   for (int x = lane; x < N; x += 32) {
     if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
-      float2 v = rows[l0 * (N + 1) + swz(x)];
-      for (int j = 1; j < G; ++j) v = c_add(v, rows[(l0 + j) * (N + 1) + swz(x)]);
+      float2 v = rows[l0 * RW + swz(x)];
+      for (int j = 1; j < G; ++j) v = c_add(v, rows[(l0 + j) * RW + swz(x)]);
       if (v.x != 0.f || v.y != 0.f) pr[x] = atan2f(v.y, v.x);  // else phi' is kept
     }
   }
@@ -370,9 +379,9 @@ __global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Bat
 }
 
 template <int N>
-constexpr size_t rows_smem() { return sizeof(float2) * (N + kTr * (N + 1)); }
+constexpr size_t rows_smem() { return sizeof(float2) * (N + kTr * (N + 4)); }
 template <int N>
-constexpr size_t cols_smem() { return sizeof(float2) * (N + kTc * (N + 1)) + 2 * sizeof(float) * kTc * (N + 1); }
+constexpr size_t cols_smem() { return sizeof(float2) * (N + kTc * (N + 4)) + 2 * sizeof(float) * kTc * (N + 4); }
 
 // launch with programmatic stream serialization (the kernel waits for its predecessor itself)
 template <typename... Params, typename... Args>
