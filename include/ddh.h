@@ -84,6 +84,19 @@ size_t ddh_trace_floats(int n);
  * The device staging buffer is owned by the state. */
 int ddh_step_host(ddh_state *s, const void *y_c64_host, float *phi_host_out);
 
+/* Pipelined form of ddh_step_host: enqueues the frame's copy in (on a library copy stream,
+ * into one of two device staging slots), the step, and the copy of phi out, and returns at
+ * once with `*ticket` = this frame's sequence number on the state, so that frame n+1's copy in
+ * overlaps frame n's step.  Both host buffers should be pinned (pageable memory makes the
+ * copies synchronous) and stay untouched until ddh_host_wait(s, ticket) or ddh_sync(s)
+ * returns.  Errors latched by the step (non-finite frame, timeout) surface at ddh_sync.
+ * Steps of one state must not be enqueued from several threads at once.  The paper has no
+ * counterpart (it describes a frame loop, not its host interface). */
+int ddh_step_host_async(ddh_state *s, const void *y_c64_host, float *phi_host_out, int64_t *ticket);
+/* Block until frame `ticket` of ddh_step_host_async has its phi in host memory (DDH_EINVAL
+ * for a ticket not issued on s). */
+int ddh_host_wait(ddh_state *s, int64_t ticket);
+
 /* WriteData (Fig. 1): stream-ordered copy of phi_n / r_n (N*N float32) into `out`, which may
  * be device or host memory (host copies synchronise the stream and report latched errors). */
 int ddh_phase(const ddh_state *s, float *out);

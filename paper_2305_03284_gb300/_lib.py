@@ -64,6 +64,8 @@ _SIGS = {
     "ddh_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
     "ddh_frame_index": (c_int64, [c_void_p]),
     "ddh_state_stream": (c_void_p, [c_void_p]),
+    "ddh_step_host_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ddh_host_wait": (c_int, [c_void_p, c_int64]),
     "ddh_strehl": (c_int, [c_void_p, c_void_p, POINTER(c_float)]),
     "ddh_step_batch": (c_int, [POINTER(c_void_p), POINTER(c_void_p), c_int]),
     "ddh_batch_create": (c_int, [POINTER(c_void_p), POINTER(c_void_p), c_int]),

@@ -30,6 +30,15 @@ struct ddh_state {
   const float2* tw;
   int64_t frame;
   int64_t ap_count;
+  // pipelined host-buffer steps (ddh_step_host_async), set up on first use: two device staging
+  // slots (ystage and hstage2) filled on a copy-in stream, events that order a slot's copy
+  // before its step and the step before the slot's next copy, and a ring of completion events
+  cudaStream_t cin = nullptr;
+  float2* hstage2 = nullptr;
+  cudaEvent_t ev_in[2] = {};
+  cudaEvent_t ev_used[2] = {};
+  cudaEvent_t ev_done[8] = {};
+  int64_t hcount = 0;
 };
 
 namespace {
@@ -417,6 +426,51 @@ int ddh_step_trace(ddh_state* s, const void* y, float* trace) {
   return enqueue(s, y, trace);
 }
 
+static int host_async_setup(ddh_state* s) {
+  if (s->cin != nullptr) return DDH_OK;
+  int prio = 0;
+  DDH_CUDA(cudaStreamGetPriority(s->stream, &prio));
+  DDH_CUDA(cudaMalloc(&s->hstage2, 2 * image_bytes(s->prm.n)));
+  for (int i = 0; i < 2; ++i) {
+    DDH_CUDA(cudaEventCreateWithFlags(&s->ev_in[i], cudaEventDisableTiming));
+    DDH_CUDA(cudaEventCreateWithFlags(&s->ev_used[i], cudaEventDisableTiming));
+  }
+  for (cudaEvent_t& e : s->ev_done) DDH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  DDH_CUDA(cudaStreamCreateWithPriority(&s->cin, cudaStreamNonBlocking, prio));
+  return DDH_OK;
+}
+
+int ddh_step_host_async(ddh_state* s, const void* y_host, float* phi_host_out, int64_t* ticket) {
+  if (s == nullptr || y_host == nullptr || phi_host_out == nullptr || ticket == nullptr) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  int rc = host_async_setup(s);
+  if (rc != DDH_OK) return rc;
+  const size_t img = image_bytes(s->prm.n);
+  const int slot = static_cast<int>(s->hcount & 1);
+  float2* stage = slot == 0 ? s->ystage : s->hstage2;
+  // the copy into a slot waits for the step that read it last (frame hcount - 2)
+  DDH_CUDA(cudaStreamWaitEvent(s->cin, s->ev_used[slot], 0));
+  DDH_CUDA(cudaMemcpyAsync(stage, y_host, 2 * img, cudaMemcpyHostToDevice, s->cin));
+  DDH_CUDA(cudaEventRecord(s->ev_in[slot], s->cin));
+  DDH_CUDA(cudaStreamWaitEvent(s->stream, s->ev_in[slot], 0));
+  rc = enqueue(s, stage, nullptr);
+  if (rc != DDH_OK) return rc;
+  DDH_CUDA(cudaEventRecord(s->ev_used[slot], s->stream));
+  // phi leaves on the state's stream, before the next step can overwrite it
+  DDH_CUDA(cudaMemcpyAsync(phi_host_out, s->phi, img, cudaMemcpyDeviceToHost, s->stream));
+  DDH_CUDA(cudaEventRecord(s->ev_done[s->hcount & 7], s->stream));
+  *ticket = s->hcount++;
+  return DDH_OK;
+}
+
+int ddh_host_wait(ddh_state* s, int64_t ticket) {
+  if (s == nullptr || ticket < 0 || ticket >= s->hcount) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  // the slot holds this frame's event or a later frame's, which completes after it
+  DDH_CUDA(cudaEventSynchronize(s->ev_done[ticket & 7]));
+  return DDH_OK;
+}
+
 int ddh_step_host(ddh_state* s, const void* y_host, float* phi_host_out) {
   if (s == nullptr || y_host == nullptr || phi_host_out == nullptr) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(s->device));
@@ -695,6 +749,16 @@ int ddh_free(ddh_state* s) {
   cudaFree(s->ystage);
   cudaFree(s->scalar);
   cudaFree(s->l2scratch);
+  if (s->cin != nullptr) {
+    cudaStreamSynchronize(s->cin);
+    cudaStreamDestroy(s->cin);
+    cudaFree(s->hstage2);
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(s->ev_in[i]);
+      cudaEventDestroy(s->ev_used[i]);
+    }
+    for (cudaEvent_t e : s->ev_done) cudaEventDestroy(e);
+  }
   delete s;
   return DDH_OK;
 }

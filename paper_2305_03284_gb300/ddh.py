@@ -6,7 +6,7 @@ library's kernels.  Frames are complex64 ``(N, N)`` CUDA tensors, phase and refl
 from __future__ import annotations
 
 import ctypes
-from ctypes import byref, c_float, c_void_p
+from ctypes import byref, c_float, c_int64, c_void_p
 
 import torch
 
@@ -76,6 +76,23 @@ class Stream:
             raise ValueError("bad host frame")
         _check_image(phi_out, self.n)
         check(lib().ddh_step_host(self._h, c_void_p(y_host.data_ptr()), c_void_p(phi_out.data_ptr())))
+
+    def step_host_async(self, y_host: torch.Tensor, phi_out: torch.Tensor) -> int:
+        """Pipelined host step: enqueues copy in, step and copy out and returns a ticket at
+        once; both (pinned) tensors stay untouched until ``host_wait(ticket)`` or ``sync()``."""
+        if y_host.is_cuda or phi_out.is_cuda:
+            raise ValueError("step_host_async takes host tensors")
+        if y_host.dtype != torch.complex64 or tuple(y_host.shape) != (self.n, self.n) or not y_host.is_contiguous():
+            raise ValueError("bad host frame")
+        _check_image(phi_out, self.n)
+        t = c_int64()
+        check(lib().ddh_step_host_async(self._h, c_void_p(y_host.data_ptr()), c_void_p(phi_out.data_ptr()),
+                                        ctypes.byref(t)))
+        return t.value
+
+    def host_wait(self, ticket: int) -> None:
+        """Block until frame ``ticket`` of ``step_host_async`` has its phase in host memory."""
+        check(lib().ddh_host_wait(self._h, int(ticket)))
 
     # -- WriteData --------------------------------------------------------------------
     def phase(self, out: torch.Tensor | None = None) -> torch.Tensor:

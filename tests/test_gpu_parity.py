@@ -303,6 +303,31 @@ def test_step_host_equals_device(ddh):
     assert b.frame_index == 3
 
 
+@pytest.mark.parametrize("n", [64, 256])
+def test_pipelined_host_steps_equal_device_steps(ddh, n):
+    """ddh_step_host_async: every frame's phase arrives in its own pinned buffer, equal to the
+    device-resident steps bitwise, with several frames in flight."""
+    cfg = sy.config_single_64() if n == 64 else sy.config_single_256(frames=10)
+    st, ys, ph, p = make(ddh, cfg, 10)
+    a, b = ddh.Stream(p), ddh.Stream(p)
+    hy = [torch.from_numpy(y).pin_memory() for y in ys]
+    outs = [torch.full((n, n), -7.0, dtype=torch.float32).pin_memory() for _ in range(10)]
+    tickets = [b.step_host_async(hy[i], outs[i]) for i in range(6)]
+    b.host_wait(tickets[1])
+    tickets += [b.step_host_async(hy[i], outs[i]) for i in range(6, 10)]
+    assert tickets == list(range(10))
+    b.host_wait(tickets[9])
+    b.sync()
+    for i in range(10):
+        a.step(cu(ys[i]))
+        assert torch.equal(a.phase().cpu(), outs[i]), i
+    assert b.frame_index == 10
+    with pytest.raises(ddh.DdhError):
+        b.host_wait(10)          # not issued
+    with pytest.raises(ddh.DdhError):
+        b.host_wait(-1)
+
+
 def test_checkpoint_roundtrip(ddh):
     cfg = sy.config_single_64()
     st, ys, ph, p = make(ddh, cfg, 6)
