@@ -41,7 +41,8 @@ typedef struct ddh_params {
   float aperture_diam;  /* pupil diameter in px, 0 < d <= N */
   float lambda;         /* Eq. 3 weight of the back-projection term (paper: 0.45) */
   float alpha;          /* Eq. 3 scale of |A^H y|^2 (paper: 0.025) */
-  int n_k;              /* EM iterations per frame, 1..16 (paper: 1) */
+  int n_k;              /* EM iterations per frame, 1..1024 (paper: 1; the static DH-MBIR mode
+                           uses one bootstrap period, 200 in the paper) */
   float noise_var;      /* sigma^2 of the noise after Normalize (> 0) */
   float prior_p;        /* q-GGMRF shape p, 1 <= p < 2 */
   float prior_q;        /* q-GGMRF shape q; must be 2 (finite surrogate weight at 0) */
@@ -60,6 +61,14 @@ typedef struct ddh_state ddh_state; /* opaque; owned by the library */
  * pupil fill fraction, prior p 1.1, q 2, T 1, sigma_r 0.1, r_floor 1e-10, tilt_mode 1,
  * phase_block 1. */
 int ddh_default_params(ddh_params *p, int n, float aperture_diam, float snr);
+
+/* Static DH-MBIR (Sec. 3: EM iterated on one frame, the reflectance reset to a back-projected
+ * estimate every `reset_every` iterations) is the frame step with lambda = 1, alpha = 1,
+ * n_k = reset_every and tilt_mode = 0: each ddh_step on the same frame then resets
+ * r = |A_phi^H y~|^2 with the current phase (Eq. 3 with lambda = alpha = 1) and runs one
+ * bootstrap period of EM iterations; phi carries over.  This fills `p` with those values on
+ * top of ddh_default_params. */
+int ddh_static_params(ddh_params *p, int n, float aperture_diam, float snr, int reset_every);
 
 /* Validate `p`, allocate the device state (r = 0, phi = 0, n = 0: Fig. 1 first line) and bind
  * it to `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The library owns

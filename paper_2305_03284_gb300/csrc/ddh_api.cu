@@ -135,7 +135,7 @@ int validate(const ddh_params* p) {
   if (p == nullptr || !supported_n(p->n)) return DDH_EINVAL;
   if (!(p->aperture_diam > 0.f && p->aperture_diam <= static_cast<float>(p->n))) return DDH_EINVAL;
   if (!(p->lambda >= 0.f && p->lambda <= 1.f && p->alpha >= 0.f && std::isfinite(p->alpha))) return DDH_EINVAL;
-  if (p->n_k < 1 || p->n_k > 16) return DDH_EINVAL;
+  if (p->n_k < 1 || p->n_k > 1024) return DDH_EINVAL;
   if (!(p->noise_var > 0.f && std::isfinite(p->noise_var))) return DDH_EINVAL;
   if (!(p->prior_p >= 1.f && p->prior_p < 2.f)) return DDH_EINVAL;
   if (p->prior_q != 2.f) return DDH_EINVAL;
@@ -378,6 +378,17 @@ int ddh_default_params(ddh_params* p, int n, float aperture_diam, float snr) {
   p->r_floor = 1e-10f;
   p->tilt_mode = 1;
   p->phase_block = 1;
+  return DDH_OK;
+}
+
+int ddh_static_params(ddh_params* p, int n, float aperture_diam, float snr, int reset_every) {
+  const int rc = ddh_default_params(p, n, aperture_diam, snr);
+  if (rc != DDH_OK) return rc;
+  if (reset_every < 1 || reset_every > 1024) return DDH_EINVAL;
+  p->lambda = 1.f;
+  p->alpha = 1.f;
+  p->n_k = reset_every;
+  p->tilt_mode = 0;
   return DDH_OK;
 }
 

@@ -129,6 +129,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     }
   }
   for (int i = tid; i < N; i += kThreads) tw[i] = batch.tw[i];
+  // the grid's outer halo columns have no neighbour to fill them; the ICD still multiplies
+  // them by a zero weight, which must not meet stale NaN or Inf bits in shared memory
+  if (k == 0)
+    for (int i = tid; i < N; i += kThreads) hl[i] = 0.f;
+  if (k == C - 1)
+    for (int i = tid; i < N; i += kThreads) hr[i] = 0.f;
   // bounded wait: on expiry the frame is dropped (flag carried into the B1 statistics)
   const bool loaded = mbar_wait_bounded(mbar, 0, 1u << 22);
   __syncthreads();

@@ -24,6 +24,20 @@ def default_params(n: int, aperture_diam: float, snr: float, /, **overrides) -> 
     return p
 
 
+def static_params(n: int, aperture_diam: float, snr: float, reset_every: int = 200, /, **overrides) -> DdhParams:
+    """Parameters of static DH-MBIR (Sec. 3) on top of the frame step: lambda = alpha = 1,
+    n_k = ``reset_every``, no tip/tilt removal.  Each ``Stream.step`` on the same frame is then
+    one bootstrap period: r reset to ``|A_phi^H y~|^2`` with the current phase, followed by
+    ``reset_every`` EM iterations (the paper resets every 200)."""
+    p = DdhParams()
+    check(lib().ddh_static_params(byref(p), int(n), float(aperture_diam), float(snr), int(reset_every)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
 def _stream_handle(stream) -> c_void_p:
     if stream is None:
         stream = torch.cuda.current_stream()

@@ -381,6 +381,30 @@ def test_argument_errors(ddh):
             ddh.Stream(q)
 
 
+# ------------------------------------------------------------------- static DH-MBIR mode
+@pytest.mark.parametrize("reset_every,cycles,block", [(10, 1, 1), (200, 1, 2), (50, 2, 2)])
+def test_static_mode_parity_64(ddh, reset_every, cycles, block):
+    """Static DH-MBIR (Sec. 3) through the frame step: EM iterated on one frame, r reset to
+    the back-projection every `reset_every` iterations (each step is one bootstrap period).
+    With the per-pixel phase the static iteration first amplifies perturbations (~20x within
+    ~50 iterations on the FP64 oracle itself), so it is compared within that horizon; with
+    tiled phase the full 200-iteration period and two shorter periods in a row."""
+    cfg = sy.config_single_64()
+    st, ys, ph, _ = make(ddh, cfg, 2)
+    p = ddh.static_params(cfg.n, cfg.aperture_diam, cfg.snr, reset_every, phase_block=block)
+    assert (p.n_k, p.tilt_mode) == (reset_every, 0) and p.lam == 1.0 and p.alpha == 1.0
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    s = ddh.Stream(p)
+    ost = o.init_state(cfg.n)
+    for _ in range(cycles):
+        s.step(cu(ys[1]))
+        ost, _ = o.step(ost, ys[1], prm)
+    e = (rel_l2_phase(np32(s.phase()), ost.phi, a), rel_l2(np32(s.reflectance()), ost.r))
+    print(f"static mode, {cycles} x {reset_every} EM iterations, G = {block}: phi {e[0]:.2e}, r {e[1]:.2e}")
+    assert e[0] < TOL and e[1] < TOL, e
+
+
 # -------------------------------------------------------------- 512 x 512 (L2-staged path)
 @pytest.mark.parametrize("over", [{}, {"phase_block": 2}, {"n_k": 2}])
 def test_parity_512_l2_staged(ddh, over):

@@ -499,3 +499,26 @@ def test_per_pixel_phase_iteration_amplifies_perturbations():
 def test_tiled_phase_iteration_contracts():
     d = _divergence(2, 40)
     assert d.max() < 1e-5 and d[-1] < 1e-6
+
+
+def test_static_mode_is_the_frame_step_with_unit_blend():
+    """Static DH-MBIR (Sec. 3): EM iterated on one frame with r reset to the back-projected
+    estimate |A_phi^H y~|^2 at the start of each bootstrap period.  The frame step with
+    lambda = alpha = 1, n_k = K and no tip/tilt removal is exactly that period: its r-init is
+    the reset (Eq. 3 with lambda = alpha = 1) and its K EM iterations are the plain loop."""
+    cfg = sy.config_single_64(3)
+    ys, _ = sy.Stream(cfg).frames(3)
+    K = 6
+    prm = o.default_params(64, cfg.aperture_diam, cfg.snr, lam=1.0, alpha=1.0, n_k=K, tilt_mode=0)
+    a = o.aperture(64, cfg.aperture_diam)
+    st = o.init_state(64)
+    r, phi = st.r, st.phi
+    yt, _ = o.normalize(ys[1])
+    for cycle in range(2):
+        st, _ = o.step(st, ys[1], prm)
+        # the static loop written out: reset, then K plain EM iterations
+        b = o.adjoint_op(yt, phi, a)
+        r = np.maximum(np.abs(b) ** 2, prm.r_floor)
+        for _ in range(K):
+            r, phi = o.em_static_step(r, phi, yt, prm, a)
+        assert np.allclose(st.r, r, rtol=1e-12, atol=0) and np.allclose(st.phi, phi, rtol=0, atol=1e-12)
