@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-stream", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-frames", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -164,10 +166,10 @@ def synth_ring(count, stream_id=0):
 
 
 # ------------------------------------------------------------------------- CPU oracle
-def oracle_frames_per_second(seconds, max_frames=None, warm=1):
-    """Time the FP64 oracle (as it stands) on the 256^2 stream for about `seconds`."""
+def oracle_frames_per_second(seconds, max_frames=None, warm=1, stream_id=0):
+    """Time the FP64 oracle (as it stands) on a 256^2 stream for about `seconds`."""
     from oracle import ddh_oracle as o
-    cfg, ys = synth_ring(64)
+    cfg, ys = synth_ring(64, stream_id=stream_id)
     prm = o.default_params(cfg.n, cfg.aperture_diam, cfg.snr)
     st = o.init_state(cfg.n)
     for i in range(warm):
@@ -183,20 +185,47 @@ def oracle_frames_per_second(seconds, max_frames=None, warm=1):
 
 
 def cpu_worker(args):
-    fps, frames, el = oracle_frames_per_second(args.cpu_seconds)
+    fps, frames, el = oracle_frames_per_second(args.cpu_seconds, max_frames=args.cpu_frames or None,
+                                               stream_id=args.cpu_stream)
     print(json.dumps({"value": fps, "frames": frames, "seconds": el}))
 
 
-def cpu_baseline(seconds):
+def host_cores():
+    return max(1, min(os.cpu_count() or 1, 64))
+
+
+def parallel_oracle(cores, seconds, frames_per_worker=0):
+    """The oracle on `cores` host cores: one single-threaded process per core, each running its
+    own 256^2 stream (independent streams, as the GPU's replicas), started together.  Returns
+    (aggregate frames/s, total frames, longest worker time) or an error string."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--cpu-seconds", str(seconds)],
-                         env=env, capture_output=True, text=True, timeout=600)
-    if out.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": out.stderr[-300:]}
-    res = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": res["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{res['frames']} consecutive 256x256 frames of the same stream in {res['seconds']:.1f} s, "
-                      "FP64 NumPy oracle, 1 thread"}
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--cpu-seconds", str(seconds),
+           "--cpu-frames", str(int(frames_per_worker))]
+    procs = [subprocess.Popen(cmd + ["--cpu-stream", str(i)], env=env, stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True) for i in range(cores)]
+    res, err = [], None
+    for p in procs:
+        out, e = p.communicate(timeout=900)
+        if p.returncode != 0:
+            err = e[-300:]
+            continue
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    if err is not None or not res:
+        return None, err or "no worker finished"
+    frames = sum(r["frames"] for r in res)
+    el = max(r["seconds"] for r in res)
+    return (sum(r["value"] for r in res), frames, el), None
+
+
+def cpu_baseline(seconds):
+    cores = host_cores()
+    out, err = parallel_oracle(cores, seconds)
+    if out is None:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": err}
+    fps, frames, el = out
+    return {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle", "per_core": fps / cores,
+            "sample": f"{cores} single-threaded processes, one 256x256 stream each, about {seconds:.0f} s "
+                      f"per process ({frames} frames in all), FP64 NumPy oracle"}
 
 
 # ------------------------------------------------------------------------------ arms
@@ -204,18 +233,23 @@ def run_reference(args):
     rank, _, world = dist_info()
     if rank != 0:
         return
-    warm = min(args.warmup, 2)
-    # each step is one oracle frame; the count is capped so the run stays within minutes
-    fps_probe, _, _ = oracle_frames_per_second(0.0, max_frames=1, warm=warm)
-    steps = max(1, min(args.steps, int(120.0 * fps_probe)))
-    fps, frames, el = oracle_frames_per_second(1e9, max_frames=steps, warm=0)
-    nproc = os.cpu_count()
+    cores = host_cores()
+    # each step is one oracle frame; the steps are spread over the host cores (one stream per
+    # core) and capped so that the run stays within a few minutes
+    fps_probe, _, _ = oracle_frames_per_second(0.0, max_frames=1, warm=1)
+    per_worker = max(1, min(-(-args.steps // cores), int(120.0 * fps_probe)))
+    out, err = parallel_oracle(cores, 1e9, frames_per_worker=per_worker)
+    if out is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle workers failed: {err}"}))
+        return
+    fps, frames, el = out
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world,
-            "steps": frames, "warmup": warm, "ms_per_step": 1e3 * el / frames, "higher_is_better": True,
+            "steps": frames, "warmup": 1, "ms_per_step": 1e3 / fps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": 256, "streams": 1},
-            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{frames} of {args.steps} requested frames (bounded), host has {nproc} cores"},
+            "config": {"workload": WORKLOAD, "grid": 256, "streams": cores},
+            "cpu_baseline": {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{frames} frames of {args.steps} requested (bounded): {cores} single-threaded "
+                                       f"processes, one 256x256 stream each, {per_worker} frames per process"},
             "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

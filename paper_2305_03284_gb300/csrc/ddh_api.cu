@@ -430,9 +430,13 @@ int ddh_init(ddh_state** out, const ddh_params* p, void* cuda_stream) {
 
 size_t ddh_trace_floats(int n) { return static_cast<size_t>(n) * n * 8 + 8; }
 
-int ddh_step(ddh_state* s, const void* y) { return enqueue(s, y, nullptr); }
+int ddh_step(ddh_state* s, const void* y) {
+  DdhNvtxRange r("ddh_step");
+  return enqueue(s, y, nullptr);
+}
 
 int ddh_step_trace(ddh_state* s, const void* y, float* trace) {
+  DdhNvtxRange nv("ddh_step_trace");
   if (trace == nullptr) return DDH_EINVAL;
   return enqueue(s, y, trace);
 }
@@ -452,6 +456,7 @@ static int host_async_setup(ddh_state* s) {
 }
 
 int ddh_step_host_async(ddh_state* s, const void* y_host, float* phi_host_out, int64_t* ticket) {
+  DdhNvtxRange nv("ddh_step_host_async");
   if (s == nullptr || y_host == nullptr || phi_host_out == nullptr || ticket == nullptr) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(s->device));
   int rc = host_async_setup(s);
@@ -483,6 +488,7 @@ int ddh_host_wait(ddh_state* s, int64_t ticket) {
 }
 
 int ddh_step_host(ddh_state* s, const void* y_host, float* phi_host_out) {
+  DdhNvtxRange nv("ddh_step_host");
   if (s == nullptr || y_host == nullptr || phi_host_out == nullptr) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(s->device));
   const size_t img = image_bytes(s->prm.n);
@@ -546,6 +552,7 @@ static int validate_batch(ddh_state* const* states, int count) {
 }
 
 int ddh_step_batch(ddh_state* const* states, const void* const* ys, int count) {
+  DdhNvtxRange nv("ddh_step_batch");
   if (ys == nullptr) return DDH_EINVAL;
   int rc = validate_batch(states, count);
   if (rc != DDH_OK) return rc;
@@ -636,6 +643,7 @@ int ddh_batch_create(ddh_batch** out, ddh_state* const* states, int count) {
 }
 
 int ddh_batch_run(ddh_batch* b, const void* const* ys) {
+  DdhNvtxRange nv("ddh_batch_run");
   if (b == nullptr || ys == nullptr) return DDH_EINVAL;
   for (int i = 0; i < b->count; ++i)
     if (ys[i] == nullptr || reinterpret_cast<uintptr_t>(ys[i]) % 16 != 0) return DDH_EINVAL;
@@ -655,6 +663,7 @@ int ddh_batch_run(ddh_batch* b, const void* const* ys) {
 int ddh_step_backward(ddh_state* s, const void* y, const float* r_prev, const float* phi_prev, const float* trace,
                       const float* r_new, const float* r_bar, const float* phi_bar, float* r_prev_bar,
                       float* phi_prev_bar, float* grads, void* workspace, size_t workspace_bytes) {
+  DdhNvtxRange nv("ddh_step_backward");
   if (s == nullptr || y == nullptr || r_prev == nullptr || phi_prev == nullptr || trace == nullptr ||
       r_new == nullptr || r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr ||
       phi_prev_bar == nullptr || grads == nullptr || workspace == nullptr)

@@ -2,6 +2,17 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+// NVTX range over one host-side library call (header-only NVTX3; a no-op unless a profiler
+// such as Nsight Compute or Nsight Systems is attached), so that traces show which API call
+// enqueued which kernels.
+struct DdhNvtxRange {
+  explicit DdhNvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~DdhNvtxRange() { nvtxRangePop(); }
+  DdhNvtxRange(const DdhNvtxRange&) = delete;
+  DdhNvtxRange& operator=(const DdhNvtxRange&) = delete;
+};
 
 // Record `e` as the library's last CUDA error and map it to DDH_ENOMEM / DDH_ECUDA.
 int ddh_internal_cuda_fail(cudaError_t e);

@@ -144,6 +144,7 @@ int service_step(ddh_service* s) {
     b.items.emplace_back(se, p);
   }
   if (b.items.empty()) return 0;
+  DdhNvtxRange nv("ddh_service_batch");
   int rc = DDH_OK;
   if (s->flags & DDH_SERVICE_PER_FRAME_LAUNCH) {
     for (size_t i = 0; i < b.items.size() && rc == DDH_OK; ++i) rc = ddh_step(s->scratch_states[i], s->scratch_ys[i]);
