@@ -378,6 +378,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Split cluster barrier: every thread arrives (release: its earlier shared-memory writes,
+// remote ones included, become visible to the cluster) and later waits (acquire); work between
+// the two must not read what other CTAs write before arriving.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
 // Programmatic dependent launch (sm_90+).  `grid_dep_launch` lets the next kernel of the
 // stream (launched with programmatic stream serialization) start its independent prologue;
 // `grid_dep_wait` blocks until every prerequisite grid has completed and its memory is visible

@@ -478,7 +478,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       __syncthreads();
       float* hr_left = k > 0 ? cluster.map_shared_rank(hr, k - 1) : hr;
       float* hl_right = k < C - 1 ? cluster.map_shared_rank(hl, k + 1) : hl;
-      for (int c = 0; c < 4; ++c) {
+      // One colour in two passes: its interior pixels read only this slab, its edge column
+      // (cl = 0 for cx = 0, cl = W-1 for cx = 1) also reads the halo values that the
+      // neighbouring slabs push.  The interior of colour c runs between this CTA's arrival at
+      // the previous colour's cluster barrier and its wait there, so that the barrier's latency
+      // is hidden; the edge column runs after the wait and pushes its own values.
+      auto colour_pass = [&](int c, bool edge) {
         const int cx = c & 1, cy = c >> 1;  // colours (0,0), (1,0), (0,1), (1,1)
         // the pixels of one colour are not neighbours of each other: every thread loads the
         // inputs of all its pixels, solves, then stores (kCp = 4N / 512 pixels per thread)
@@ -492,6 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           if (4 * N % kThreads != 0 && idx >= 4 * N) continue;
           const int j = idx % (N / 2), ci = idx / (N / 2);
           const int cl = cx + 2 * ci, rho = cy + 2 * j;
+          if ((cl == 0 || cl == W - 1) != edge) continue;
           const int o = cl * CS + rho;
           const bool up = rho > 0, dn = rho + 1 < N;
           // neighbour values: current r (earlier colours already updated)
@@ -534,8 +540,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           if (cv[u] == 0 && k > 0) hr_left[hv[u]] = rn;
           if (cv[u] == W - 1 && k < C - 1) hl_right[hv[u]] = rn;
         }
-        cluster.sync();  // B4..B7
+      };
+      for (int c = 0; c < 4; ++c) {
+        colour_pass(c, false);
+        if (c > 0) cluster_wait();  // B4..B6: the previous colour's halo pushes are visible
+        colour_pass(c, true);
+        __syncthreads();            // this colour's slab updates before the next interior pass
+        cluster_arrive();           // B4..B7
       }
+      cluster_wait();  // B7 (also guards shared memory until every remote reader is done)
     }
   }
   // ---- write the reflectance slab back (row-major N x N) ---------------------------------
