@@ -90,8 +90,16 @@ __device__ __forceinline__ int swz(int i) { return i ^ ((i >> 4) & 15); }
 // Group i (0 <= i < N/R) reads x_m = element i + m N/R, multiplies by exp(S 2 pi i m k /(P R)) with k = i mod P, takes
 // the R-point DFT and writes y_q to element (i - k) R + k + q P.  All reads of the warp finish
 // before any write, so the pass runs in place.  `tw[t] = exp(-2 pi i t / N)`.
-template <int N, int R, int P, int S>
-__device__ __forceinline__ void stockham_pass(float2* row, const float2* __restrict__ tw, int lane) {
+// Reads element e of a swizzled row.
+struct RowLoad {
+  const float2* row;
+  __device__ __forceinline__ float2 operator()(int e) const { return row[swz(e)]; }
+};
+
+// `load(e)` supplies element e of the input (the row itself, or another buffer for a first
+// pass that gathers its input); the output always goes to `row`.
+template <int N, int R, int P, int S, typename Load>
+__device__ __forceinline__ void stockham_pass(float2* row, const float2* __restrict__ tw, int lane, const Load& load) {
   constexpr int G = N / R;
   constexpr int GPL = (G + 31) / 32;
   float2 v[GPL][R];
@@ -100,7 +108,7 @@ __device__ __forceinline__ void stockham_pass(float2* row, const float2* __restr
     const int i = lane + 32 * g;
     if (G % 32 == 0 || i < G) {
 #pragma unroll
-      for (int m = 0; m < R; ++m) v[g][m] = row[swz(i + m * G)];
+      for (int m = 0; m < R; ++m) v[g][m] = load(i + m * G);
     }
   }
   __syncwarp();
@@ -143,58 +151,66 @@ struct FftSchedules<512> { static constexpr int count = 1; };
 
 // Unscaled length-N DFT of one shared-memory row by one warp (S = -1 forward, +1 inverse),
 // radix schedule V:  32: {8,4} | {4,8};  64: {8,8} | {4,4,4};  128: {8,4,4} | {2,8,8};
-// 256: {8,8,4} | {4,4,4,4} | {4,8,8};  512: {8,8,8}.
-template <int N, int S, int V = 0>
-__device__ __forceinline__ void fft_row(float2* row, const float2* __restrict__ tw, int lane) {
+// 256: {8,8,4} | {4,4,4,4} | {4,8,8};  512: {8,8,8}.  The first pass takes its input from
+// `first(e)` (a gather from another buffer, or the row itself), the later ones from the row.
+template <int N, int S, int V, typename Load>
+__device__ __forceinline__ void fft_row_from(float2* row, const float2* __restrict__ tw, int lane, const Load& first) {
+  const RowLoad rl{row};
   static_assert(N == 32 || N == 64 || N == 128 || N == 256 || N == 512, "unsupported N");
   static_assert(V >= 0 && V < FftSchedules<N>::count, "unknown schedule");
   if constexpr (N == 32) {
     if constexpr (V == 0) {
-      stockham_pass<32, 8, 1, S>(row, tw, lane);
-      stockham_pass<32, 4, 8, S>(row, tw, lane);
+      stockham_pass<32, 8, 1, S>(row, tw, lane, first);
+      stockham_pass<32, 4, 8, S>(row, tw, lane, rl);
     } else {
-      stockham_pass<32, 4, 1, S>(row, tw, lane);
-      stockham_pass<32, 8, 4, S>(row, tw, lane);
+      stockham_pass<32, 4, 1, S>(row, tw, lane, first);
+      stockham_pass<32, 8, 4, S>(row, tw, lane, rl);
     }
   } else if constexpr (N == 64) {
     if constexpr (V == 0) {
-      stockham_pass<64, 8, 1, S>(row, tw, lane);
-      stockham_pass<64, 8, 8, S>(row, tw, lane);
+      stockham_pass<64, 8, 1, S>(row, tw, lane, first);
+      stockham_pass<64, 8, 8, S>(row, tw, lane, rl);
     } else {
-      stockham_pass<64, 4, 1, S>(row, tw, lane);
-      stockham_pass<64, 4, 4, S>(row, tw, lane);
-      stockham_pass<64, 4, 16, S>(row, tw, lane);
+      stockham_pass<64, 4, 1, S>(row, tw, lane, first);
+      stockham_pass<64, 4, 4, S>(row, tw, lane, rl);
+      stockham_pass<64, 4, 16, S>(row, tw, lane, rl);
     }
   } else if constexpr (N == 128) {
     if constexpr (V == 0) {
-      stockham_pass<128, 8, 1, S>(row, tw, lane);
-      stockham_pass<128, 4, 8, S>(row, tw, lane);
-      stockham_pass<128, 4, 32, S>(row, tw, lane);
+      stockham_pass<128, 8, 1, S>(row, tw, lane, first);
+      stockham_pass<128, 4, 8, S>(row, tw, lane, rl);
+      stockham_pass<128, 4, 32, S>(row, tw, lane, rl);
     } else {
-      stockham_pass<128, 2, 1, S>(row, tw, lane);
-      stockham_pass<128, 8, 2, S>(row, tw, lane);
-      stockham_pass<128, 8, 16, S>(row, tw, lane);
+      stockham_pass<128, 2, 1, S>(row, tw, lane, first);
+      stockham_pass<128, 8, 2, S>(row, tw, lane, rl);
+      stockham_pass<128, 8, 16, S>(row, tw, lane, rl);
     }
   } else if constexpr (N == 256) {
     if constexpr (V == 0) {
-      stockham_pass<256, 8, 1, S>(row, tw, lane);
-      stockham_pass<256, 8, 8, S>(row, tw, lane);
-      stockham_pass<256, 4, 64, S>(row, tw, lane);
+      stockham_pass<256, 8, 1, S>(row, tw, lane, first);
+      stockham_pass<256, 8, 8, S>(row, tw, lane, rl);
+      stockham_pass<256, 4, 64, S>(row, tw, lane, rl);
     } else if constexpr (V == 1) {
-      stockham_pass<256, 4, 1, S>(row, tw, lane);
-      stockham_pass<256, 4, 4, S>(row, tw, lane);
-      stockham_pass<256, 4, 16, S>(row, tw, lane);
-      stockham_pass<256, 4, 64, S>(row, tw, lane);
+      stockham_pass<256, 4, 1, S>(row, tw, lane, first);
+      stockham_pass<256, 4, 4, S>(row, tw, lane, rl);
+      stockham_pass<256, 4, 16, S>(row, tw, lane, rl);
+      stockham_pass<256, 4, 64, S>(row, tw, lane, rl);
     } else {
-      stockham_pass<256, 4, 1, S>(row, tw, lane);
-      stockham_pass<256, 8, 4, S>(row, tw, lane);
-      stockham_pass<256, 8, 32, S>(row, tw, lane);
+      stockham_pass<256, 4, 1, S>(row, tw, lane, first);
+      stockham_pass<256, 8, 4, S>(row, tw, lane, rl);
+      stockham_pass<256, 8, 32, S>(row, tw, lane, rl);
     }
   } else {
-    stockham_pass<512, 8, 1, S>(row, tw, lane);
-    stockham_pass<512, 8, 8, S>(row, tw, lane);
-    stockham_pass<512, 8, 64, S>(row, tw, lane);
+    stockham_pass<512, 8, 1, S>(row, tw, lane, first);
+    stockham_pass<512, 8, 8, S>(row, tw, lane, rl);
+    stockham_pass<512, 8, 64, S>(row, tw, lane, rl);
   }
+}
+
+// Row DFT in place (the first pass reads the row itself).
+template <int N, int S, int V = 0>
+__device__ __forceinline__ void fft_row(float2* row, const float2* __restrict__ tw, int lane) {
+  fft_row_from<N, S, V>(row, tw, lane, RowLoad{row});
 }
 
 // ------------------------------------------------------------------------ warp reductions

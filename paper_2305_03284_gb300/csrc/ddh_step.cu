@@ -320,16 +320,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       const int cl = warp;
       float2* cb = colbuf + cl * CS;
       {
+        // the first IFFT pass gathers the column straight from the staging buffer (rows
+        // outside the aperture are zero and were not sent)
         const float2* st2 = reinterpret_cast<const float2*>(stage);
-        for (int rho = lane; rho < N; rho += 32) {
-          float2 v = make_float2(0.f, 0.f);
-          if (ap_dist2(rho, N) <= P.ap_lim)
-            v = st2[rho * 16 + 2 * ((cl >> 1) ^ (rho & 7)) + ((cl & 1) ^ ((rho >> 3) & 1))];
-          cb[swz(rho)] = v;
-        }
+        const int ap_lim = P.ap_lim;
+        auto gather = [st2, cl, ap_lim](int rho) {
+          return ap_dist2(rho, N) <= ap_lim
+                     ? st2[rho * 16 + 2 * ((cl >> 1) ^ (rho & 7)) + ((cl & 1) ^ ((rho >> 3) & 1))]
+                     : make_float2(0.f, 0.f);
+        };
+        fft_row_from<N, +1, V>(cb, tw, lane, gather);
       }
-      __syncwarp();
-      fft_row<N, +1, V>(cb, tw, lane);
       for (int rho = lane; rho < N; rho += 32) {
         const float2 b = c_scale(cb[swz(rho)], invN);
         const float rp = rS[cl * CS + rho];
