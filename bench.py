@@ -76,6 +76,21 @@ def job_throughput(steps_per_rank, world, max_ms):
     return steps_per_rank * world / (max_ms * 1e-3)
 
 
+def fp32_cobound(avg_launch_s):
+    """The FP32 pipes as a co-bound of the step kernel: the FP32 operations of one launch (ncu:
+    fadd + fmul + 2 ffma thread instructions) over the measured launch time, against the part's
+    nominal FP32 rate and against the 16 SMs that one 256^2 cluster occupies."""
+    flop = profiled_value("fp32_flop_per_launch")
+    if flop is None:
+        return None
+    achieved = flop / avg_launch_s / 1e12
+    cluster_peak = FP32_PEAK_TFLOPS * 16 / 152
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "flop_per_launch": flop,
+            "peak_16_sm_cluster": cluster_peak, "frac_16_sm_cluster": achieved / cluster_peak,
+            "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+
+
 def measured_peak_gbs():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -93,17 +108,27 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+def profiled_value(key):
+    """A per-launch figure (`key: value`) from the committed ncu summary, if it was taken on
+    this kernel source; None otherwise."""
     try:
         txt = open(PROFILE).read()
     except OSError:
         return None
-    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m = re.search(key + r":\s*([0-9.eE+]+)", txt)
     s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
     if not m or not s or s.group(1) != kernel_source_sha():
         return None
     return float(m.group(1))
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    return profiled_value("dram_bytes_per_launch")
+
+
+# Nominal FP32 rate of the part: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 class ClockSampler:
@@ -503,6 +528,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(), "kernel": "k_ddh_step<256>",
                      "bytes_per_launch": bytes_per_launch, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
+        "roofline_fp32": fp32_cobound(avg_launch_s),
         "e2e": {"value": ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 4,
                 "steps": ke},
         "static_mode": static,
