@@ -41,8 +41,11 @@ struct StepLayout {
   static constexpr size_t rS = al(phin + size_t(R) * N * 4);
   static constexpr size_t sS = al(rS + size_t(W) * CS * 4);
   // row-major staging of the row pass for this slab: 16 columns (8 chunks of 2) per row
+  // (it holds the SE and SW pair weights of the ICD once the column pass has read it)
   static constexpr size_t stage = al(sS + size_t(W) * CS * 4);
-  static constexpr size_t hl = al(stage + size_t(N) * 16 * 8);  // r of the left slab's last column
+  static constexpr size_t stage_bytes =
+      size_t(N) * 16 * 8 > size_t(2) * W * CS * 4 ? size_t(N) * 16 * 8 : size_t(2) * W * CS * 4;
+  static constexpr size_t hl = al(stage + stage_bytes);          // r of the left slab's last column
   static constexpr size_t hr = al(hl + size_t(N) * 4);         // r of the right slab's first column
   static constexpr size_t halo = al(hr + size_t(N) * 4);       // 3 x N halo-pair weights
   static constexpr size_t red = al(halo + size_t(3) * N * 4);  // 16 warps x 8 floats
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     q = warp_sum(q);
   }
 
-  // ---- phase 0b: the state written by the previous frame: phi rows, r slab ----------------
+  // ---- phase 0b: the state written by the previous frame: phi rows (r slab after B1's arrival)
   grid_dep_wait();
   {
     // phi rows rho and rho + 1 (the latter for the y tip/tilt pairs), 16-byte vectors
@@ -166,15 +169,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       reinterpret_cast<float4*>(phib)[i] = src[static_cast<size_t>(rho) * NV4 + xv];
       reinterpret_cast<float4*>(phin)[i] =
           rho + 1 < N ? src[static_cast<size_t>(rho + 1) * NV4 + xv] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    // reflectance slab: W = 16 consecutive floats per row = 4 vectors
-    for (int i = tid; i < N * (W / 4); i += kThreads) {
-      const int rho = i / (W / 4), cv = i - rho * (W / 4);
-      const float4 v = reinterpret_cast<const float4*>(A.r + static_cast<size_t>(rho) * N + W * k)[cv];
-      rS[(4 * cv + 0) * CS + rho] = v.x;
-      rS[(4 * cv + 1) * CS + rho] = v.y;
-      rS[(4 * cv + 2) * CS + rho] = v.z;
-      rS[(4 * cv + 3) * CS + rho] = v.w;
     }
   }
   __syncthreads();
@@ -224,7 +218,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     dst[0] = srcv[0];
     dst[1] = srcv[1];
   }
-  cluster.sync();  // B1
+  cluster_arrive();  // B1
+  // the reflectance slab (W = 16 consecutive floats per row = 4 vectors) is first needed in
+  // phase 3: its loads overlap the barrier
+  for (int i = tid; i < N * (W / 4); i += kThreads) {
+    const int rho = i / (W / 4), cv = i - rho * (W / 4);
+    const float4 v = reinterpret_cast<const float4*>(A.r + static_cast<size_t>(rho) * N + W * k)[cv];
+    rS[(4 * cv + 0) * CS + rho] = v.x;
+    rS[(4 * cv + 1) * CS + rho] = v.y;
+    rS[(4 * cv + 2) * CS + rho] = v.z;
+    rS[(4 * cv + 3) * CS + rho] = v.w;
+  }
+  cluster_wait();  // B1
   if (warp == 0) {
     // lane q fetches CTA q's partials (C <= 32 remote loads in parallel), then lane 0
     // combines them in rank order, so every CTA derives bit-identical statistics
@@ -368,7 +373,83 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       float2* row = cluster.map_shared_rank(rowbuf, row_owner<C>(rho, P.g_shift)) + row_local<C>(rho, P.g_shift) * RS;
       reinterpret_cast<float4*>(row + W * k)[m] = make_float4(a.x, a.y, b.x, b.y);
     }
-    cluster.sync();  // B3
+    __syncthreads();  // the column buffer's last readers are done: it now takes weights
+    cluster_arrive();  // B3
+    // Surrogate weights beta_ij = b_ij rho'(D)/D at the entry values (r-init), once per pixel
+    // pair: E, S, SE, SW pairs of every slab pixel (E, S in the column buffer, SE, SW in the
+    // staging buffer, both idle now), and the three pairs that cross into the left/right slabs
+    // from this side (W, NW at cl = 0; NE at cl = W-1).  A pair shared by two CTAs gets the same
+    // value on both sides (|D| symmetric).  The slab's interior pairs are formed while the
+    // cluster barrier completes; the edge columns and the halo pairs read the neighbours'
+    // pushed r-init columns after it.
+    {
+      float* bE = reinterpret_cast<float*>(colbuf);
+      float* bS = bE + W * CS;
+      float* bSE = reinterpret_cast<float*>(stage);
+      float* bSW = bSE + W * CS;
+      // before colour 0 the slab holds r-init, and hl / hr hold the neighbours' edge columns
+      auto wgt = [&](float d) { return prior_weight_fast(d, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p); };
+      // every load of a batch precedes its stores (the weight arrays alias other buffers, so
+      // a load after a store could not be moved above it), which keeps 4 pixels x 4 weights
+      // of MUFU work in flight per thread
+      constexpr int kPx = W * N / kThreads;  // pixels per thread (N / 32)
+      constexpr int kB = kPx < 4 ? kPx : 4;
+      // edge == false: the pixels of columns 1 .. W-2, whose pairs lie inside this slab;
+      // edge == true: columns 0 and W-1, whose pairs reach the neighbours' pushed columns
+      auto pair_weights = [&](bool edge) {
+#pragma unroll
+      for (int u0 = 0; u0 < kPx; u0 += kB) {
+        float dd[kB][4];
+        bool ok[kB][4];
+        int oo[kB];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          const int i = tid + kThreads * (u0 + b);
+          const int cl = i / N, rho = i - cl * N;
+          const int x = W * k + cl;
+          const int o = cl * CS + rho;
+          oo[b] = ((cl == 0 || cl == W - 1) == edge) ? o : -1;
+          if (oo[b] < 0) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { dd[b][e] = 0.f; ok[b][e] = false; }
+            continue;
+          }
+          const bool dn = rho + 1 < N;
+          const float r0i = rS[o];
+          const float rE = cl + 1 < W ? rS[o + CS] : hr[rho];
+          const float rSo = dn ? rS[o + 1] : 0.f;
+          const float rSE = !dn ? 0.f : (cl + 1 < W ? rS[o + CS + 1] : hr[rho + 1]);
+          const float rSW = !dn ? 0.f : (cl > 0 ? rS[o - CS + 1] : hl[rho + 1]);
+          dd[b][0] = r0i - rE;  dd[b][1] = r0i - rSo;  dd[b][2] = r0i - rSE;  dd[b][3] = r0i - rSW;
+          ok[b][0] = x + 1 < N;  ok[b][1] = dn;  ok[b][2] = x + 1 < N && dn;  ok[b][3] = x > 0 && dn;
+        }
+        float ww[kB][4];
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) ww[b][e] = ok[b][e] ? (e < 2 ? kBnn : kBdiag) * wgt(dd[b][e]) : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+          if (oo[b] < 0) continue;
+          bE[oo[b]] = ww[b][0];
+          bS[oo[b]] = ww[b][1];
+          bSE[oo[b]] = ww[b][2];
+          bSW[oo[b]] = ww[b][3];
+        }
+      }
+      };
+      pair_weights(false);
+      cluster_wait();  // B3: neighbours' row segments and edge columns have arrived
+      pair_weights(true);
+      for (int rho = tid; rho < N; rho += kThreads) {
+        // hW: pair (rho, x0-1)-(rho, x0); hNW: (rho-1, x0-1)-(rho, x0); hNE: (rho-1, x1+1)-(rho, x1)
+        const float a0 = rS[rho], a1 = rS[(W - 1) * CS + rho];
+        halo[rho] = k > 0 ? kBnn * wgt(a0 - hl[rho]) : 0.f;
+        halo[N + rho] = (k > 0 && rho > 0) ? kBdiag * wgt(a0 - hl[rho - 1]) : 0.f;
+        halo[2 * N + rho] = (k < C - 1 && rho > 0) ? kBdiag * wgt(a1 - hr[rho - 1]) : 0.f;
+      }
+    }
     // ---- phase 4: row FFT of mu (aperture rows) and phase M-step ------------------------
     // v = a y~ conj(z) per pixel (summed over the G x G tile when G > 1); phi = angle(v).
     {
@@ -416,67 +497,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
         phi_out[x] = out;
       }
     }
-    __syncthreads();  // phase 4 reads of the row buffer end before it holds weights
+    __syncthreads();  // the surrogate weights (formed around B3) and phase 4 are complete
     // ---- phase 5: r M-step, 4-colour ICD sweep on the q-GGMRF surrogate ------------------
-    // Surrogate weights beta_ij = b_ij rho'(D)/D at the entry values, once per pixel pair:
-    // E, S, SE, SW pairs of every slab pixel (in the free column/row buffers), and the three
-    // pairs that cross into the left/right slabs from this side (W, NW at cl = 0; NE at
-    // cl = W-1).  A pair shared by two CTAs gets the same value on both sides (|D| symmetric).
     {
       float* bE = reinterpret_cast<float*>(colbuf);
       float* bS = bE + W * CS;
-      float* bSE = reinterpret_cast<float*>(rowbuf);
+      float* bSE = reinterpret_cast<float*>(stage);
       float* bSW = bSE + W * CS;
-      // before colour 0 the slab holds r-init, and hl / hr hold the neighbours' edge columns
-      auto wgt = [&](float d) { return prior_weight_fast(d, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p); };
-      // every load of a batch precedes its stores (the weight arrays alias other buffers, so
-      // a load after a store could not be moved above it), which keeps 4 pixels x 4 weights
-      // of MUFU work in flight per thread
-      constexpr int kPx = W * N / kThreads;  // pixels per thread (N / 32)
-      constexpr int kB = kPx < 4 ? kPx : 4;
-#pragma unroll
-      for (int u0 = 0; u0 < kPx; u0 += kB) {
-        float dd[kB][4];
-        bool ok[kB][4];
-        int oo[kB];
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-          const int i = tid + kThreads * (u0 + b);
-          const int cl = i / N, rho = i - cl * N;
-          const int x = W * k + cl;
-          const int o = cl * CS + rho;
-          const bool dn = rho + 1 < N;
-          const float r0i = rS[o];
-          const float rE = cl + 1 < W ? rS[o + CS] : hr[rho];
-          const float rSo = dn ? rS[o + 1] : 0.f;
-          const float rSE = !dn ? 0.f : (cl + 1 < W ? rS[o + CS + 1] : hr[rho + 1]);
-          const float rSW = !dn ? 0.f : (cl > 0 ? rS[o - CS + 1] : hl[rho + 1]);
-          dd[b][0] = r0i - rE;  dd[b][1] = r0i - rSo;  dd[b][2] = r0i - rSE;  dd[b][3] = r0i - rSW;
-          ok[b][0] = x + 1 < N;  ok[b][1] = dn;  ok[b][2] = x + 1 < N && dn;  ok[b][3] = x > 0 && dn;
-          oo[b] = o;
-        }
-        float ww[kB][4];
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) ww[b][e] = ok[b][e] ? (e < 2 ? kBnn : kBdiag) * wgt(dd[b][e]) : 0.f;
-        }
-#pragma unroll
-        for (int b = 0; b < kB; ++b) {
-          bE[oo[b]] = ww[b][0];
-          bS[oo[b]] = ww[b][1];
-          bSE[oo[b]] = ww[b][2];
-          bSW[oo[b]] = ww[b][3];
-        }
-      }
-      for (int rho = tid; rho < N; rho += kThreads) {
-        // hW: pair (rho, x0-1)-(rho, x0); hNW: (rho-1, x0-1)-(rho, x0); hNE: (rho-1, x1+1)-(rho, x1)
-        const float a0 = rS[rho], a1 = rS[(W - 1) * CS + rho];
-        halo[rho] = k > 0 ? kBnn * wgt(a0 - hl[rho]) : 0.f;
-        halo[N + rho] = (k > 0 && rho > 0) ? kBdiag * wgt(a0 - hl[rho - 1]) : 0.f;
-        halo[2 * N + rho] = (k < C - 1 && rho > 0) ? kBdiag * wgt(a1 - hr[rho - 1]) : 0.f;
-      }
-      __syncthreads();
       float* hr_left = k > 0 ? cluster.map_shared_rank(hr, k - 1) : hr;
       float* hl_right = k < C - 1 ? cluster.map_shared_rank(hl, k + 1) : hl;
       // One colour in two passes: its interior pixels read only this slab, its edge column
