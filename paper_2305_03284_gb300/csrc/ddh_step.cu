@@ -4,13 +4,18 @@
 // CTA k holds, in shared memory,
 //   * rows  rho = k + C l (l = 0..15) of the pupil plane: the frame y, phi, and a row buffer;
 //   * the column slab x = 16 k .. 16 k + 15 of the image plane: a column buffer (one column
-//     per warp, contiguous), r, the r-init copy and s = E|g|^2.
+//     per warp, contiguous), r and s = E|g|^2;
+//   * a row-major staging buffer that receives the row pass (later: two of the ICD's weight
+//     arrays), the halo columns of r from the neighbouring slabs, and the halo pair weights.
 // The 2-D DFT is a row pass (one warp per row), a transpose through distributed shared
 // memory (16-byte remote stores of each row's 16-column segments into the column owner's
-// row-major staging buffer; 8-byte remote stores on the way back), and a column pass.  Cluster barriers
-// separate the frame's global dependencies:
+// staging buffer, and 16-byte stores of two-column chunks on the way back), and a column pass.
+// Cluster barriers separate the frame's global dependencies:
 //   B1 Normalize / tip-tilt statistics   B2 row IFFT -> columns   B3 r-init + column FFT -> rows
 //   B4..B7 the four ICD colours (the last also guards shared memory until every reader is done).
+// Each barrier is split into arrive and wait where local work can fill the gap: the r slab
+// loads at B1, the slab's interior surrogate weights at B3, the next colour's interior pixels
+// at B4..B6 (only work that reads no other CTA's pushes goes between the two).
 // Per frame the kernel reads y (8 B/px), phi and r (4 B/px each) and writes phi and r.
 // Everything before `grid_dep_wait` (frame TMA, twiddles, frame statistics) is independent of
 // the previous frame, so under programmatic dependent launch it overlaps the previous frame's
