@@ -403,6 +403,65 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
     return out
 
 
+def adjoint_measure(ddh, streams=16, frames=8, reps=3):
+    """Config 4: 16 streams at 256^2, K = 8 unrolled frame steps each, gradients w.r.t. r0, phi0,
+    sigma_r, p and sigma^2 through the autograd Function (forward with per-frame checkpoints,
+    then the hand-written adjoint kernels frame by frame in reverse)."""
+    import torch
+    from paper_2305_03284_gb300 import adjoint
+    from synth import ddh_synth as sy
+    cfgs = sy.config_adjoint(streams=streams, frames=frames)
+    work = []
+    for c in cfgs:
+        ys, _ = sy.Stream(c).frames(frames)
+        p = ddh.default_params(c.n, c.aperture_diam, c.snr)
+        work.append((torch.from_numpy(ys).cuda(), p))
+    n = cfgs[0].n
+
+    def one_pass():
+        for ys, p in work:
+            r0 = torch.full((n, n), 1e-3, device="cuda", requires_grad=True)
+            phi0 = torch.zeros((n, n), device="cuda", requires_grad=True)
+            sig = torch.tensor(float(p.prior_sigma), dtype=torch.float64, requires_grad=True)
+            pp = torch.tensor(float(p.prior_p), dtype=torch.float64, requires_grad=True)
+            s2 = torch.tensor(float(p.noise_var), dtype=torch.float64, requires_grad=True)
+            r_k, phi_k = adjoint.unrolled(r0, phi0, sig, pp, s2, ys, p)
+            (r_k.sum() + phi_k.square().sum()).backward()
+    one_pass()  # warm-up (allocations, first launches)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        one_pass()
+    torch.cuda.synchronize()
+    el = (time.perf_counter() - t0) / reps
+    return {"workload": f"{streams} streams at {n}^2, K = {frames} unrolled frame steps each, gradients w.r.t. "
+                        "r0, phi0, sigma_r, p, sigma^2 (per-frame checkpoints, hand-written adjoint kernels)",
+            "ms_per_pass": el * 1e3, "unrolled_windows_per_s": streams / el,
+            "frames_per_s_forward_and_backward": streams * frames / el,
+            "timing": "host clock around whole passes (forward, checkpoints, backward), device synchronised"}
+
+
+def nk_sweep(ddh, ring, ptrs, lib, cfg, stream, steps=200):
+    """Frames per second of the 256^2 stream with N_k EM iterations per frame (Fig. 1)."""
+    import torch
+    out = {}
+    for nk in (1, 2, 4, 8):
+        s = ddh.Stream(ddh.default_params(cfg.n, cfg.aperture_diam, cfg.snr, n_k=nk), stream=stream)
+        for i in range(5):
+            lib.ddh_step(s._h, ptrs[i % len(ptrs)])
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            lib.ddh_step(s._h, ptrs[i % len(ptrs)])
+        e1.record(stream)
+        e1.synchronize()
+        s.sync()
+        us = e0.elapsed_time(e1) * 1e3 / steps
+        out[str(nk)] = {"us_per_frame": us, "frames_per_s": 1e6 / us}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -461,6 +520,8 @@ def run_ours(args):
             b.synchronize()
             lat.append(a.elapsed_time(b) * 1e3)
         s.sync()
+        # ---- N_k EM iterations per frame (the inner loop of Fig. 1) ----------------------
+        nk = nk_sweep(ddh, ring, ptrs, lib, cfg, stream) if world == 1 else None
         # ---- static DH-MBIR (Sec. 3): EM iterated on one frame, bootstrap every 200 -------
         static = None
         if world == 1:
@@ -516,6 +577,7 @@ def run_ours(args):
         service = service_measure(ddh)
         batched = batched_measure(ddh, peak)
         batched["service"] = service
+        batched["adjoint"] = adjoint_measure(ddh)
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -535,6 +597,7 @@ def run_ours(args):
         "e2e": {"value": ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 4,
                 "steps": ke},
         "static_mode": static,
+        "n_k_sweep": nk,
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
