@@ -164,7 +164,7 @@ int ddh_step_backward(ddh_state *s, const void *y_c64_dev, const float *r_prev, 
 
 /* Allocation-free variant of ddh_step_backward (the paper has no counterpart; this is a
  * library service).  Same arguments and results without the workspace: the scratch is a
- * static device array inside the library, 769 KiB, present on every device that loads the
+ * static device array inside the library, 772 KiB, present on every device that loads the
  * library until the process exits, sized for grids up to 128 x 128 (larger grids return
  * DDH_EINVAL with a message in ddh_last_cuda_error).  It is meant for callers that must not
  * allocate device memory while they run, such as a real-time control loop where cudaMalloc's

@@ -17,6 +17,9 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <utility>
+
 #include "../../include/ddh.h"
 #include "ddh_device.cuh"
 #include "ddh_internal.h"
@@ -26,6 +29,8 @@ namespace ddh {
 namespace {
 
 constexpr int kBwThreads = 256;
+constexpr int kBwMaxBlocks = 128;  // the partial-sum area holds 2 + 3 floats per block
+constexpr int kBwRedFloats = 1024;
 
 struct BwParams {
   int n, ap_lim, tilt_mode;
@@ -54,7 +59,7 @@ struct BwBuffers {
   float* cbar;
   float* wbar;
   float* pg;      // 3 x M per-pixel parameter partials (sigma_r, p, sigma^2)
-  float* red;     // block partials of the tilt sums
+  float* red;     // block partials: tilt sums (2 per block), then parameter partials (3 per block)
 };
 
 struct WD {
@@ -93,6 +98,8 @@ __device__ __forceinline__ void neighbour(int nb, int& dy, int& dx, float& bij) 
 
 // phase M-step adjoint; also initialises the accumulators
 __global__ void k_bw_phase(BwParams P, BwBuffers B) {
+  grid_dep_launch();
+  grid_dep_wait();
   const int n = P.n, M = n * n;
   const float* stats = B.trace + static_cast<size_t>(8) * M;
   const float2 mean = make_float2(stats[0], stats[1]);
@@ -124,6 +131,8 @@ __global__ void k_bw_phase(BwParams P, BwBuffers B) {
 
 // ICD adjoint, pass A for the pixels of colour c: implicit derivative of the root.
 __global__ void k_bw_icd_a(BwParams P, BwBuffers B, int c) {
+  grid_dep_launch();
+  grid_dep_wait();
   const int n = P.n, M = n * n;
   const float* r0 = B.trace + static_cast<size_t>(6) * M;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
@@ -178,6 +187,8 @@ __global__ void k_bw_icd_a(BwParams P, BwBuffers B, int c) {
 
 // ICD adjoint, pass B: every pixel gathers from its colour-c neighbours.
 __global__ void k_bw_icd_b(BwParams P, BwBuffers B, int c) {
+  grid_dep_launch();
+  grid_dep_wait();
   const int n = P.n, M = n * n;
   const float* r0 = B.trace + static_cast<size_t>(6) * M;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
@@ -205,6 +216,8 @@ __global__ void k_bw_icd_b(BwParams P, BwBuffers B, int c) {
 
 // E-step and r-init adjoint.
 __global__ void k_bw_estep(BwParams P, BwBuffers B) {
+  grid_dep_launch();
+  grid_dep_wait();
   const int n = P.n, M = n * n;
   const float2* bt = reinterpret_cast<const float2*>(B.trace);
   const float2* mut = bt + M;
@@ -236,6 +249,8 @@ __global__ void k_bw_estep(BwParams P, BwBuffers B) {
 // Back-projection adjoint: phi'_bar = Im(conj(u_bar) u) on the pupil, plus block partials of
 // the tilt adjoints t_x_bar = -sum phi'_bar (x - c), t_y_bar = -sum phi'_bar (y - c).
 __global__ void k_bw_tilt_a(BwParams P, BwBuffers B) {
+  grid_dep_launch();
+  grid_dep_wait();
   const int n = P.n, M = n * n;
   const float* stats = B.trace + static_cast<size_t>(8) * M;
   const float2 mean = make_float2(stats[0], stats[1]);
@@ -276,12 +291,15 @@ __global__ void k_bw_tilt_a(BwParams P, BwBuffers B) {
   }
 }
 
-// Tilt-estimate adjoint (one block): phi_bar(x+1) += t_bar/|P|, phi_bar(x) -= t_bar/|P| for
-// every aperture pair; then the per-pixel parameter partials are reduced into grads.
+// Tilt-estimate adjoint: phi_bar(x+1) += t_bar/|P|, phi_bar(x) -= t_bar/|P| for every
+// aperture pair (every block sums the tilt partials in the same order), and each block's
+// partial sums of the three per-pixel parameter partials (fixed order within the block).
 __global__ void k_bw_tilt_b(BwParams P, BwBuffers B, int blocks) {
+  grid_dep_launch();
+  grid_dep_wait();
   const int n = P.n, M = n * n;
   __shared__ float g[2];
-  __shared__ float sh[3][1024];
+  __shared__ float sh[3][kBwThreads];
   if (threadIdx.x == 0) {
     float tx = 0.f, ty = 0.f;
     for (int b = 0; b < blocks; ++b) {
@@ -293,7 +311,10 @@ __global__ void k_bw_tilt_b(BwParams P, BwBuffers B, int blocks) {
   }
   __syncthreads();
   const float gx = g[0], gy = g[1];
-  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] += B.pg[k * M + i];
     const int row = i / n, col = i - row * n;
     const int dy2 = ap_dist2(row, n);
     if (dy2 + ap_dist2(col, n) > P.ap_lim) {
@@ -308,20 +329,42 @@ __global__ void k_bw_tilt_b(BwParams P, BwBuffers B, int blocks) {
     if (row + 1 < n && ap_dist2(row + 1, n) + dx2 <= P.ap_lim) add -= gy;
     B.phi_prev_bar[i] += add;
   }
-  // parameter partials: fixed-order block reduction
-  for (int k = 0; k < 3; ++k) {
-    float acc = 0.f;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) acc += B.pg[k * M + i];
-    sh[k][threadIdx.x] = acc;
-  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] = acc[k];
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+  for (int o = kBwThreads / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o)
       for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int k = 0; k < 3; ++k) B.grads[k] += sh[k][0];
+    for (int k = 0; k < 3; ++k) B.red[2 * kBwMaxBlocks + 3 * blockIdx.x + k] = sh[k][0];
+}
+
+// The parameter gradients: the blocks' partials summed in block order.
+__global__ void k_bw_grads(BwBuffers B, int blocks) {
+  grid_dep_launch();
+  grid_dep_wait();
+  if (threadIdx.x < 3) {
+    float acc = 0.f;
+    for (int b = 0; b < blocks; ++b) acc += B.red[2 * kBwMaxBlocks + 3 * b + threadIdx.x];
+    B.grads[threadIdx.x] += acc;
+  }
+}
+
+// Launch with programmatic stream serialization (each kernel waits for its predecessor itself).
+template <typename... Params, typename... Args>
+cudaError_t launch_bw(void (*kern)(Params...), int blocks, int threads, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(blocks), 1, 1);
+  cfg.blockDim = dim3(static_cast<unsigned>(threads), 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 }  // namespace
@@ -332,7 +375,7 @@ extern "C" {
 size_t ddh_backward_workspace_bytes(int n) {
   if (n != 32 && n != 64 && n != 128 && n != 256) return 0;
   const size_t M = static_cast<size_t>(n) * n;
-  return sizeof(float) * (4 * M + 5 * M + 3 * M + 256);
+  return sizeof(float) * (4 * M + 5 * M + 3 * M + ddh::kBwRedFloats);
 }
 
 }  // extern "C"
@@ -397,27 +440,32 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
   B.wbar = ws + 8 * M;
   B.pg = ws + 9 * M;
   B.red = ws + 12 * M;
-  const int blocks = 64;
-  k_bw_phase<<<blocks, kBwThreads, 0, st>>>(P, B);
+  // grid-stride kernels over the N x N image: as many blocks as pixels fill, up to 128
+  const int blocks = static_cast<int>(std::min<size_t>(kBwMaxBlocks, (M + kBwThreads - 1) / kBwThreads));
+  cudaError_t e = launch_bw(k_bw_phase, blocks, kBwThreads, st, P, B);
+  if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
   Fft2Args f{};
   f.in = B.cbuf1;
   f.out = B.cbuf1;
   f.tw = static_cast<const float2*>(twiddle);
   f.inverse = 1;
-  cudaError_t e = launch_fft2(n, f, st);  // mu_bar = F^H z_bar
+  e = launch_fft2(n, f, st);  // mu_bar = F^H z_bar
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
-  for (int c = 3; c >= 0; --c) {
-    k_bw_icd_a<<<blocks, kBwThreads, 0, st>>>(P, B, c);
-    k_bw_icd_b<<<blocks, kBwThreads, 0, st>>>(P, B, c);
+  for (int c = 3; c >= 0 && e == cudaSuccess; --c) {
+    e = launch_bw(k_bw_icd_a, blocks, kBwThreads, st, P, B, c);
+    if (e == cudaSuccess) e = launch_bw(k_bw_icd_b, blocks, kBwThreads, st, P, B, c);
   }
-  k_bw_estep<<<blocks, kBwThreads, 0, st>>>(P, B);
+  if (e == cudaSuccess) e = launch_bw(k_bw_estep, blocks, kBwThreads, st, P, B);
+  if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
   f.in = B.cbuf2;
   f.out = B.cbuf2;
   f.inverse = 0;
   e = launch_fft2(n, f, st);  // u_bar = F b_bar
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
-  k_bw_tilt_a<<<blocks, kBwThreads, 0, st>>>(P, B);
-  k_bw_tilt_b<<<1, 1024, 0, st>>>(P, B, blocks);
+  e = launch_bw(k_bw_tilt_a, blocks, kBwThreads, st, P, B);
+  if (e == cudaSuccess) e = launch_bw(k_bw_tilt_b, blocks, kBwThreads, st, P, B, blocks);
+  if (e == cudaSuccess) e = launch_bw(k_bw_grads, 1, 32, st, B, blocks);
+  if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
   e = cudaGetLastError();
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
   return DDH_OK;
@@ -426,11 +474,11 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
 // ---- allocation-free variant -----------------------------------------------------------------
 // Scratch for ddh_step_backward_noalloc: a file-scope device array, present on every device
 // that loads the library until the process exits.  It holds the backward workspace of grids up
-// to 128 x 128 (12 N^2 + 256 floats = 769 KiB).  Host code must not pass the array's name to a
+// to 128 x 128 (12 N^2 + 1024 floats = 772 KiB).  Host code must not pass the array's name to a
 // kernel (on the host it is only a stand-in); its device address is looked up once per device.
 namespace {
 constexpr int kNoAllocMaxN = 128;
-constexpr size_t kNoAllocScratchFloats = 12 * static_cast<size_t>(kNoAllocMaxN) * kNoAllocMaxN + 256;
+constexpr size_t kNoAllocScratchFloats = 12 * static_cast<size_t>(kNoAllocMaxN) * kNoAllocMaxN + ddh::kBwRedFloats;
 static __device__ __align__(256) float g_backward_scratch[kNoAllocScratchFloats];
 std::mutex g_scratch_mu;
 void* g_scratch_addr[64] = {};
@@ -449,7 +497,7 @@ extern "C" int ddh_step_backward_noalloc(ddh_state* s, const void* y, const floa
       r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr || phi_prev_bar == nullptr || grads == nullptr)
     return DDH_EINVAL;
   if (prm->n > kNoAllocMaxN) {
-    ddh_internal_set_error("ddh_step_backward_noalloc: grid larger than 128 x 128 (its static scratch is 769 KiB); "
+    ddh_internal_set_error("ddh_step_backward_noalloc: grid larger than 128 x 128 (its static scratch is 772 KiB); "
                            "use ddh_step_backward with a caller workspace");
     return DDH_EINVAL;
   }
