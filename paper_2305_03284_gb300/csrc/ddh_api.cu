@@ -678,6 +678,71 @@ int ddh_step_backward(ddh_state* s, const void* y, const float* r_prev, const fl
                                     phi_bar, r_prev_bar, phi_prev_bar, grads, workspace);
 }
 
+size_t ddh_unrolled_workspace_bytes(int n) {
+  const size_t bw = ddh_backward_workspace_bytes(n);
+  if (bw == 0) return 0;
+  const size_t M = static_cast<size_t>(n) * n;
+  // backward workspace, one trace, two (r_bar, phi_bar) ping-pong pairs; 256-byte aligned parts
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return al(bw) + al(ddh_trace_floats(n) * sizeof(float)) + 4 * al(M * sizeof(float));
+}
+
+int ddh_unrolled_forward(ddh_state* s, int k_frames, const void* const* ys, float* const* r_ckpt,
+                         float* const* phi_ckpt) {
+  DdhNvtxRange nv("ddh_unrolled_forward");
+  if (s == nullptr || ys == nullptr || r_ckpt == nullptr || phi_ckpt == nullptr || k_frames < 1) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  const size_t img = image_bytes(s->prm.n);
+  for (int k = 0; k <= k_frames; ++k) {
+    if (r_ckpt[k] == nullptr || phi_ckpt[k] == nullptr) return DDH_EINVAL;
+    DDH_CUDA(cudaMemcpyAsync(r_ckpt[k], s->r, img, cudaMemcpyDeviceToDevice, s->stream));
+    DDH_CUDA(cudaMemcpyAsync(phi_ckpt[k], s->phi, img, cudaMemcpyDeviceToDevice, s->stream));
+    if (k == k_frames) break;
+    const int rc = enqueue(s, ys[k], nullptr);
+    if (rc != DDH_OK) return rc;
+  }
+  return DDH_OK;
+}
+
+int ddh_unrolled_backward(ddh_state* s, int k_frames, const void* const* ys, const float* const* r_ckpt,
+                          const float* const* phi_ckpt, const float* r_bar, const float* phi_bar, float* r0_bar,
+                          float* phi0_bar, float* grads, void* workspace, size_t workspace_bytes) {
+  DdhNvtxRange nv("ddh_unrolled_backward");
+  if (s == nullptr || ys == nullptr || r_ckpt == nullptr || phi_ckpt == nullptr || r_bar == nullptr ||
+      phi_bar == nullptr || r0_bar == nullptr || phi0_bar == nullptr || grads == nullptr || workspace == nullptr ||
+      k_frames < 1)
+    return DDH_EINVAL;
+  const int n = s->prm.n;
+  if (workspace_bytes < ddh_unrolled_workspace_bytes(n) || reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
+    return DDH_EINVAL;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t M = static_cast<size_t>(n) * n, img = image_bytes(n);
+  char* w = static_cast<char*>(workspace);
+  void* bw = w;
+  w += al(ddh_backward_workspace_bytes(n));
+  float* trace = reinterpret_cast<float*>(w);
+  w += al(ddh_trace_floats(n) * sizeof(float));
+  float* rb[2] = {reinterpret_cast<float*>(w), reinterpret_cast<float*>(w + al(M * sizeof(float)))};
+  w += 2 * al(M * sizeof(float));
+  float* pb[2] = {reinterpret_cast<float*>(w), reinterpret_cast<float*>(w + al(M * sizeof(float)))};
+  const float* rin = r_bar;
+  const float* pin = phi_bar;
+  for (int k = k_frames - 1; k >= 0; --k) {
+    float* rout = k == 0 ? r0_bar : rb[k & 1];
+    float* pout = k == 0 ? phi0_bar : pb[k & 1];
+    int rc = ddh_set_state(s, r_ckpt[k], phi_ckpt[k], k);
+    if (rc == DDH_OK) rc = enqueue(s, ys[k], trace);
+    if (rc == DDH_OK)
+      rc = ddh_step_backward(s, ys[k], r_ckpt[k], phi_ckpt[k], trace, r_ckpt[k + 1], rin, pin, rout, pout, grads, bw,
+                             ddh_backward_workspace_bytes(n));
+    if (rc != DDH_OK) return rc;
+    rin = rout;
+    pin = pout;
+  }
+  (void)img;
+  return DDH_OK;
+}
+
 int ddh_fft_schedule_count(int n) { return supported_n(n) ? ddh::schedule_count(n) : 0; }
 
 int ddh_set_fft_schedule(int n, int schedule) {

@@ -1,5 +1,7 @@
 """GPU adjoint (ddh_step_backward, the autograd Function) against the FP64 oracle gradient
 and FP64 finite differences."""
+from ctypes import c_void_p
+
 import numpy as np
 import pytest
 import torch
@@ -139,3 +141,65 @@ def test_config4_sixteen_streams_256(mods):
         (torch.cos(phiK).sum() + rK.sum()).backward()
         for t in (sig.grad, pp.grad, s2.grad, r0.grad, phi0.grad):
             assert torch.isfinite(t).all()
+
+
+def test_unrolled_calls_equal_per_frame_calls(mods):
+    """ddh_unrolled_forward / ddh_unrolled_backward (the K-frame loops inside the library)
+    give bit for bit what the per-frame calls give: ddh_step from each checkpoint, then
+    ddh_step_trace + ddh_step_backward frame by frame in reverse."""
+    ddh, adjoint = mods
+    cfg = sy.config_adjoint(small=True, streams=1, frames=5)[0]
+    K, n = 5, 32
+    ys = torch.from_numpy(sy.Stream(cfg).frames(K)[0]).cuda()
+    p = ddh.default_params(n, 16.0, cfg.snr)
+    L = ddh.lib()
+    rng = np.random.default_rng(3)
+    r0 = torch.from_numpy((0.05 + rng.random((n, n))).astype(np.float32)).cuda()
+    phi0 = torch.zeros((n, n), device="cuda")
+    rbar = torch.from_numpy(rng.standard_normal((n, n)).astype(np.float32)).cuda()
+    pbar = torch.from_numpy(rng.standard_normal((n, n)).astype(np.float32)).cuda()
+    ptrs = lambda ts: (c_void_p * len(ts))(*[c_void_p(t.data_ptr()) for t in ts])
+    # library loops
+    s = ddh.Stream(p)
+    s.set_state(r0, phi0, 0)
+    ck = torch.empty((K + 1, 2, n, n), device="cuda")
+    ddh.check(L.ddh_unrolled_forward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck[k, 0] for k in range(K + 1)]),
+                                     ptrs([ck[k, 1] for k in range(K + 1)])))
+    wsb = L.ddh_unrolled_workspace_bytes(n)
+    ws = torch.empty(wsb // 4, device="cuda")
+    r0b, p0b, g = torch.empty((n, n), device="cuda"), torch.empty((n, n), device="cuda"), torch.zeros(3, device="cuda")
+    ddh.check(L.ddh_unrolled_backward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck[k, 0] for k in range(K + 1)]),
+                                      ptrs([ck[k, 1] for k in range(K + 1)]), c_void_p(rbar.data_ptr()),
+                                      c_void_p(pbar.data_ptr()), c_void_p(r0b.data_ptr()), c_void_p(p0b.data_ptr()),
+                                      c_void_p(g.data_ptr()), c_void_p(ws.data_ptr()), wsb))
+    s.sync()
+    # the same through per-frame calls
+    t = ddh.Stream(p)
+    t.set_state(r0, phi0, 0)
+    states = [(r0.clone(), phi0.clone())]
+    for k in range(K):
+        t.step(ys[k])
+        states.append((t.reflectance().clone(), t.phase().clone()))
+    for k in range(K + 1):
+        assert torch.equal(ck[k, 0], states[k][0]) and torch.equal(ck[k, 1], states[k][1]), k
+    bws = torch.empty(L.ddh_backward_workspace_bytes(n) // 4, device="cuda")
+    trace = torch.zeros(L.ddh_trace_floats(n), device="cuda")
+    g2 = torch.zeros(3, device="cuda")
+    rb, pb = rbar, pbar
+    for k in range(K - 1, -1, -1):
+        t.set_state(states[k][0], states[k][1], k)
+        ddh.check(L.ddh_step_trace(t._h, c_void_p(ys[k].data_ptr()), c_void_p(trace.data_ptr())))
+        out_r, out_p = torch.empty_like(rb), torch.empty_like(pb)
+        ddh.check(L.ddh_step_backward(t._h, c_void_p(ys[k].data_ptr()), c_void_p(states[k][0].data_ptr()),
+                                      c_void_p(states[k][1].data_ptr()), c_void_p(trace.data_ptr()),
+                                      c_void_p(states[k + 1][0].data_ptr()), c_void_p(rb.data_ptr()),
+                                      c_void_p(pb.data_ptr()), c_void_p(out_r.data_ptr()), c_void_p(out_p.data_ptr()),
+                                      c_void_p(g2.data_ptr()), c_void_p(bws.data_ptr()), bws.numel() * 4))
+        rb, pb = out_r, out_p
+    t.sync()
+    assert torch.equal(r0b, rb) and torch.equal(p0b, pb) and torch.equal(g, g2)
+    with pytest.raises(ddh.DdhError):   # workspace too small
+        ddh.check(L.ddh_unrolled_backward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck[k, 0] for k in range(K + 1)]),
+                                          ptrs([ck[k, 1] for k in range(K + 1)]), c_void_p(rbar.data_ptr()),
+                                          c_void_p(pbar.data_ptr()), c_void_p(r0b.data_ptr()), c_void_p(p0b.data_ptr()),
+                                          c_void_p(g.data_ptr()), c_void_p(ws.data_ptr()), wsb - 4))
