@@ -115,6 +115,13 @@ int ddh_reflectance(const ddh_state *s, float *out);
  * used to resume from a checkpoint and by teacher-forced comparisons. */
 int ddh_set_state(ddh_state *s, const float *r, const float *phi, int64_t frame_index);
 int64_t ddh_frame_index(const ddh_state *s);
+/* Replace the state's parameters by `p` (validated; same N, else DDH_EINVAL), keeping r, phi,
+ * the frame count and the device buffers.  Host-side only: calls enqueued afterwards use the
+ * new values (each launch takes its parameters by value), work already enqueued keeps the old
+ * ones.  A ddh_batch created before the call keeps the old values (create it again).  Used to
+ * reuse one state across calls whose prior or noise parameters differ (training through the
+ * unrolled adjoint updates them every iteration); not thread-safe against other calls on s. */
+int ddh_set_params(ddh_state *s, const ddh_params *p);
 /* The cudaStream_t the state's work is ordered on (the one given to ddh_init, or the service's
  * stream for a state admitted by ddh_service_admit); NULL if s is NULL. */
 void *ddh_state_stream(const ddh_state *s);
@@ -186,7 +193,7 @@ int ddh_unrolled_backward(ddh_state *s, int k_frames, const void *const *ys, con
 
 /* Allocation-free variant of ddh_step_backward (the paper has no counterpart; this is a
  * library service).  Same arguments and results without the workspace: the scratch is a
- * static device array inside the library, 772 KiB, present on every device that loads the
+ * static device array inside the library, 1796 KiB, present on every device that loads the
  * library until the process exits, sized for grids up to 128 x 128 (larger grids return
  * DDH_EINVAL with a message in ddh_last_cuda_error).  It is meant for callers that must not
  * allocate device memory while they run, such as a real-time control loop where cudaMalloc's

@@ -64,6 +64,7 @@ _SIGS = {
     "ddh_reflectance": (c_int, [c_void_p, c_void_p]),
     "ddh_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
     "ddh_frame_index": (c_int64, [c_void_p]),
+    "ddh_set_params": (c_int, [c_void_p, POINTER(DdhParams)]),
     "ddh_state_stream": (c_void_p, [c_void_p]),
     "ddh_step_host_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ddh_host_wait": (c_int, [c_void_p, c_int64]),

@@ -60,6 +60,7 @@ struct BwBuffers {
   float* wbar;
   float* pg;      // 3 x M per-pixel parameter partials (sigma_r, p, sigma^2)
   float* red;     // block partials: tilt sums (2 per block), then parameter partials (3 per block)
+  float4* pairs;  // 4 x M: (w, dw/dD, dw/dsigma_r, dw/dp) of the pair (p, p + dir), D = r0_p - r0_q
 };
 
 struct WD {
@@ -94,6 +95,47 @@ __device__ __forceinline__ void neighbour(int nb, int& dy, int& dx, float& bij) 
   dy = dys[nb];
   dx = dxs[nb];
   bij = nb < 4 ? kBnn : kBdiag;
+}
+
+// Each neighbour pair is stored once, at the pixel p from which the other pixel q lies in one of
+// the four "forward" directions S, E, SW, SE (table planes 0..3), with D = r0_p - r0_q.  w, dw/ds
+// and dw/dp depend on |D| only and dw/dD is odd in D, so the entry seen from q is the stored one
+// with dw/dD negated (bit for bit).  Offsets nb and its opposite share a plane.
+__device__ __forceinline__ int pair_plane(int nb) {
+  const int planes[8] = {0, 0, 1, 1, 3, 2, 2, 3};
+  return planes[nb];
+}
+__device__ __forceinline__ bool pair_forward(int nb) { return nb == 1 || nb == 3 || nb >= 6; }
+
+// The pair between pixel `a` and its neighbour b = a + offset nb, as seen from `a`.
+__device__ __forceinline__ float4 pair_from(const float4* pairs, int M, int nb, int a, int b) {
+  if (pair_forward(nb)) return pairs[pair_plane(nb) * M + a];
+  float4 e = pairs[pair_plane(nb) * M + b];
+  e.y = -e.y;
+  return e;
+}
+
+// The pair table of the frame: one thread per (plane, pixel).
+__global__ void k_bw_pairs(BwParams P, BwBuffers B) {
+  grid_dep_launch();
+  grid_dep_wait();
+  const int n = P.n, M = n * n;
+  const float* r0 = B.trace + static_cast<size_t>(6) * M;
+  const int fwd[4] = {1, 3, 6, 7};  // S, E, SW, SE
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 4 * M; t += gridDim.x * blockDim.x) {
+    const int plane = t / M, i = t - plane * M;
+    const int row = i / n, col = i - row * n;
+    int dy, dx;
+    float bij;
+    neighbour(fwd[plane], dy, dx, bij);
+    const int rr = row + dy, cc = col + dx;
+    float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (rr < n && cc >= 0 && cc < n) {
+      const WD wd = weight_derivs(r0[i] - r0[rr * n + cc], P);
+      e = make_float4(wd.w, wd.dd, wd.ds, wd.dp);
+    }
+    B.pairs[t] = e;
+  }
 }
 
 // phase M-step adjoint; also initialises the accumulators
@@ -133,16 +175,17 @@ __global__ void k_bw_phase(BwParams P, BwBuffers B) {
 __global__ void k_bw_icd_a(BwParams P, BwBuffers B, int c) {
   grid_dep_launch();
   grid_dep_wait();
-  const int n = P.n, M = n * n;
+  const int n = P.n, M = n * n, h = n / 2;
   const float* r0 = B.trace + static_cast<size_t>(6) * M;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-    const int row = i / n, col = i - row * n;
-    if (colour_of(row, col) != c) continue;
+  // the colour-c pixels: rows of parity c / 2, columns of parity c % 2
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M / 4; k += gridDim.x * blockDim.x) {
+    const int kr = k / h;
+    const int row = 2 * kr + (c >> 1), col = 2 * (k - kr * h) + (c & 1);
+    const int i = row * n + col;
     const float rn = B.r_new[i];
-    const float r0i = r0[i];
     float Wsum = 0.f, Csum = 0.f;
     float beta[8], cur[8];
-    WD wd[8];
+    float4 wd[8];
     bool in[8];
     for (int nb = 0; nb < 8; ++nb) {
       int dy, dx;
@@ -152,8 +195,8 @@ __global__ void k_bw_icd_a(BwParams P, BwBuffers B, int c) {
       in[nb] = rr >= 0 && rr < n && cc >= 0 && cc < n;
       if (!in[nb]) continue;
       const int j = rr * n + cc;
-      wd[nb] = weight_derivs(r0i - r0[j], P);
-      beta[nb] = bij * wd[nb].w;
+      wd[nb] = pair_from(B.pairs, M, nb, i, j);
+      beta[nb] = bij * wd[nb].x;
       cur[nb] = colour_of(rr, cc) < c ? B.r_new[j] : r0[j];
       Wsum += beta[nb];
       Csum = fmaf(beta[nb], cur[nb], Csum);
@@ -175,9 +218,9 @@ __global__ void k_bw_icd_a(BwParams P, BwBuffers B, int c) {
       float bij;
       neighbour(nb, dy, dx, bij);
       const float bb = fmaf(cbar, cur[nb], wbar) * bij;
-      r0b = fmaf(bb, wd[nb].dd, r0b);
-      gs = fmaf(bb, wd[nb].ds, gs);
-      gpp = fmaf(bb, wd[nb].dp, gpp);
+      r0b = fmaf(bb, wd[nb].y, r0b);
+      gs = fmaf(bb, wd[nb].z, gs);
+      gpp = fmaf(bb, wd[nb].w, gpp);
     }
     B.r0bar[i] += r0b;
     B.pg[i] += gs;
@@ -204,10 +247,17 @@ __global__ void k_bw_icd_b(BwParams P, BwBuffers B, int c) {
       const int rr = row + dy, cc = col + dx;
       if (rr < 0 || rr >= n || cc < 0 || cc >= n || colour_of(rr, cc) != c) continue;
       const int i = rr * n + cc;
-      const WD wd = weight_derivs(r0[i] - r0[j], P);  // the pair as pixel i saw it
+      // the pair as pixel i saw it (D = r0_i - r0_j): stored at j when i lies forward of j
+      float4 wd;
+      if (pair_forward(nb)) {
+        wd = B.pairs[pair_plane(nb) * M + j];
+        wd.y = -wd.y;
+      } else {
+        wd = B.pairs[pair_plane(nb) * M + i];
+      }
       const float ci = B.cbar[i];
-      ab = fmaf(ci, bij * wd.w, ab);
-      r0b = fmaf(fmaf(ci, cur, B.wbar[i]) * bij, wd.dd, r0b);
+      ab = fmaf(ci, bij * wd.x, ab);
+      r0b = fmaf(fmaf(ci, cur, B.wbar[i]) * bij, wd.y, r0b);
     }
     B.abar[j] += ab;
     B.r0bar[j] -= r0b;
@@ -375,7 +425,7 @@ extern "C" {
 size_t ddh_backward_workspace_bytes(int n) {
   if (n != 32 && n != 64 && n != 128 && n != 256) return 0;
   const size_t M = static_cast<size_t>(n) * n;
-  return sizeof(float) * (4 * M + 5 * M + 3 * M + ddh::kBwRedFloats);
+  return sizeof(float) * (4 * M + 5 * M + 3 * M + ddh::kBwRedFloats + 16 * M);
 }
 
 }  // extern "C"
@@ -440,6 +490,7 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
   B.wbar = ws + 8 * M;
   B.pg = ws + 9 * M;
   B.red = ws + 12 * M;
+  B.pairs = reinterpret_cast<float4*>(ws + 12 * M + kBwRedFloats);  // 16-byte aligned
   // grid-stride kernels over the N x N image: as many blocks as pixels fill, up to 128
   const int blocks = static_cast<int>(std::min<size_t>(kBwMaxBlocks, (M + kBwThreads - 1) / kBwThreads));
   cudaError_t e = launch_bw(k_bw_phase, blocks, kBwThreads, st, P, B);
@@ -451,9 +502,13 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
   f.inverse = 1;
   e = launch_fft2(n, f, st);  // mu_bar = F^H z_bar
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
+  const int pair_blocks = static_cast<int>((4 * M + kBwThreads - 1) / kBwThreads);
+  const int colour_blocks = static_cast<int>((M / 4 + kBwThreads - 1) / kBwThreads);
+  const int pixel_blocks = static_cast<int>((M + kBwThreads - 1) / kBwThreads);
+  if (e == cudaSuccess) e = launch_bw(k_bw_pairs, pair_blocks, kBwThreads, st, P, B);
   for (int c = 3; c >= 0 && e == cudaSuccess; --c) {
-    e = launch_bw(k_bw_icd_a, blocks, kBwThreads, st, P, B, c);
-    if (e == cudaSuccess) e = launch_bw(k_bw_icd_b, blocks, kBwThreads, st, P, B, c);
+    e = launch_bw(k_bw_icd_a, colour_blocks, kBwThreads, st, P, B, c);
+    if (e == cudaSuccess) e = launch_bw(k_bw_icd_b, pixel_blocks, kBwThreads, st, P, B, c);
   }
   if (e == cudaSuccess) e = launch_bw(k_bw_estep, blocks, kBwThreads, st, P, B);
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
@@ -474,11 +529,11 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
 // ---- allocation-free variant -----------------------------------------------------------------
 // Scratch for ddh_step_backward_noalloc: a file-scope device array, present on every device
 // that loads the library until the process exits.  It holds the backward workspace of grids up
-// to 128 x 128 (12 N^2 + 1024 floats = 772 KiB).  Host code must not pass the array's name to a
+// to 128 x 128 (28 N^2 + 1024 floats = 1796 KiB).  Host code must not pass the array's name to a
 // kernel (on the host it is only a stand-in); its device address is looked up once per device.
 namespace {
 constexpr int kNoAllocMaxN = 128;
-constexpr size_t kNoAllocScratchFloats = 12 * static_cast<size_t>(kNoAllocMaxN) * kNoAllocMaxN + ddh::kBwRedFloats;
+constexpr size_t kNoAllocScratchFloats = 28 * static_cast<size_t>(kNoAllocMaxN) * kNoAllocMaxN + ddh::kBwRedFloats;
 static __device__ __align__(256) float g_backward_scratch[kNoAllocScratchFloats];
 std::mutex g_scratch_mu;
 void* g_scratch_addr[64] = {};
@@ -497,7 +552,7 @@ extern "C" int ddh_step_backward_noalloc(ddh_state* s, const void* y, const floa
       r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr || phi_prev_bar == nullptr || grads == nullptr)
     return DDH_EINVAL;
   if (prm->n > kNoAllocMaxN) {
-    ddh_internal_set_error("ddh_step_backward_noalloc: grid larger than 128 x 128 (its static scratch is 772 KiB); "
+    ddh_internal_set_error("ddh_step_backward_noalloc: grid larger than 128 x 128 (its static scratch is 1796 KiB); "
                            "use ddh_step_backward with a caller workspace");
     return DDH_EINVAL;
   }

@@ -523,6 +523,14 @@ int ddh_set_state(ddh_state* s, const float* r, const float* phi, int64_t frame_
 }
 
 int64_t ddh_frame_index(const ddh_state* s) { return s ? s->frame : -1; }
+
+int ddh_set_params(ddh_state* s, const ddh_params* p) {
+  if (s == nullptr || p == nullptr || validate(p) != DDH_OK || p->n != s->prm.n) return DDH_EINVAL;
+  s->prm = *p;
+  s->kp = derive(*p);
+  s->ap_count = aperture_count(p->n, aperture_limit(p->aperture_diam));
+  return DDH_OK;
+}
 void* ddh_state_stream(const ddh_state* s) { return s ? static_cast<void*>(s->stream) : nullptr; }
 
 int ddh_strehl(ddh_state* s, const float* phi_true_dev, float* out) {

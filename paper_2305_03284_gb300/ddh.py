@@ -136,6 +136,12 @@ class Stream:
         _check_image(phi, self.n)
         check(lib().ddh_set_state(self._h, c_void_p(r.data_ptr()), c_void_p(phi.data_ptr()), int(frame_index)))
 
+    def set_params(self, params: DdhParams) -> None:
+        """Replace the parameters (same grid size), keeping r, phi and the frame count; steps
+        enqueued afterwards use them."""
+        check(lib().ddh_set_params(self._h, byref(params)))
+        self.params = params
+
     @property
     def frame_index(self) -> int:
         return int(lib().ddh_frame_index(self._h))

@@ -71,3 +71,4 @@ def test_host_helpers(lib):
     assert lib.ddh_step(None, None) == -1
     assert lib.ddh_sync(None) == -1
     assert lib.ddh_step_batch(None, None, 0) == -1
+    assert lib.ddh_set_params(None, None) == -1

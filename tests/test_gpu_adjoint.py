@@ -203,3 +203,38 @@ def test_unrolled_calls_equal_per_frame_calls(mods):
                                           ptrs([ck[k, 1] for k in range(K + 1)]), c_void_p(rbar.data_ptr()),
                                           c_void_p(pbar.data_ptr()), c_void_p(r0b.data_ptr()), c_void_p(p0b.data_ptr()),
                                           c_void_p(g.data_ptr()), c_void_p(ws.data_ptr()), wsb - 4))
+
+
+def test_set_params_and_the_reused_adjoint_state(mods):
+    """ddh_set_params: a state whose prior/noise parameters are replaced steps bit for bit like
+    a fresh state built with them; a different grid size is refused.  The autograd Function
+    reuses one state per stream through it, so a call after a call with other parameters
+    gives bit for bit what it gave before."""
+    ddh, adjoint = mods
+    K, n = 4, 32
+    cfg = sy.config_adjoint(small=True, streams=1, frames=K)[0]
+    ys = torch.from_numpy(sy.Stream(cfg).frames(K)[0]).cuda()
+    p1 = ddh.default_params(n, 16.0, cfg.snr)
+    p2 = ddh.default_params(n, 16.0, cfg.snr)
+    p2.prior_sigma, p2.prior_p, p2.noise_var = 2.0 * p1.prior_sigma, 1.5, 0.5 * p1.noise_var
+    a, b = ddh.Stream(p1), ddh.Stream(p2)
+    a.set_params(p2)
+    for k in range(K):
+        a.step(ys[k])
+        b.step(ys[k])
+    assert torch.equal(a.phase(), b.phase()) and torch.equal(a.reflectance(), b.reflectance())
+    with pytest.raises(ddh.DdhError):
+        a.set_params(ddh.default_params(64, 32.0, cfg.snr))
+
+    def grads(p):
+        r0 = torch.full((n, n), 0.05, device="cuda", requires_grad=True)
+        phi0 = torch.zeros((n, n), device="cuda", requires_grad=True)
+        ts = [torch.tensor(float(v), dtype=torch.float64, requires_grad=True)
+              for v in (p.prior_sigma, p.prior_p, p.noise_var)]
+        rK, phiK = adjoint.unrolled(r0, phi0, *ts, ys, p)
+        (rK.sum() + torch.sin(phiK).sum()).backward()
+        return [r0.grad.clone(), phi0.grad.clone()] + [t.grad.clone() for t in ts]
+
+    g1, g2, g3 = grads(p1), grads(p2), grads(p1)
+    assert all(torch.equal(x, y) for x, y in zip(g1, g3))
+    assert not torch.equal(g1[0], g2[0])
