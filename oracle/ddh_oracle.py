@@ -18,14 +18,21 @@ reading of its forward model (Eq. 1, Sec. 2) and MAP objective (Eq. 2):
   sweep's entry values; each pixel minimises a 1-D function whose stationarity condition is the
   cubic ``W r^3 - C r^2 + r - s = 0``;
 * phase M-step: ``phi_i = angle(y_i conj(z_i))`` on the aperture, ``z = F mu`` (or, with the
-  phase held constant on G x G tiles, the angle of the tile sum of ``y conj(z)``);
+  phase held constant on G x G tiles, the angle of the tile sum of ``y conj(z)``; optionally
+  under a Gaussian MRF prior on the wrapped differences of neighbouring tiles, minimised by
+  majorised ICD sweeps);
+* optional sigma^2 M-step, once per frame after its last EM iteration: ``E||y - A g||^2 / |P|``
+  over the posterior of g; the next frame's E-steps use the new value;
 * loop (Fig. 1): Normalize (Eq. 4), RemoveTipTilt, r-init (Eq. 3), ``N_k`` EM iterations.
 
 Arithmetic is float64 throughout; the input frame is the complex64 frame promoted to complex128.
 
 Parity status: the FFT, operator, Normalize, RemoveTipTilt, E-step, cubic/ICD, surrogate,
 phase M-step and Strehl functions are each pinned by tests against closed forms, brute force or
-the exact posterior (see the oracle tests).  The multi-frame trajectory as a whole has no
+the exact posterior (see the oracle tests).  The prior-weighted tile-phase M-step is pinned by
+monotone descent of its per-pixel cost, stationarity at its fixed point (finite differences)
+and a two-tile closed form; the sigma^2 M-step by the exact-fit case, the sample noise power
+over the pupil, and convergence of EM to the maximum-likelihood variance.  The multi-frame trajectory as a whole has no
 printed values in the paper: beyond those pins it is *parity unpinned*.
 """
 from __future__ import annotations
@@ -59,6 +66,9 @@ class Params:
     r_floor: float = 1e-10
     tilt_mode: int = 1           # 1: RemoveTipTilt each frame, 0: skip
     phase_block: int = 1         # 1: per-pixel phase; G > 1: phase constant on G x G blocks
+    phase_prior: float = 0.0     # precision 1/sigma_phi^2 of the tile-phase GMRF (0: flat prior)
+    phase_sweeps: int = 2        # ICD sweeps of the tile-phase M-step under that prior
+    noise_update: int = 0        # 1: sigma^2 is re-estimated by an M-step every frame
 
 
 @dataclass
@@ -66,6 +76,7 @@ class State:
     r: np.ndarray                # reflectance, N x N
     phi: np.ndarray              # phase, N x N (zero off the aperture)
     n: int = 0
+    noise_var: float | None = None  # current sigma^2 estimate (noise_update); None: the parameter
 
 
 @dataclass
@@ -330,6 +341,105 @@ def phase_mstep(y_norm: np.ndarray, mu: np.ndarray, phi_old: np.ndarray, a: np.n
 
 
 # ---------------------------------------------------------------------------------------
+# tile-phase M-step under a GMRF phase prior, and the sigma^2 M-step (extensions: the paper
+# names p(phi) in Eq. 2 but defers its form; the noise variance is a parameter of Eq. 1)
+# ---------------------------------------------------------------------------------------
+NOISE_FLOOR = 1e-6  # lower bound on the re-estimated sigma^2 (normalised units)
+
+
+def phase_tile_sums(y_norm: np.ndarray, z: np.ndarray, a: np.ndarray, block: int):
+    """Per aligned ``block x block`` tile t: ``v_t = sum_{i in t} a_i y_i conj(z_i)`` and
+    whether the tile holds an aperture pixel."""
+    n = y_norm.shape[0]
+    nt = n // block
+    v = np.where(a, y_norm * np.conj(z), 0.0)
+    vt = v.reshape(nt, block, nt, block).sum(axis=(1, 3))
+    has_ap = np.asarray(a, bool).reshape(nt, block, nt, block).any(axis=(1, 3))
+    return vt, has_ap
+
+
+def phase_prior_icd(vt: np.ndarray, active: np.ndarray, s2: float, lam: float, sweeps: int,
+                    start: np.ndarray) -> np.ndarray:
+    """Minimise over the active tiles' phases
+        f(phi) = -(2/s2) sum_t |v_t| cos(phi_t - angle v_t)
+                 + (lam/2) sum_{t~s} b_ts wrap(phi_t - phi_s)^2
+    (the EM data term of Eq. 1 with ``A^H A`` independent of phi, and a Gaussian MRF on the
+    wrapped differences of 8-neighbour active tiles, weights as the reflectance prior's) by
+    ``sweeps`` 4-colour ICD sweeps from ``start``.  Each tile minimises a quadratic majoriser
+    of its 1-D function at the current value: ``1 - cos x`` by its symmetric bound
+    ``sin(x0)/(2 x0) x^2`` (+ const) about ``x0 = wrap(phi_t - angle v_t)``, and each
+    ``wrap(d)^2`` by ``(d - 2 pi k)^2`` with k its current branch; the minimiser is wrapped
+    into (-pi, pi].  A tile whose majoriser has zero curvature keeps its value."""
+    nt = vt.shape[0]
+    kap = 2.0 * np.abs(vt) / s2
+    th = np.angle(vt)
+    pt = np.array(start, np.float64, copy=True)
+    for _ in range(sweeps):
+        for cx, cy in COLOURS:
+            for T in range(cy, nt, 2):
+                for X in range(cx, nt, 2):
+                    if not active[T, X]:
+                        continue
+                    p0 = pt[T, X]
+                    x0 = float(wrap(p0 - th[T, X]))
+                    c0 = 0.5 if x0 == 0.0 else math.sin(x0) / (2.0 * x0)
+                    wsum = ssum = 0.0
+                    for dy, dx, bij in NEIGHBOURS:
+                        T2, X2 = T + dy, X + dx
+                        if 0 <= T2 < nt and 0 <= X2 < nt and active[T2, X2]:
+                            wsum += bij
+                            ssum += bij * (p0 - float(wrap(p0 - pt[T2, X2])))
+                    den = 2.0 * kap[T, X] * c0 + lam * wsum
+                    if den > 0.0:
+                        pt[T, X] = float(wrap((2.0 * kap[T, X] * c0 * (p0 - x0) + lam * ssum) / den))
+    return pt
+
+
+def phase_map_objective(phi: np.ndarray, y_norm: np.ndarray, z: np.ndarray, a: np.ndarray, s2: float,
+                        block: int, lam: float, active: np.ndarray) -> float:
+    """The phase M-step's cost, per pixel: ``-(2/s2) sum_{i in P} Re(conj(y_i) e^{j phi_i} z_i)``
+    plus the prior of ``phase_prior_icd`` on the tile values of ``phi`` (constant on tiles)."""
+    ab = np.asarray(a, bool)
+    data = -2.0 / s2 * float(np.sum(np.real(np.conj(y_norm) * np.exp(1j * phi) * z)[ab]))
+    nt = phi.shape[0] // block
+    cnt = ab.reshape(nt, block, nt, block).sum(axis=(1, 3))
+    tot = np.where(ab, phi, 0.0).reshape(nt, block, nt, block).sum(axis=(1, 3))
+    pt = np.where(cnt > 0, tot / np.maximum(cnt, 1), 0.0)  # the tile value at its aperture pixels
+    e = 0.0
+    for dy, dx, bij in [(0, 1, B_NN), (1, 0, B_NN), (1, 1, B_DIAG), (1, -1, B_DIAG)]:
+        p1, p2 = _pair_views(pt, dy, dx)
+        m1, m2 = _pair_views(active, dy, dx)
+        e += bij * float(np.sum(np.where(m1 & m2, wrap(p1 - p2) ** 2, 0.0)))
+    return data + 0.5 * lam * e
+
+
+def phase_mstep_prior(y_norm: np.ndarray, mu: np.ndarray, phi_old: np.ndarray, a: np.ndarray, block: int,
+                      lam: float, s2: float, sweeps: int):
+    """Tile-phase M-step under the GMRF phase prior: start from the prior-free tile angles
+    (``phase_mstep``), then ``phase_prior_icd`` over the tiles that hold an aperture pixel and a
+    non-zero tile sum; their aperture pixels take the tile value.  ``lam = 0`` is
+    ``phase_mstep``.  Returns (phi, z)."""
+    phi, z = phase_mstep(y_norm, mu, phi_old, a, block)
+    if lam <= 0.0:
+        return phi, z
+    vt, has_ap = phase_tile_sums(y_norm, z, a, block)
+    active = has_ap & (vt != 0)
+    pt = phase_prior_icd(vt, active, s2, lam, sweeps, np.angle(vt))
+    on = np.kron(active, np.ones((block, block), bool)) & np.asarray(a, bool)
+    return np.where(on, np.kron(pt, np.ones((block, block))), phi), z
+
+
+def noise_mstep(y_norm: np.ndarray, z: np.ndarray, phi: np.ndarray, a: np.ndarray, cvar: np.ndarray) -> float:
+    """EM update of sigma^2 under Eq. 1 (noise CN(0, sigma^2) on the P measured pupil pixels):
+    ``E||y - A g||^2 / |P|`` over the posterior of g, with ``A = D_a D(e^{j phi}) F``:
+    ``(1/|P|) sum_{i in P} |y_i - e^{j phi_i} z_i|^2 + (1/M) sum_j C_jj`` (diagonal posterior
+    covariance C, unitary F), floored at ``NOISE_FLOOR``."""
+    ab = np.asarray(a, bool)
+    res = float(np.sum(np.abs(y_norm - np.exp(1j * phi) * z)[ab] ** 2)) / float(ab.sum())
+    return max(res + float(np.mean(cvar)), NOISE_FLOOR)
+
+
+# ---------------------------------------------------------------------------------------
 # one frame of DDH-MBIR (Fig. 1)
 # ---------------------------------------------------------------------------------------
 def step(state: State, y: np.ndarray, prm: Params) -> tuple[State, Trace]:
@@ -349,16 +459,24 @@ def step(state: State, y: np.ndarray, prm: Params) -> tuple[State, Trace]:
     tr.b = b
     r = r_init(state.r, b, prm)
     tr.r_init = r
+    s2 = state.noise_var if (prm.noise_update and state.noise_var is not None) else prm.noise_var
+    pe = replace(prm, noise_var=s2)
     for it in range(prm.n_k):
         if it > 0:
             b = adjoint_op(yt, phi, a)
-        mu, s, _ = estep(r, b, prm)
-        r_new = icd_sweep(r, s, prm)
-        phi, z = phase_mstep(yt, mu, phi, a, prm.phase_block)
+        mu, s, w = estep(r, b, pe)
+        r_new = icd_sweep(r, s, pe)
+        if prm.phase_prior > 0.0:
+            phi, z = phase_mstep_prior(yt, mu, phi, a, prm.phase_block, prm.phase_prior, s2, prm.phase_sweeps)
+        else:
+            phi, z = phase_mstep(yt, mu, phi, a, prm.phase_block)
+        if prm.noise_update and it == prm.n_k - 1:  # once per frame, after its last EM iteration
+            s2 = noise_mstep(yt, z, phi, a, s2 * w)
         r = r_new
         if it == 0:
             tr.mu, tr.s, tr.z = mu, s, z
-    return State(r=r, phi=phi, n=state.n + 1), tr
+    nv = s2 if prm.noise_update else state.noise_var
+    return State(r=r, phi=phi, n=state.n + 1, noise_var=nv), tr
 
 
 def run(y_frames, prm: Params, state: State | None = None):

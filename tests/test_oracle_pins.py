@@ -522,3 +522,129 @@ def test_static_mode_is_the_frame_step_with_unit_blend():
         for _ in range(K):
             r, phi = o.em_static_step(r, phi, yt, prm, a)
         assert np.allclose(st.r, r, rtol=1e-12, atol=0) and np.allclose(st.phi, phi, rtol=0, atol=1e-12)
+
+
+# ---- tile-phase M-step under the GMRF phase prior, sigma^2 M-step ----------------------------
+def _phase_case(seed=5, n=64, d=32.0):
+    rng = _rng(seed)
+    a = o.aperture(n, d)
+    yt = _crandn(rng, n, n)
+    mu = 0.7 * o.ifft2u(yt) + 0.3 * _crandn(rng, n, n)  # z = F mu correlated with y
+    return a, yt, mu
+
+
+def test_phase_prior_zero_precision_is_the_tile_angle_step():
+    a, yt, mu = _phase_case()
+    phi_old = _rng(1).uniform(-1, 1, a.shape) * a
+    for G in (2, 4):
+        p0, z0 = o.phase_mstep(yt, mu, phi_old, a, G)
+        p1, z1 = o.phase_mstep_prior(yt, mu, phi_old, a, G, 0.0, 0.3, 3)
+        assert np.array_equal(p0, p1) and np.array_equal(z0, z1)
+
+
+def test_phase_prior_sweeps_do_not_increase_the_map_cost():
+    """Each majorised ICD sweep lowers (never raises) the phase M-step's cost, evaluated per
+    pixel from its definition (data term over the aperture pixels, prior on the tile values)."""
+    a, yt, mu = _phase_case()
+    z = o.fft2u(mu)
+    for G, lam in ((2, 4.0), (4, 40.0)):
+        vt, has_ap = o.phase_tile_sums(yt, z, a, G)
+        active = has_ap & (vt != 0)
+        costs = []
+        for k in range(7):
+            phi, _ = o.phase_mstep_prior(yt, mu, np.zeros_like(yt.real), a, G, lam, 0.3, k)
+            costs.append(o.phase_map_objective(phi, yt, z, a, 0.3, G, lam, active))
+        assert all(c1 <= c0 + 1e-9 * abs(c0) for c0, c1 in zip(costs, costs[1:])), costs
+        assert costs[-1] < costs[0] - 1e-4 * abs(costs[0])  # the prior moves the estimate
+
+
+def test_phase_prior_fixed_point_is_stationary():
+    """After many sweeps every active tile sits where the cost's derivative in its phase (a
+    central difference of the per-pixel cost, all the tile's aperture pixels moved) is zero."""
+    a, yt, mu = _phase_case(seed=7)
+    z = o.fft2u(mu)
+    G, lam, s2 = 4, 20.0, 0.3
+    vt, has_ap = o.phase_tile_sums(yt, z, a, G)
+    active = has_ap & (vt != 0)
+    phi, _ = o.phase_mstep_prior(yt, mu, np.zeros_like(yt.real), a, G, lam, s2, 400)
+    h = 1e-5
+    nt = a.shape[0] // G
+    worst = 0.0
+    for T in range(nt):
+        for X in range(nt):
+            if not active[T, X]:
+                continue
+            m = np.zeros(a.shape, bool)
+            m[T * G:(T + 1) * G, X * G:(X + 1) * G] = True
+            m &= a
+            fp = o.phase_map_objective(np.where(m, phi + h, phi), yt, z, a, s2, G, lam, active)
+            fm = o.phase_map_objective(np.where(m, phi - h, phi), yt, z, a, s2, G, lam, active)
+            scale = 2.0 * abs(vt[T, X]) / s2 + lam
+            worst = max(worst, abs(fp - fm) / (2 * h) / scale)
+    assert worst < 1e-5, worst
+
+
+def test_phase_prior_two_tiles_closed_form():
+    """Two active neighbouring tiles with equal |v| and angles +-alpha: the symmetric optimum
+    phi = (beta, -beta) solves K sin(beta - alpha) + 2 lam b beta = 0, K = 2|v|/s2 (a scalar
+    root found by bracketing, independent of the sweep's update formula)."""
+    from scipy.optimize import brentq
+    nt, alpha, m, s2, lam = 4, 1.0, 1.0, 0.5, 3.0
+    vt = np.zeros((nt, nt), complex)
+    vt[1, 1] = m * np.exp(1j * alpha)
+    vt[1, 2] = m * np.exp(-1j * alpha)
+    active = vt != 0
+    pt = o.phase_prior_icd(vt, active, s2, lam, 500, np.angle(vt))
+    K = 2 * m / s2
+    beta = brentq(lambda b: K * math.sin(b - alpha) + 2 * lam * o.B_NN * b, 0.0, alpha)
+    assert abs(pt[1, 1] - beta) < 1e-10 and abs(pt[1, 2] + beta) < 1e-10, (pt[1, 1], pt[1, 2], beta)
+    assert np.all(pt[~active] == 0.0)
+
+
+def test_noise_mstep_exact_fit_leaves_the_posterior_variance():
+    rng = _rng(11)
+    n = 32
+    a = o.aperture(n, 16.0)
+    z = _crandn(rng, n, n)
+    phi = rng.uniform(-3, 3, (n, n))
+    y = np.where(a, np.exp(1j * phi) * z, _crandn(rng, n, n))  # exact fit on the pupil only
+    cvar = rng.uniform(0.01, 0.2, (n, n))
+    assert abs(o.noise_mstep(y, z, phi, a, cvar) - cvar.mean()) < 1e-15
+
+
+def test_noise_mstep_em_reaches_the_ml_variance():
+    """Full aperture, phi = 0, constant r: y ~ CN(0, (r + s2) I) marginally, so the ML noise
+    variance is mean|y|^2 - r; EM iterations of (E-step, sigma^2 M-step) must converge there."""
+    rng = _rng(12)
+    n = 32
+    a = np.ones((n, n), bool)
+    y = 1.1 * _crandn(rng, n, n)
+    r0 = 0.4
+    r = np.full((n, n), r0)
+    phi = np.zeros((n, n))
+    s2 = 2.0
+    for _ in range(5000):
+        prm = o.Params(n=n, aperture_diam=float(n), noise_var=s2)
+        b = o.adjoint_op(y, phi, a)
+        mu, _, w = o.estep(r, b, prm)
+        s2_new = o.noise_mstep(y, o.fft2u(mu), phi, a, s2 * w)
+        if abs(s2_new - s2) < 1e-15:
+            break
+        s2 = s2_new
+    target = float(np.mean(np.abs(y) ** 2)) - r0
+    assert target > 0.1 and abs(s2 - target) < 1e-9 * target, (s2, target)
+
+
+def test_noise_mstep_residual_is_the_pupil_noise_power():
+    """With the posterior variance zero and y = e^{j phi} z + w on the pupil (w ~ CN(0, v0)),
+    the update is the sample noise power over the pupil pixels only: within 4 standard errors
+    of v0 (about 6,400 pixels), whatever the data off the pupil."""
+    rng = _rng(13)
+    n = 128
+    a = o.aperture(n, 90.0)
+    z = _crandn(rng, n, n)
+    phi = rng.uniform(-3, 3, (n, n))
+    v0 = 0.37
+    y = np.where(a, np.exp(1j * phi) * z + math.sqrt(v0) * _crandn(rng, n, n), 5.0 * _crandn(rng, n, n))
+    est = o.noise_mstep(y, z, phi, a, np.zeros((n, n)))
+    assert abs(est - v0) < 4 * v0 / math.sqrt(a.sum()), (est, v0)
