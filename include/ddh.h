@@ -52,6 +52,19 @@ typedef struct ddh_params {
   int tilt_mode;        /* 1: RemoveTipTilt each frame; 0: skip it */
   int phase_block;      /* 1: per-pixel phase; 2 or 4: phase constant on aligned G x G tiles,
                            phi_B = angle(sum over the tile of a y~ conj(F mu)) */
+  float phase_prior;    /* p(phi) of Eq. 2 on the tiles (the paper defers its form): precision
+                           1/sigma_phi^2 of a Gaussian MRF on the wrapped differences of
+                           8-neighbour tiles; the tile-phase M-step then minimises
+                           -(2/sigma^2) sum_t |v_t| cos(phi_t - angle v_t) + prior by
+                           `phase_sweeps` majorised 4-colour ICD sweeps from the tile angles.
+                           0 (default): flat prior.  > 0 needs phase_block 2 or 4, n_k = 1,
+                           N <= 256, and steps outside batches and the service */
+  int phase_sweeps;     /* ICD sweeps of that M-step, 1..16 (0 counts as the default, 2) */
+  int noise_update;     /* 1: sigma^2 (noise_var above is then its starting value) is
+                           re-estimated once per frame, after the frame's last EM iteration, by
+                           its EM M-step (1/|P|) sum_pupil |y~ - e^{j phi} F mu|^2 + mean(C);
+                           floored at 1e-6.  N <= 256, outside batches and the service, no
+                           adjoint.  0 (default): sigma^2 fixed */
 } ddh_params;
 
 typedef struct ddh_state ddh_state; /* opaque; owned by the library */
@@ -59,7 +72,7 @@ typedef struct ddh_state ddh_state; /* opaque; owned by the library */
 /* Fill `p` with the defaults for grid `n`, pupil `aperture_diam` and a linear SNR over the
  * pupil: lambda 0.45, alpha 0.025 (Sec. 5.B), n_k 1, noise_var 1/(1 + f SNR) with f the
  * pupil fill fraction, prior p 1.1, q 2, T 1, sigma_r 0.1, r_floor 1e-10, tilt_mode 1,
- * phase_block 1. */
+ * phase_block 1, phase_prior 0, phase_sweeps 2, noise_update 0. */
 int ddh_default_params(ddh_params *p, int n, float aperture_diam, float snr);
 
 /* Static DH-MBIR (Sec. 3: EM iterated on one frame, the reflectance reset to a back-projected
@@ -115,6 +128,10 @@ int ddh_reflectance(const ddh_state *s, float *out);
  * used to resume from a checkpoint and by teacher-forced comparisons. */
 int ddh_set_state(ddh_state *s, const float *r, const float *phi, int64_t frame_index);
 int64_t ddh_frame_index(const ddh_state *s);
+/* The sigma^2 the next frame's E-step will use: the running estimate when noise_update is on
+ * (synchronises the state's stream), else noise_var.  ddh_init, ddh_set_params and
+ * ddh_set_state (re)start the estimate at noise_var; checkpoints carry it. */
+int ddh_noise_estimate(ddh_state *s, float *out);
 /* Replace the state's parameters by `p` (validated; same N, else DDH_EINVAL), keeping r, phi,
  * the frame count and the device buffers.  Host-side only: calls enqueued afterwards use the
  * new values (each launch takes its parameters by value), work already enqueued keeps the old

@@ -32,6 +32,9 @@ class DdhParams(ctypes.Structure):
         ("r_floor", c_float),
         ("tilt_mode", c_int),
         ("phase_block", c_int),
+        ("phase_prior", c_float),
+        ("phase_sweeps", c_int),
+        ("noise_update", c_int),
     ]
 
 
@@ -65,6 +68,7 @@ _SIGS = {
     "ddh_set_state": (c_int, [c_void_p, c_void_p, c_void_p, c_int64]),
     "ddh_frame_index": (c_int64, [c_void_p]),
     "ddh_set_params": (c_int, [c_void_p, POINTER(DdhParams)]),
+    "ddh_noise_estimate": (c_int, [c_void_p, POINTER(c_float)]),
     "ddh_state_stream": (c_void_p, [c_void_p]),
     "ddh_step_host_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ddh_host_wait": (c_int, [c_void_p, c_int64]),

@@ -556,7 +556,7 @@ extern "C" int ddh_step_backward_noalloc(ddh_state* s, const void* y, const floa
                            "use ddh_step_backward with a caller workspace");
     return DDH_EINVAL;
   }
-  if (prm->n_k != 1 || prm->phase_block != 1) return DDH_EINVAL;
+  if (prm->n_k != 1 || prm->phase_block != 1 || prm->phase_prior > 0.f || prm->noise_update) return DDH_EINVAL;
   if (reinterpret_cast<uintptr_t>(y) % 16 != 0 || reinterpret_cast<uintptr_t>(trace) % 8 != 0) return DDH_EINVAL;
   if (dev < 0 || dev >= 64) return DDH_EINVAL;
   cudaError_t e = cudaSetDevice(dev);

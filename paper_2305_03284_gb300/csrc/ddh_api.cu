@@ -3,7 +3,9 @@
 // Host side only: argument validation, device state ownership, parameter derivation, the
 // per-device twiddle tables and kernel attributes, error latching.  Every compute step is one
 // of the kernels in ddh_step.cu.
+#include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -30,6 +32,9 @@ struct ddh_state {
   const float2* tw;
   int64_t frame;
   int64_t ap_count;
+  // side buffer of the tile-phase prior and sigma^2 M-steps (ddh::aux_floats floats; null
+  // while neither is enabled): sigma^2 in use, the step's partial sums and tile sums
+  float* aux = nullptr;
   // pipelined host-buffer steps (ddh_step_host_async), set up on first use: two device staging
   // slots (ystage and hstage2) filled on a copy-in stream, events that order a slot's copy
   // before its step and the step before the slot's next copy, and a ring of completion events
@@ -43,7 +48,7 @@ struct ddh_state {
 
 namespace {
 
-constexpr int kVersion = 100;
+constexpr int kVersion = 101;
 constexpr int kMaxDevices = 64;
 thread_local char g_cuda_err[256] = "";
 
@@ -144,7 +149,60 @@ int validate(const ddh_params* p) {
   if (!(p->r_floor > 0.f && std::isfinite(p->r_floor))) return DDH_EINVAL;
   if (p->tilt_mode != 0 && p->tilt_mode != 1) return DDH_EINVAL;
   if (p->phase_block != 1 && p->phase_block != 2 && p->phase_block != 4) return DDH_EINVAL;
+  if (!(p->phase_prior >= 0.f && std::isfinite(p->phase_prior))) return DDH_EINVAL;
+  if (p->phase_sweeps < 0 || p->phase_sweeps > 16) return DDH_EINVAL;
+  if (p->noise_update != 0 && p->noise_update != 1) return DDH_EINVAL;
+  if (p->phase_prior > 0.f && (p->phase_block == 1 || p->n_k != 1 || p->n > 256)) return DDH_EINVAL;
+  if (p->noise_update && p->n > 256) return DDH_EINVAL;
   return DDH_OK;
+}
+
+bool aux_needed(const ddh_params& p) { return p.phase_prior > 0.f || p.noise_update != 0; }
+
+// The side buffer of the prior / sigma^2 M-steps: allocated when first needed; sigma^2 in use
+// restarts at `nv` (stream-ordered).
+int aux_reset(ddh_state* s, float nv) {
+  if (!aux_needed(s->prm)) return DDH_OK;
+  if (s->aux == nullptr) {
+    DDH_CUDA(cudaMalloc(&s->aux, sizeof(float) * ddh::aux_floats(s->prm.n)));
+    DDH_CUDA(cudaMemsetAsync(s->aux, 0, sizeof(float) * ddh::aux_floats(s->prm.n), s->stream));
+  }
+  const float h[2] = {nv, 0.f};
+  DDH_CUDA(cudaMemcpyAsync(s->aux, h, sizeof(h), cudaMemcpyHostToDevice, s->stream));
+  return DDH_OK;
+}
+
+// The post kernel's arguments for this state: the pupil's tile box from the integer pupil test.
+ddh::PostArgs post_args(const ddh_state* s) {
+  ddh::PostArgs a{};
+  const int n = s->prm.n, gs = s->kp.g_shift;
+  a.aux = s->aux;
+  a.phi = s->phi;
+  a.n = n;
+  a.gs = gs;
+  a.ap_lim = s->kp.ap_lim;
+  a.ctas = n / ddh::kRowsPerCta;
+  a.prior = s->prm.phase_prior > 0.f ? 1 : 0;
+  a.sweeps = s->prm.phase_sweeps > 0 ? s->prm.phase_sweeps : 2;
+  a.noise_update = s->prm.noise_update;
+  a.lam = s->prm.phase_prior;
+  a.inv_ap_count = s->ap_count > 0 ? static_cast<float>(1.0 / static_cast<double>(s->ap_count)) : 0.f;
+  a.inv_m = static_cast<float>(1.0 / (static_cast<double>(n) * n));
+  a.nv_floor = 1e-6f;
+  // a column x holds pupil pixels iff (2x - (n-1))^2 + min_y (2y - (n-1))^2 <= ap_lim
+  int64_t miny = INT64_MAX;
+  for (int y = 0; y < n; ++y) miny = std::min<int64_t>(miny, int64_t(2 * y - (n - 1)) * (2 * y - (n - 1)));
+  int lo = n, hi = -1;
+  for (int x = 0; x < n; ++x) {
+    const int64_t dx = 2 * x - (n - 1);
+    if (dx * dx + miny <= a.ap_lim) {
+      lo = std::min(lo, x);
+      hi = std::max(hi, x);
+    }
+  }
+  a.t_lo = hi >= lo ? lo >> gs : 0;
+  a.nt = hi >= lo ? (hi >> gs) - a.t_lo + 1 : 0;
+  return a;
 }
 
 ddh::KParams derive(const ddh_params& p) {
@@ -227,7 +285,12 @@ int enqueue(ddh_state* s, const void* y, float* trace) {
   b.fa[0] = frame_args(s, y, trace);
   b.tw = s->tw;
   b.count = 1;
+  if (s->aux != nullptr && aux_needed(s->prm)) {
+    b.fa[0].aux = s->aux;
+    b.fa[0].aux_tiles = s->prm.phase_prior > 0.f ? 1 : 0;
+  }
   DDH_CUDA(ddh::launch_step(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], b, s->stream, /*pdl=*/true));
+  if (b.fa[0].aux != nullptr) DDH_CUDA(ddh::launch_post(post_args(s), s->stream));
   s->frame += 1;
   return DDH_OK;
 }
@@ -322,8 +385,11 @@ struct CkptHeader {
   uint32_t version;
   ddh_params prm;
   int64_t frame;
+  float noise_est;  // the running sigma^2 estimate (noise_update), else noise_var
+  float pad;
 };
 constexpr uint32_t kMagic = 0x31484444u;  // "DDH1"
+
 
 }  // namespace
 
@@ -378,6 +444,9 @@ int ddh_default_params(ddh_params* p, int n, float aperture_diam, float snr) {
   p->r_floor = 1e-10f;
   p->tilt_mode = 1;
   p->phase_block = 1;
+  p->phase_prior = 0.f;
+  p->phase_sweeps = 2;
+  p->noise_update = 0;
   return DDH_OK;
 }
 
@@ -423,6 +492,11 @@ int ddh_init(ddh_state** out, const ddh_params* p, void* cuda_stream) {
     const int code = cuda_fail(e);
     ddh_free(s);
     return code;
+  }
+  rc = aux_reset(s, p->noise_var);
+  if (rc != DDH_OK) {
+    ddh_free(s);
+    return rc;
   }
   *out = s;
   return DDH_OK;
@@ -519,16 +593,31 @@ int ddh_set_state(ddh_state* s, const float* r, const float* phi, int64_t frame_
   DDH_CUDA(cudaMemcpyAsync(s->phi, phi, img, cudaMemcpyDefault, s->stream));
   if (is_host_pointer(r) || is_host_pointer(phi)) DDH_CUDA(cudaStreamSynchronize(s->stream));
   s->frame = frame_index;
-  return DDH_OK;
+  return aux_reset(s, s->prm.noise_var);
 }
 
 int64_t ddh_frame_index(const ddh_state* s) { return s ? s->frame : -1; }
 
 int ddh_set_params(ddh_state* s, const ddh_params* p) {
   if (s == nullptr || p == nullptr || validate(p) != DDH_OK || p->n != s->prm.n) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
   s->prm = *p;
   s->kp = derive(*p);
   s->ap_count = aperture_count(p->n, aperture_limit(p->aperture_diam));
+  return aux_reset(s, p->noise_var);
+}
+
+int ddh_noise_estimate(ddh_state* s, float* out) {
+  if (s == nullptr || out == nullptr) return DDH_EINVAL;
+  if (s->aux == nullptr || !aux_needed(s->prm) || !s->prm.noise_update) {
+    *out = s->prm.noise_var;
+    return DDH_OK;
+  }
+  DDH_CUDA(cudaSetDevice(s->device));
+  float h = 0.f;
+  DDH_CUDA(cudaMemcpyAsync(&h, s->aux, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  DDH_CUDA(cudaStreamSynchronize(s->stream));
+  *out = h;
   return DDH_OK;
 }
 void* ddh_state_stream(const ddh_state* s) { return s ? static_cast<void*>(s->stream) : nullptr; }
@@ -552,6 +641,7 @@ static int validate_batch(ddh_state* const* states, int count) {
   if (states == nullptr || count < 0) return DDH_EINVAL;
   for (int i = 0; i < count; ++i) {
     if (states[i] == nullptr) return DDH_EINVAL;
+    if (aux_needed(states[i]->prm)) return DDH_EINVAL;  // the post-step M-steps run per stream only
     if (states[i]->stream != states[0]->stream || states[i]->device != states[0]->device) return DDH_EINVAL;
     for (int j = 0; j < i; ++j)
       if (states[j] == states[i]) return DDH_EINVAL;  // a stream advances once per batch
@@ -676,7 +766,7 @@ int ddh_step_backward(ddh_state* s, const void* y, const float* r_prev, const fl
       r_new == nullptr || r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr ||
       phi_prev_bar == nullptr || grads == nullptr || workspace == nullptr)
     return DDH_EINVAL;
-  if (s->prm.n_k != 1 || s->prm.phase_block != 1 || !cluster_n(s->prm.n)) return DDH_EINVAL;
+  if (s->prm.n_k != 1 || s->prm.phase_block != 1 || !cluster_n(s->prm.n) || aux_needed(s->prm)) return DDH_EINVAL;
   if (workspace_bytes < ddh_backward_workspace_bytes(s->prm.n)) return DDH_EINVAL;
   if (reinterpret_cast<uintptr_t>(y) % 16 != 0 || reinterpret_cast<uintptr_t>(workspace) % 16 != 0 ||
       reinterpret_cast<uintptr_t>(trace) % 8 != 0)
@@ -699,6 +789,7 @@ int ddh_unrolled_forward(ddh_state* s, int k_frames, const void* const* ys, floa
                          float* const* phi_ckpt) {
   DdhNvtxRange nv("ddh_unrolled_forward");
   if (s == nullptr || ys == nullptr || r_ckpt == nullptr || phi_ckpt == nullptr || k_frames < 1) return DDH_EINVAL;
+  if (aux_needed(s->prm)) return DDH_EINVAL;  // no adjoint through the post-step M-steps
   DDH_CUDA(cudaSetDevice(s->device));
   const size_t img = image_bytes(s->prm.n);
   for (int k = 0; k <= k_frames; ++k) {
@@ -805,7 +896,11 @@ int ddh_save(ddh_state* s, void* buf, size_t bytes) {
   h.version = kVersion;
   h.prm = s->prm;
   h.frame = s->frame;
+  h.noise_est = s->prm.noise_var;
   std::memcpy(buf, &h, sizeof(h));
+  if (s->aux != nullptr && aux_needed(s->prm) && s->prm.noise_update)  // the running estimate
+    DDH_CUDA(cudaMemcpyAsync(static_cast<char*>(buf) + offsetof(CkptHeader, noise_est), s->aux, sizeof(float),
+                             cudaMemcpyDeviceToHost, s->stream));
   char* p = static_cast<char*>(buf) + sizeof(h);
   const size_t img = image_bytes(s->prm.n);
   DDH_CUDA(cudaMemcpyAsync(p, s->r, img, cudaMemcpyDeviceToHost, s->stream));
@@ -829,6 +924,9 @@ int ddh_load(ddh_state* s, const void* buf, size_t bytes) {
   s->kp = derive(h.prm);
   s->ap_count = aperture_count(h.prm.n, aperture_limit(h.prm.aperture_diam));
   s->frame = h.frame;
+  const int rc = aux_reset(s, h.noise_est);
+  if (rc != DDH_OK) return rc;
+  DDH_CUDA(cudaStreamSynchronize(s->stream));
   return DDH_OK;
 }
 
@@ -842,6 +940,7 @@ int ddh_free(ddh_state* s) {
   cudaFree(s->ystage);
   cudaFree(s->scalar);
   cudaFree(s->l2scratch);
+  cudaFree(s->aux);
   if (s->cin != nullptr) {
     cudaStreamSynchronize(s->cin);
     cudaStreamDestroy(s->cin);

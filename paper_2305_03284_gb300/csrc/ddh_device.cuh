@@ -239,6 +239,17 @@ __device__ __forceinline__ float wrap_pi(float d) {
 // (`ap_lim` = floor(d^2)).
 __device__ __forceinline__ int ap_dist2(int v, int n) { const int t = 2 * v - (n - 1); return t * t; }
 
+// Tile (T, X) of the G x G tile grid (G = 2^gs) holds a pupil pixel: the tile's smallest
+// squared distances along y and along x together (the test is separable and exact).
+__device__ __forceinline__ bool tile_in_pupil(int T, int X, int gs, int n, int ap_lim) {
+  int my = 1 << 30, mx = 1 << 30;
+  for (int j = 0; j < (1 << gs); ++j) {
+    my = min(my, ap_dist2((T << gs) + j, n));
+    mx = min(mx, ap_dist2((X << gs) + j, n));
+  }
+  return my + mx <= ap_lim;
+}
+
 // q-GGMRF surrogate weight rho'(D)/D for q = 2:
 //   (T sigma)^(p-2) sigma^(-p) (q/p + u) / (1 + u)^2,  u = (|D| / (T sigma))^(q - p).
 __device__ __forceinline__ float prior_weight(float delta, float w0, float inv_tsig, float q_minus_p,

@@ -30,13 +30,39 @@ struct KParams {
   float r_floor;
 };
 
-// One stream's frame: input, state (in/out), status word, optional trace output.
+// One stream's frame: input, state (in/out), status word, optional trace output, optional
+// side outputs for the post kernel (`aux`, below).
 struct FrameArgs {
   const float2* y;
   float* r;
   float* phi;
   unsigned* status;
   float* trace;
+  float* aux;      // null: sigma^2 from KParams, no side outputs
+  int aux_tiles;   // 1: write the pupil tiles' sums (phase prior), 0: per-CTA residual partials
+};
+
+// Per-stream side buffer of the tile-phase prior and sigma^2 M-steps (aux_floats(n) floats):
+//   aux[0]                     sigma^2 in use: read by the step kernel after its dependency
+//                              wait, replaced by the post kernel when sigma^2 is re-estimated
+//   aux[1]                     1 when the step accepted the frame, 0 when it dropped it
+//   aux[kAuxPart + 2k, + 1]    CTA k's sums: pupil residual at the tile angles, sum of C
+//   aux[kAuxTiles ...]         float4 per tile of the N/G x N/G grid (row-major), written for
+//                              the tiles that hold a pupil pixel: (Re v_t, Im v_t, E_t, 0),
+//                              v_t = sum a y~ conj(z), E_t = sum a (|y~|^2 + |z|^2)
+constexpr int kAuxPart = 16;
+constexpr int kAuxTiles = 64;
+inline size_t aux_floats(int n) { return kAuxTiles + size_t(4) * (n / 2) * (n / 2); }
+
+struct PostArgs {
+  float* aux;
+  float* phi;
+  int n, gs, ap_lim, ctas;    // grid, log2 tile, pupil limit, CTAs of the step kernel
+  int prior, sweeps, noise_update;
+  float lam;                  // precision of the tile-phase prior
+  float inv_ap_count, inv_m;  // 1 / |P|, 1 / N^2
+  float nv_floor;
+  int t_lo, nt;               // the pupil tiles lie in [t_lo, t_lo + nt)^2
 };
 
 struct StepBatch {
@@ -102,6 +128,9 @@ struct Fft2Args {
 cudaError_t launch_step(int n, int schedule, const StepBatch& b, cudaStream_t st, bool pdl = false);
 cudaError_t launch_strehl(int n, const StrehlArgs& a, cudaStream_t st);
 cudaError_t launch_fft2(int n, const Fft2Args& a, cudaStream_t st);
+// Post-step kernel (one CTA; programmatic launch): prior-weighted tile-phase M-step and/or
+// the sigma^2 M-step from the step kernel's side outputs.
+cudaError_t launch_post(const PostArgs& a, cudaStream_t st);
 // One-time per-device function attributes (shared memory size, cluster size); also checks
 // that a cluster of this shape can be resident.  Returns cudaSuccess or the failing error.
 cudaError_t configure(int n, int* max_active_clusters);

@@ -164,6 +164,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
 
   // ---- phase 0b: the state written by the previous frame: phi rows (r slab after B1's arrival)
   grid_dep_wait();
+  // sigma^2 of this frame: the stream's running estimate when it is re-estimated (written by
+  // the previous frame's post kernel), else the parameter
+  const float nv = A.aux != nullptr ? A.aux[0] : P.noise_var;
   {
     // phi rows rho and rho + 1 (the latter for the y tip/tilt pairs), 16-byte vectors
     constexpr int NV4 = N / 4;
@@ -277,6 +280,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   const float scale = glob[2];
   const float tx = glob[3], ty = glob[4];
   if (glob[5] != 0.f) {  // uniform across the cluster: every CTA combined the same partials
+    if (A.aux != nullptr && k == 0 && tid == 0) A.aux[1] = 0.f;  // the post kernel keeps the state
     cluster.sync();
     return;
   }
@@ -284,6 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   for (int it = 0; it < P.n_k; ++it) {
     const bool first = (it == 0);
     float* trace = first ? A.trace : nullptr;
+    const bool aux_out = A.aux != nullptr && it == P.n_k - 1;  // side outputs of the last iteration
     // ---- phase 2: back-projection prologue a e^{-j phi} y~ and row IFFT (aperture rows) --
     {
       const int l = warp, rho = row_of<C>(k, l, P.g_shift);
@@ -341,13 +346,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
         };
         fft_row_from<N, +1, V>(cb, tw, lane, gather);
       }
+      float csum = 0.f;  // sum of the posterior variances C = sigma^2 w (side output)
       for (int rho = lane; rho < N; rho += 32) {
         const float2 b = c_scale(cb[swz(rho)], invN);
         const float rp = rS[cl * CS + rho];
         const float ri = first ? fmaxf(fmaf(P.lam1, rp, P.lam_alpha * c_abs2(b)), P.r_floor) : rp;
-        const float wgt = ri * hw_rcp(ri + P.noise_var);
+        const float wgt = ri * hw_rcp(ri + nv);
         const float2 mu = c_scale(b, wgt);
-        const float s = fmaf(P.noise_var, wgt, c_abs2(mu));
+        const float s = fmaf(nv, wgt, c_abs2(mu));
+        if (aux_out) csum += nv * wgt;
         cb[swz(rho)] = mu;
         rS[cl * CS + rho] = ri;
         sS[cl * CS + rho] = s;
@@ -362,6 +369,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           trace[6 * M + gi] = ri;
           trace[7 * M + gi] = s;
         }
+      }
+      if (aux_out) {
+        csum = warp_sum(csum);
+        if (lane == 0) red[warp] = csum;
       }
       __syncwarp();
       fft_row<N, -1, V>(cb, tw, lane);
@@ -467,10 +478,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       if (row_ap) fft_row<N, -1, V>(rb, tw, lane);
       for (int x = lane; x < N; x += 32) {
         float2 v = make_float2(0.f, 0.f);
+        float e = 0.f;  // a (|y~|^2 + |z|^2) (side output)
         if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
           const float2 z = c_scale(rb[swz(x)], invN);
           const float2 yt = c_scale(c_sub(yr[x], ymean), scale);
           v = make_float2(fmaf(yt.x, z.x, yt.y * z.y), fmaf(yt.y, z.x, -yt.x * z.y));
+          if (aux_out) e = c_abs2(yt) + c_abs2(z);
           if (trace != nullptr) {
             const size_t M = static_cast<size_t>(N) * N;
             reinterpret_cast<float2*>(trace)[2 * M + static_cast<size_t>(rho) * N + x] = z;
@@ -479,8 +492,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
         for (int o = 1; o < G; o <<= 1) {  // sum over the G consecutive x of the tile
           v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
           v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+          if (aux_out) e += __shfl_xor_sync(0xffffffffu, e, o);
         }
         rb[swz(x)] = v;
+        if (aux_out) phin[l * N + x] = e;  // phin (the tip/tilt rows) is free after phase 1
       }
     }
     if (P.g_shift > 0) __syncthreads();  // tile rows are other warps of this CTA
@@ -503,6 +518,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
       }
     }
     __syncthreads();  // the surrogate weights (formed around B3) and phase 4 are complete
+    if (aux_out) {
+      // Side outputs for the post kernel, per G x G tile of this CTA's rows: the tile sums
+      // v_t (as in the phase step) and E_t.  With the phase prior they go to the tile grid;
+      // otherwise the tile phase is angle(v_t) and the pupil residual sum |y~ - e^{j phi} z|^2
+      // over the tile is E_t - 2 |v_t|, summed here.  Then this CTA's two partial sums.
+      const int gs = P.g_shift, G = 1 << gs, NT = N >> gs;
+      float res = 0.f;
+      for (int t = tid; t < (R >> gs) * NT; t += kThreads) {
+        const int tl = t / NT, tx = t - tl * NT;
+        const int l0 = tl << gs, x0 = tx << gs;
+        float2 v = rowbuf[l0 * RS + swz(x0)];
+        float e = phin[l0 * N + x0];
+        for (int j = 1; j < G; ++j) {
+          v = c_add(v, rowbuf[(l0 + j) * RS + swz(x0)]);
+          e += phin[(l0 + j) * N + x0];
+        }
+        if (A.aux_tiles) {
+          const int T = row_of<C>(k, l0, gs) >> gs;
+          if (tile_in_pupil(T, tx, gs, N, P.ap_lim))
+            reinterpret_cast<float4*>(A.aux + kAuxTiles)[T * NT + tx] = make_float4(v.x, v.y, e, 0.f);
+        } else {
+          res += e - 2.f * sqrtf(fmaf(v.x, v.x, v.y * v.y));
+        }
+      }
+      res = warp_sum(res);
+      if (lane == 0) red[16 + warp] = res;
+      __syncthreads();
+      if (tid == 0) {
+        float sr = 0.f, sc = 0.f;
+        for (int w = 0; w < 16; ++w) {
+          sr += red[16 + w];
+          sc += red[w];
+        }
+        A.aux[kAuxPart + 2 * k] = sr;
+        A.aux[kAuxPart + 2 * k + 1] = sc;
+        if (k == 0) A.aux[1] = 1.f;
+      }
+    }
     // ---- phase 5: r M-step, 4-colour ICD sweep on the q-GGMRF surrogate ------------------
     {
       float* bE = reinterpret_cast<float*>(colbuf);

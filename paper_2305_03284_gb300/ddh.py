@@ -142,6 +142,13 @@ class Stream:
         check(lib().ddh_set_params(self._h, byref(params)))
         self.params = params
 
+    def noise_estimate(self) -> float:
+        """sigma^2 the next frame will use: the running estimate with ``noise_update``
+        (synchronises the stream), else ``noise_var``."""
+        v = c_float()
+        check(lib().ddh_noise_estimate(self._h, byref(v)))
+        return float(v.value)
+
     @property
     def frame_index(self) -> int:
         return int(lib().ddh_frame_index(self._h))

@@ -51,6 +51,24 @@ def test_default_params_match_oracle(lib, n, d, snr):
     assert math.isclose(p.noise_var, ref.noise_var, rel_tol=1e-6)
     assert math.isclose(p.prior_sigma, ref.prior_sigma, rel_tol=1e-7)
     assert p.prior_q == 2.0 and math.isclose(p.prior_p, 1.1, rel_tol=1e-7)
+    assert (p.phase_prior, p.phase_sweeps, p.noise_update) == (ref.phase_prior, ref.phase_sweeps, ref.noise_update)
+
+
+@pytest.mark.parametrize("over", [{"phase_prior": 1.0}, {"phase_prior": 1.0, "phase_block": 2, "n_k": 2},
+                                  {"phase_prior": -1.0}, {"phase_prior": float("nan"), "phase_block": 2},
+                                  {"phase_sweeps": 17}, {"phase_sweeps": -1}, {"noise_update": 2},
+                                  {"n": 512, "aperture_diam": 256.0, "noise_update": 1},
+                                  {"n": 512, "aperture_diam": 256.0, "phase_prior": 1.0, "phase_block": 2}])
+def test_init_rejects_unsupported_prior_and_noise_options(lib, over):
+    """Parameter validation runs before any CUDA call, so it is checked without a GPU."""
+    from paper_2305_03284_gb300._lib import DdhParams, DDH_EINVAL
+    p = DdhParams()
+    n = over.get("n", 64)
+    assert lib.ddh_default_params(ctypes.byref(p), n, over.get("aperture_diam", 32.0), 10.0) == 0
+    for k, v in over.items():
+        setattr(p, k, v)
+    h = ctypes.c_void_p()
+    assert lib.ddh_init(ctypes.byref(h), ctypes.byref(p), None) == DDH_EINVAL
 
 
 def test_default_params_rejects_bad_grid(lib):

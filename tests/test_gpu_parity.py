@@ -32,7 +32,9 @@ def oracle_params(p) -> o.Params:
     return o.Params(n=p.n, aperture_diam=float(p.aperture_diam), lam=float(p.lam), alpha=float(p.alpha),
                     n_k=p.n_k, noise_var=float(p.noise_var), prior_p=float(p.prior_p),
                     prior_q=float(p.prior_q), prior_T=float(p.prior_T), prior_sigma=float(p.prior_sigma),
-                    r_floor=float(p.r_floor), tilt_mode=p.tilt_mode, phase_block=p.phase_block)
+                    r_floor=float(p.r_floor), tilt_mode=p.tilt_mode, phase_block=p.phase_block,
+                    phase_prior=float(p.phase_prior), phase_sweeps=p.phase_sweeps or 2,
+                    noise_update=p.noise_update)
 
 
 def rel_l2(a, b):
