@@ -540,6 +540,29 @@ def run_ours(args):
                       "em_iterations_per_s": 1e6 / us_it,
                       "definition": "one 256^2 frame, r reset to the back-projection then 200 EM "
                                     "iterations per launch (ddh_static_params), CUDA events"}
+        # ---- tile-phase prior and sigma^2 M-step (post-step kernel) against the plain step --
+        prior = None
+        if world == 1:
+            prior = {}
+            for name, over in (("tiles_2x2", {"phase_block": 2}),
+                               ("tiles_2x2_prior_20_noise_update", {"phase_block": 2, "phase_prior": 20.0,
+                                                                    "noise_update": 1}),
+                               ("per_pixel_noise_update", {"noise_update": 1})):
+                sp = ddh.Stream(ddh.default_params(n, cfg.aperture_diam, cfg.snr, **over), stream=stream)
+                for i in range(5):
+                    lib.ddh_step(sp._h, ptrs[i % len(ptrs)])
+                stream.synchronize()
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                for i in range(200):
+                    lib.ddh_step(sp._h, ptrs[i % len(ptrs)])
+                c1.record(stream)
+                c1.synchronize()
+                sp.sync()
+                us = c0.elapsed_time(c1) * 1e3 / 200
+                prior[name] = {"us_per_frame": us, "frames_per_s": 1e6 / us}
+            prior["definition"] = ("256^2 stream, 200 frames back to back (CUDA events); the prior and "
+                                   "sigma^2 variants add the post-step kernel per frame")
         # ---- end to end through the pipelined host-buffer call ---------------------------
         # pinned host frames in, every frame's phase back to pinned host memory; four output
         # buffers in rotation, each reused only after its previous frame has arrived
@@ -597,6 +620,7 @@ def run_ours(args):
         "e2e": {"value": ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 4,
                 "steps": ke},
         "static_mode": static,
+        "phase_prior_noise_update": prior,
         "n_k_sweep": nk,
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
