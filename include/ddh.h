@@ -106,12 +106,16 @@ size_t ddh_trace_floats(int n);
  * The device staging buffer is owned by the state. */
 int ddh_step_host(ddh_state *s, const void *y_c64_host, float *phi_host_out);
 
-/* Pipelined form of ddh_step_host: enqueues the frame's copy in (on a library copy stream,
- * into one of two device staging slots), the step, and the copy of phi out, and returns at
- * once with `*ticket` = this frame's sequence number on the state, so that frame n+1's copy in
- * overlaps frame n's step.  Both host buffers should be pinned (pageable memory makes the
- * copies synchronous) and stay untouched until ddh_host_wait(s, ticket) or ddh_sync(s)
- * returns.  Errors latched by the step (non-finite frame, timeout) surface at ddh_sync.
+/* Pipelined form of ddh_step_host: enqueues the frame's step and returns at once with
+ * `*ticket` = this frame's sequence number on the state.  When both host buffers are pinned and
+ * mapped into the device's address space (cudaHostAlloc / torch pin_memory), N <= 256 and
+ * neither post-step M-step (phase_prior, noise_update) is on, the step kernel reads the frame
+ * and writes phi over the CPU-GPU link itself: one launch per frame, no staging copies (the
+ * same results bit for bit).  Otherwise the frame is copied in on a library copy stream into
+ * one of two device staging slots, so that frame n+1's copy overlaps frame n's step, and phi is
+ * copied out after the step.  Both buffers stay untouched until ddh_host_wait(s, ticket) or
+ * ddh_sync(s) returns (pageable memory makes the staged copies synchronous).  ddh_step_host
+ * takes the in-place route under the same conditions.  Errors latched by the step (non-finite frame, timeout) surface at ddh_sync.
  * Steps of one state must not be enqueued from several threads at once.  The paper has no
  * counterpart (it describes a frame loop, not its host interface). */
 int ddh_step_host_async(ddh_state *s, const void *y_c64_host, float *phi_host_out, int64_t *ticket);

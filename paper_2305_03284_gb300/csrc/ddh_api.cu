@@ -265,12 +265,15 @@ ddh::L2Stream l2_view(ddh_state* s, const void* y) {
   return v;
 }
 
-int enqueue(ddh_state* s, const void* y, float* trace) {
+// One step of `s` on frame `y`.  `y_host`: y is pinned host memory mapped into the device's
+// address space (read in place by the kernel); `phi_host`: also write phi there (cluster path,
+// neither post-step M-step on).
+int enqueue(ddh_state* s, const void* y, float* trace, bool y_host = false, float* phi_host = nullptr) {
   if (s == nullptr || y == nullptr) return DDH_EINVAL;
   if (reinterpret_cast<uintptr_t>(y) % 16 != 0) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(s->device));
   if (!cluster_n(s->prm.n)) {
-    if (trace != nullptr) return DDH_EINVAL;  // no trace output on the L2-staged path
+    if (trace != nullptr || y_host || phi_host != nullptr) return DDH_EINVAL;  // cluster path only
     ddh::L2Batch lb{};
     lb.prm[0] = s->kp;
     lb.st[0] = l2_view(s, y);
@@ -286,9 +289,12 @@ int enqueue(ddh_state* s, const void* y, float* trace) {
   b.tw = s->tw;
   b.count = 1;
   if (s->aux != nullptr && aux_needed(s->prm)) {
+    if (phi_host != nullptr) return DDH_EINVAL;  // the post kernel changes phi after the step
     b.fa[0].aux = s->aux;
     b.fa[0].aux_tiles = s->prm.phase_prior > 0.f ? 1 : 0;
   }
+  b.fa[0].y_host = y_host ? 1 : 0;
+  b.fa[0].phi_host = phi_host;
   DDH_CUDA(ddh::launch_step(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], b, s->stream, /*pdl=*/true));
   if (b.fa[0].aux != nullptr) DDH_CUDA(ddh::launch_post(post_args(s), s->stream));
   s->frame += 1;
@@ -515,6 +521,26 @@ int ddh_step_trace(ddh_state* s, const void* y, float* trace) {
   return enqueue(s, y, trace);
 }
 
+// The device address of pinned, mapped host memory (cudaHostAlloc / cudaHostRegister), or null.
+static void* mapped_host(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Host frames in place: where both buffers are pinned and mapped, the step kernel reads the frame
+// and writes phi over the CPU-GPU link itself (no staging copies, one launch per frame).
+static bool zero_copy(const ddh_state* s, const void* y_host, float* phi_host, const void** yd, float** pd) {
+  if (!cluster_n(s->prm.n) || aux_needed(s->prm)) return false;
+  *yd = mapped_host(y_host);
+  *pd = static_cast<float*>(mapped_host(phi_host));
+  return *yd != nullptr && *pd != nullptr && reinterpret_cast<uintptr_t>(*yd) % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(*pd) % 16 == 0;
+}
+
 static int host_async_setup(ddh_state* s) {
   if (s->cin != nullptr) return DDH_OK;
   int prio = 0;
@@ -535,6 +561,15 @@ int ddh_step_host_async(ddh_state* s, const void* y_host, float* phi_host_out, i
   DDH_CUDA(cudaSetDevice(s->device));
   int rc = host_async_setup(s);
   if (rc != DDH_OK) return rc;
+  const void* yd = nullptr;
+  float* pd = nullptr;
+  if (zero_copy(s, y_host, phi_host_out, &yd, &pd)) {
+    rc = enqueue(s, yd, nullptr, true, pd);
+    if (rc != DDH_OK) return rc;
+    DDH_CUDA(cudaEventRecord(s->ev_done[s->hcount & 7], s->stream));
+    *ticket = s->hcount++;
+    return DDH_OK;
+  }
   const size_t img = image_bytes(s->prm.n);
   const int slot = static_cast<int>(s->hcount & 1);
   float2* stage = slot == 0 ? s->ystage : s->hstage2;
@@ -565,6 +600,13 @@ int ddh_step_host(ddh_state* s, const void* y_host, float* phi_host_out) {
   DdhNvtxRange nv("ddh_step_host");
   if (s == nullptr || y_host == nullptr || phi_host_out == nullptr) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(s->device));
+  const void* yd = nullptr;
+  float* pd = nullptr;
+  if (zero_copy(s, y_host, phi_host_out, &yd, &pd)) {
+    const int rc = enqueue(s, yd, nullptr, true, pd);
+    if (rc != DDH_OK) return rc;
+    return check_status(s);
+  }
   const size_t img = image_bytes(s->prm.n);
   DDH_CUDA(cudaMemcpyAsync(s->ystage, y_host, 2 * img, cudaMemcpyHostToDevice, s->stream));
   int rc = enqueue(s, s->ystage, nullptr);

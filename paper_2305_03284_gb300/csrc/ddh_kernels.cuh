@@ -40,6 +40,9 @@ struct FrameArgs {
   float* trace;
   float* aux;      // null: sigma^2 from KParams, no side outputs
   int aux_tiles;   // 1: write the pupil tiles' sums (phase prior), 0: per-CTA residual partials
+  int y_host;      // 1: y is pinned host memory mapped into the device's address space, read
+                   //    with plain 16-byte loads (not TMA) over the CPU-GPU link
+  float* phi_host; // optional: the frame's phi also written here (pinned, mapped host memory)
 };
 
 // Per-stream side buffer of the tile-phase prior and sigma^2 M-steps (aux_floats(n) floats):

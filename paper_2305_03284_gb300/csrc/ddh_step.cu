@@ -128,7 +128,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0) {
+  if (A.y_host) {
+    // a frame in pinned host memory, read in place over the CPU-GPU link with 16-byte loads
+    constexpr int NV = N / 2;  // float4 (two complex values) per row
+    const float4* y4 = reinterpret_cast<const float4*>(A.y);
+#pragma unroll 4
+    for (int i = tid; i < R * NV; i += kThreads) {
+      const int l = i / NV, xv = i - l * NV;
+      reinterpret_cast<float4*>(ybuf + l * N)[xv] = y4[static_cast<size_t>(row_of<C>(k, l, P.g_shift)) * NV + xv];
+    }
+  } else if (tid == 0) {
     mbar_arrive_expect_tx(mbar, static_cast<uint32_t>(R * N * sizeof(float2)));
     const float2* y = batch.ytab != nullptr ? batch.ytab[batch.ytab_base + sidx] : A.y;
     for (int l = 0; l < R; ++l) {
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   if (k == C - 1)
     for (int i = tid; i < N; i += kThreads) hr[i] = 0.f;
   // bounded wait: on expiry the frame is dropped (flag carried into the B1 statistics)
-  const bool loaded = mbar_wait_bounded(mbar, 0, 1u << 22);
+  const bool loaded = A.y_host ? true : mbar_wait_bounded(mbar, 0, 1u << 22);
   __syncthreads();
 
   // ---- phase 1a: per-row statistics of the frame (Normalize, Eq. 4) ----------------------
@@ -515,6 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           pr[x] = out;
         }
         phi_out[x] = out;
+        if (A.phi_host != nullptr && it == P.n_k - 1) A.phi_host[static_cast<size_t>(rho) * N + x] = out;
       }
     }
     __syncthreads();  // the surrogate weights (formed around B3) and phase 4 are complete

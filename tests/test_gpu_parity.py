@@ -330,6 +330,26 @@ def test_pipelined_host_steps_equal_device_steps(ddh, n):
         b.host_wait(-1)
 
 
+@pytest.mark.parametrize("over", [{}, {"noise_update": 1}, {"phase_block": 2, "phase_prior": 20.0}])
+def test_host_steps_staged_fallbacks(ddh, over):
+    """Pinned buffers take the in-place path (the kernel reads the frame and writes phi over the
+    CPU-GPU link); pageable buffers, and streams whose phi a post-step kernel changes, take the
+    staged copies.  Every combination equals the device-resident steps bitwise."""
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 6, **over)
+    a, b, c = ddh.Stream(p), ddh.Stream(p), ddh.Stream(p)
+    for i in range(6):
+        a.step(cu(ys[i]))
+        out_b = torch.full((64, 64), -7.0, dtype=torch.float32)           # pageable
+        b.step_host(torch.from_numpy(ys[i]).clone(), out_b)
+        out_c = torch.full((64, 64), -7.0, dtype=torch.float32).pin_memory()
+        t = c.step_host_async(torch.from_numpy(ys[i]).pin_memory(), out_c)
+        c.host_wait(t)
+        ref = a.phase().cpu()
+        assert torch.equal(ref, out_b) and torch.equal(ref, out_c), i
+    c.sync()
+
+
 def test_checkpoint_roundtrip(ddh):
     cfg = sy.config_single_64()
     st, ys, ph, p = make(ddh, cfg, 6)
