@@ -403,7 +403,7 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
     return out
 
 
-def adjoint_measure(ddh, streams=16, frames=8, reps=3):
+def adjoint_measure(ddh, streams=16, frames=8, reps=3, store_traces=True):
     """Config 4: 16 streams at 256^2, K = 8 unrolled frame steps each, gradients w.r.t. r0, phi0,
     sigma_r, p and sigma^2 through the autograd Function (forward with per-frame checkpoints,
     then the hand-written adjoint kernels frame by frame in reverse)."""
@@ -425,7 +425,7 @@ def adjoint_measure(ddh, streams=16, frames=8, reps=3):
             sig = torch.tensor(float(p.prior_sigma), dtype=torch.float64, requires_grad=True)
             pp = torch.tensor(float(p.prior_p), dtype=torch.float64, requires_grad=True)
             s2 = torch.tensor(float(p.noise_var), dtype=torch.float64, requires_grad=True)
-            r_k, phi_k = adjoint.unrolled(r0, phi0, sig, pp, s2, ys, p)
+            r_k, phi_k = adjoint.unrolled(r0, phi0, sig, pp, s2, ys, p, store_traces)
             (r_k.sum() + phi_k.square().sum()).backward()
     one_pass()  # warm-up (allocations, first launches)
     torch.cuda.synchronize()
@@ -438,6 +438,7 @@ def adjoint_measure(ddh, streams=16, frames=8, reps=3):
                         "r0, phi0, sigma_r, p, sigma^2 (per-frame checkpoints, hand-written adjoint kernels)",
             "ms_per_pass": el * 1e3, "unrolled_windows_per_s": streams / el,
             "frames_per_s_forward_and_backward": streams * frames / el,
+            "intermediates": "stored by the forward pass" if store_traces else "recomputed per frame in the backward",
             "timing": "host clock around whole passes (forward, checkpoints, backward), device synchronised"}
 
 

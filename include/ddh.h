@@ -195,22 +195,26 @@ int ddh_step_backward(ddh_state *s, const void *y_c64_dev, const float *r_prev, 
  * ddh_unrolled_forward: from the state's current (r, phi), runs frames ys[0..K-1] (device,
  * complex64, 16-byte aligned) and stores the state entering each frame in r_ckpt[k],
  * phi_ckpt[k] (k = 0..K-1) and the final state in r_ckpt[K], phi_ckpt[K] (caller-owned device
- * images, N*N float32).  The state ends in the final state.
+ * images, N*N float32).  `traces` is NULL, or K caller-owned device buffers of
+ * ddh_trace_floats(N) floats (8-byte aligned) that receive each frame's ddh_step_trace output.
+ * The state ends in the final state.
  * ddh_unrolled_backward: given those checkpoints and the loss gradients with respect to the
  * final state (r_bar, phi_bar), writes the gradients with respect to the initial state
  * (r0_bar, phi0_bar) and ADDS the parameter gradients to grads[3] (as ddh_step_backward),
- * frame by frame in reverse: each frame is recomputed from its checkpoint into a trace, then
- * its adjoint runs.  `workspace` is caller-owned device memory of
- * ddh_unrolled_workspace_bytes(N) bytes (16-byte aligned).  Both enqueue on the state's stream;
- * the backward leaves the state at checkpoint 0.  Requirements as ddh_step_backward (N <= 256,
- * n_k = 1, per-pixel phase).  The paper has no counterpart (training through the method is an
- * extension). */
+ * frame by frame in reverse.  With `traces` (the forward's) each frame's adjoint reads its
+ * stored intermediates; with NULL each frame is first recomputed from its checkpoint into a
+ * trace (less memory, one more step per frame); both give the same results bit for bit.
+ * `workspace` is caller-owned device memory of ddh_unrolled_workspace_bytes(N) bytes (16-byte
+ * aligned).  Both enqueue on the state's stream; the backward leaves the state at checkpoint
+ * 0.  Requirements as ddh_step_backward (N <= 256, n_k = 1, per-pixel phase).  The paper has
+ * no counterpart (training through the method is an extension). */
 size_t ddh_unrolled_workspace_bytes(int n);
 int ddh_unrolled_forward(ddh_state *s, int k_frames, const void *const *ys, float *const *r_ckpt,
-                         float *const *phi_ckpt);
+                         float *const *phi_ckpt, float *const *traces);
 int ddh_unrolled_backward(ddh_state *s, int k_frames, const void *const *ys, const float *const *r_ckpt,
-                          const float *const *phi_ckpt, const float *r_bar, const float *phi_bar, float *r0_bar,
-                          float *phi0_bar, float *grads, void *workspace, size_t workspace_bytes);
+                          const float *const *phi_ckpt, const float *const *traces, const float *r_bar,
+                          const float *phi_bar, float *r0_bar, float *phi0_bar, float *grads, void *workspace,
+                          size_t workspace_bytes);
 
 /* Allocation-free variant of ddh_step_backward (the paper has no counterpart; this is a
  * library service).  Same arguments and results without the workspace: the scratch is a

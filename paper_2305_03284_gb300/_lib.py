@@ -92,8 +92,9 @@ _SIGS = {
     "ddh_service_free": (c_int, [c_void_p]),
     "ddh_backward_workspace_bytes": (c_size_t, [c_int]),
     "ddh_unrolled_workspace_bytes": (c_size_t, [c_int]),
-    "ddh_unrolled_forward": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
-    "ddh_unrolled_backward": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_size_t]),
+    "ddh_unrolled_forward": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ddh_unrolled_backward": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p, c_void_p, c_void_p, c_void_p, c_size_t]),
     "ddh_step_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_void_p, c_void_p, c_size_t]),
     "ddh_step_backward_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

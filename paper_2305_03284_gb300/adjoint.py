@@ -3,11 +3,13 @@ kernels of libddh).
 
 ``unrolled(r0, phi0, prior_sigma, prior_p, noise_var, frames, params)`` runs ``len(frames)``
 frame steps from the state ``(r0, phi0)`` and returns the final ``(r_K, phi_K)``.  The
-forward pass keeps one checkpoint of the state per frame (``ddh_unrolled_forward``); the
-backward pass (``ddh_unrolled_backward``) recomputes each frame's intermediates from its
-checkpoint and runs the hand-written adjoint, frame by frame in reverse inside the library,
-giving gradients with respect to ``r0``, ``phi0`` and the scalar tensors ``prior_sigma``,
-``prior_p`` and ``noise_var``.
+forward pass keeps one checkpoint of the state per frame and, with ``store_traces`` (the
+default), each frame's intermediates (``ddh_unrolled_forward``, about 40 bytes per pixel and
+frame in all); the backward pass (``ddh_unrolled_backward``) runs the hand-written adjoint
+frame by frame in reverse inside the library, from the stored intermediates or, without them,
+recomputing each frame from its checkpoint (the same gradients bit for bit), giving gradients
+with respect to ``r0``, ``phi0`` and the scalar tensors ``prior_sigma``, ``prior_p`` and
+``noise_var``.
 """
 from __future__ import annotations
 
@@ -52,7 +54,7 @@ def _ptr_array(base, stride, count):
 
 class UnrolledDDH(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, r0, phi0, prior_sigma, prior_p, noise_var, frames, params):
+    def forward(ctx, r0, phi0, prior_sigma, prior_p, noise_var, frames, params, store_traces=True):
         p = _with(params, prior_sigma, prior_p, noise_var)
         n = int(p.n)
         if (frames.dtype != torch.complex64 or frames.dim() != 3 or tuple(frames.shape[1:]) != (n, n)
@@ -64,12 +66,17 @@ class UnrolledDDH(torch.autograd.Function):
         ys = _ptr_array(frames.data_ptr(), 2 * img, K)
         rc = _ptr_array(ck.data_ptr(), 2 * img, K + 1)
         pc = _ptr_array(ck.data_ptr() + img, 2 * img, K + 1)
+        tr, tc = None, None
+        if store_traces:
+            tf = int(ddh.lib().ddh_trace_floats(n))
+            tr = torch.empty((K, tf), dtype=torch.float32, device="cuda")
+            tc = _ptr_array(tr.data_ptr(), 4 * tf, K)
         with _lock:
             s = _state(p, torch.cuda.current_stream())
             s.set_state(r0.detach().contiguous(), phi0.detach().contiguous(), 0)
-            ddh.check(ddh.lib().ddh_unrolled_forward(s._h, K, ys, rc, pc))
+            ddh.check(ddh.lib().ddh_unrolled_forward(s._h, K, ys, rc, pc, tc))
         r_k, phi_k = ck[K, 0].clone(), ck[K, 1].clone()
-        ctx.params, ctx.stream, ctx.ck, ctx.arrays = p, s, ck, (ys, rc, pc)
+        ctx.params, ctx.stream, ctx.ck, ctx.traces, ctx.arrays = p, s, ck, tr, (ys, rc, pc, tc)
         ctx.save_for_backward(frames)
         return r_k, phi_k
 
@@ -77,7 +84,7 @@ class UnrolledDDH(torch.autograd.Function):
     def backward(ctx, r_bar, phi_bar):
         (frames,) = ctx.saved_tensors
         p, s, ck = ctx.params, ctx.stream, ctx.ck
-        ys, rc, pc = ctx.arrays
+        ys, rc, pc, tc = ctx.arrays
         n, K = p.n, frames.shape[0]
         L = ddh.lib()
         wsb = L.ddh_unrolled_workspace_bytes(n)
@@ -93,13 +100,13 @@ class UnrolledDDH(torch.autograd.Function):
                 t.record_stream(s.torch_stream)
         with _lock:
             s.set_params(p)
-            ddh.check(L.ddh_unrolled_backward(s._h, K, ys, rc, pc, c_void_p(rb.data_ptr()), c_void_p(pb.data_ptr()),
+            ddh.check(L.ddh_unrolled_backward(s._h, K, ys, rc, pc, tc, c_void_p(rb.data_ptr()), c_void_p(pb.data_ptr()),
                                               c_void_p(r0b.data_ptr()), c_void_p(p0b.data_ptr()),
                                               c_void_p(grads.data_ptr()), c_void_p(ws.data_ptr()), wsb))
         s.sync()  # waits for the adjoint and raises a latched device error (a non-finite frame)
         g = grads.to(torch.float64)
-        return r0b, p0b, g[0], g[1], g[2], None, None
+        return r0b, p0b, g[0], g[1], g[2], None, None, None
 
 
-def unrolled(r0, phi0, prior_sigma, prior_p, noise_var, frames, params):
-    return UnrolledDDH.apply(r0, phi0, prior_sigma, prior_p, noise_var, frames, params)
+def unrolled(r0, phi0, prior_sigma, prior_p, noise_var, frames, params, store_traces=True):
+    return UnrolledDDH.apply(r0, phi0, prior_sigma, prior_p, noise_var, frames, params, store_traces)

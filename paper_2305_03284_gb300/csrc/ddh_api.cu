@@ -828,7 +828,7 @@ size_t ddh_unrolled_workspace_bytes(int n) {
 }
 
 int ddh_unrolled_forward(ddh_state* s, int k_frames, const void* const* ys, float* const* r_ckpt,
-                         float* const* phi_ckpt) {
+                         float* const* phi_ckpt, float* const* traces) {
   DdhNvtxRange nv("ddh_unrolled_forward");
   if (s == nullptr || ys == nullptr || r_ckpt == nullptr || phi_ckpt == nullptr || k_frames < 1) return DDH_EINVAL;
   if (aux_needed(s->prm)) return DDH_EINVAL;  // no adjoint through the post-step M-steps
@@ -839,15 +839,18 @@ int ddh_unrolled_forward(ddh_state* s, int k_frames, const void* const* ys, floa
     DDH_CUDA(cudaMemcpyAsync(r_ckpt[k], s->r, img, cudaMemcpyDeviceToDevice, s->stream));
     DDH_CUDA(cudaMemcpyAsync(phi_ckpt[k], s->phi, img, cudaMemcpyDeviceToDevice, s->stream));
     if (k == k_frames) break;
-    const int rc = enqueue(s, ys[k], nullptr);
+    float* tr = traces != nullptr ? traces[k] : nullptr;
+    if (traces != nullptr && (tr == nullptr || reinterpret_cast<uintptr_t>(tr) % 8 != 0)) return DDH_EINVAL;
+    const int rc = enqueue(s, ys[k], tr);
     if (rc != DDH_OK) return rc;
   }
   return DDH_OK;
 }
 
 int ddh_unrolled_backward(ddh_state* s, int k_frames, const void* const* ys, const float* const* r_ckpt,
-                          const float* const* phi_ckpt, const float* r_bar, const float* phi_bar, float* r0_bar,
-                          float* phi0_bar, float* grads, void* workspace, size_t workspace_bytes) {
+                          const float* const* phi_ckpt, const float* const* traces, const float* r_bar,
+                          const float* phi_bar, float* r0_bar, float* phi0_bar, float* grads, void* workspace,
+                          size_t workspace_bytes) {
   DdhNvtxRange nv("ddh_unrolled_backward");
   if (s == nullptr || ys == nullptr || r_ckpt == nullptr || phi_ckpt == nullptr || r_bar == nullptr ||
       phi_bar == nullptr || r0_bar == nullptr || phi0_bar == nullptr || grads == nullptr || workspace == nullptr ||
@@ -871,16 +874,23 @@ int ddh_unrolled_backward(ddh_state* s, int k_frames, const void* const* ys, con
   for (int k = k_frames - 1; k >= 0; --k) {
     float* rout = k == 0 ? r0_bar : rb[k & 1];
     float* pout = k == 0 ? phi0_bar : pb[k & 1];
-    int rc = ddh_set_state(s, r_ckpt[k], phi_ckpt[k], k);
-    if (rc == DDH_OK) rc = enqueue(s, ys[k], trace);
+    const float* tr = traces != nullptr ? traces[k] : trace;
+    int rc = DDH_OK;
+    if (traces == nullptr) {  // recompute the frame's intermediates from its checkpoint
+      rc = ddh_set_state(s, r_ckpt[k], phi_ckpt[k], k);
+      if (rc == DDH_OK) rc = enqueue(s, ys[k], trace);
+    } else if (tr == nullptr) {
+      rc = DDH_EINVAL;
+    }
     if (rc == DDH_OK)
-      rc = ddh_step_backward(s, ys[k], r_ckpt[k], phi_ckpt[k], trace, r_ckpt[k + 1], rin, pin, rout, pout, grads, bw,
+      rc = ddh_step_backward(s, ys[k], r_ckpt[k], phi_ckpt[k], tr, r_ckpt[k + 1], rin, pin, rout, pout, grads, bw,
                              ddh_backward_workspace_bytes(n));
     if (rc != DDH_OK) return rc;
     rin = rout;
     pin = pout;
   }
   (void)img;
+  if (traces != nullptr) return ddh_set_state(s, r_ckpt[0], phi_ckpt[0], 0);  // as after recomputing
   return DDH_OK;
 }
 

@@ -164,15 +164,28 @@ def test_unrolled_calls_equal_per_frame_calls(mods):
     s.set_state(r0, phi0, 0)
     ck = torch.empty((K + 1, 2, n, n), device="cuda")
     ddh.check(L.ddh_unrolled_forward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck[k, 0] for k in range(K + 1)]),
-                                     ptrs([ck[k, 1] for k in range(K + 1)])))
+                                     ptrs([ck[k, 1] for k in range(K + 1)]), None))
     wsb = L.ddh_unrolled_workspace_bytes(n)
     ws = torch.empty(wsb // 4, device="cuda")
     r0b, p0b, g = torch.empty((n, n), device="cuda"), torch.empty((n, n), device="cuda"), torch.zeros(3, device="cuda")
     ddh.check(L.ddh_unrolled_backward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck[k, 0] for k in range(K + 1)]),
-                                      ptrs([ck[k, 1] for k in range(K + 1)]), c_void_p(rbar.data_ptr()),
+                                      ptrs([ck[k, 1] for k in range(K + 1)]), None, c_void_p(rbar.data_ptr()),
                                       c_void_p(pbar.data_ptr()), c_void_p(r0b.data_ptr()), c_void_p(p0b.data_ptr()),
                                       c_void_p(g.data_ptr()), c_void_p(ws.data_ptr()), wsb))
     s.sync()
+    # the same with the forward's stored traces instead of recomputing each frame
+    s.set_state(r0, phi0, 0)
+    ck2 = torch.empty((K + 1, 2, n, n), device="cuda")
+    trs = torch.empty((K, L.ddh_trace_floats(n)), device="cuda")
+    ddh.check(L.ddh_unrolled_forward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck2[k, 0] for k in range(K + 1)]),
+                                     ptrs([ck2[k, 1] for k in range(K + 1)]), ptrs([trs[k] for k in range(K)])))
+    r0b2, p0b2, gt = torch.empty((n, n), device="cuda"), torch.empty((n, n), device="cuda"), torch.zeros(3, device="cuda")
+    ddh.check(L.ddh_unrolled_backward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck2[k, 0] for k in range(K + 1)]),
+                                      ptrs([ck2[k, 1] for k in range(K + 1)]), ptrs([trs[k] for k in range(K)]),
+                                      c_void_p(rbar.data_ptr()), c_void_p(pbar.data_ptr()), c_void_p(r0b2.data_ptr()),
+                                      c_void_p(p0b2.data_ptr()), c_void_p(gt.data_ptr()), c_void_p(ws.data_ptr()), wsb))
+    s.sync()
+    assert torch.equal(ck, ck2) and torch.equal(r0b, r0b2) and torch.equal(p0b, p0b2) and torch.equal(g, gt)
     # the same through per-frame calls
     t = ddh.Stream(p)
     t.set_state(r0, phi0, 0)
@@ -200,7 +213,7 @@ def test_unrolled_calls_equal_per_frame_calls(mods):
     assert torch.equal(r0b, rb) and torch.equal(p0b, pb) and torch.equal(g, g2)
     with pytest.raises(ddh.DdhError):   # workspace too small
         ddh.check(L.ddh_unrolled_backward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck[k, 0] for k in range(K + 1)]),
-                                          ptrs([ck[k, 1] for k in range(K + 1)]), c_void_p(rbar.data_ptr()),
+                                          ptrs([ck[k, 1] for k in range(K + 1)]), None, c_void_p(rbar.data_ptr()),
                                           c_void_p(pbar.data_ptr()), c_void_p(r0b.data_ptr()), c_void_p(p0b.data_ptr()),
                                           c_void_p(g.data_ptr()), c_void_p(ws.data_ptr()), wsb - 4))
 
@@ -238,3 +251,25 @@ def test_set_params_and_the_reused_adjoint_state(mods):
     g1, g2, g3 = grads(p1), grads(p2), grads(p1)
     assert all(torch.equal(x, y) for x, y in zip(g1, g3))
     assert not torch.equal(g1[0], g2[0])
+
+
+def test_autograd_stored_and_recomputed_traces_agree(mods):
+    """UnrolledDDH with the forward's stored intermediates and with per-frame recomputation:
+    the same gradients bit for bit."""
+    ddh, adjoint = mods
+    K, n = 4, 64
+    cfg = sy.config_single_64(K)
+    ys = torch.from_numpy(sy.Stream(cfg).frames(K)[0]).cuda()
+    p = ddh.default_params(n, cfg.aperture_diam, cfg.snr)
+
+    def grads(store):
+        r0 = torch.full((n, n), 0.05, device="cuda", requires_grad=True)
+        phi0 = torch.zeros((n, n), device="cuda", requires_grad=True)
+        ts = [torch.tensor(float(v), dtype=torch.float64, requires_grad=True)
+              for v in (p.prior_sigma, p.prior_p, p.noise_var)]
+        rK, phiK = adjoint.unrolled(r0, phi0, *ts, ys, p, store_traces=store)
+        (rK.sum() + torch.cos(phiK).sum()).backward()
+        return [r0.grad, phi0.grad] + [t.grad for t in ts]
+
+    a, b = grads(True), grads(False)
+    assert all(torch.equal(x, y) for x, y in zip(a, b))
