@@ -266,14 +266,15 @@ ddh::L2Stream l2_view(ddh_state* s, const void* y) {
 }
 
 // One step of `s` on frame `y`.  `y_host`: y is pinned host memory mapped into the device's
-// address space (read in place by the kernel); `phi_host`: also write phi there (cluster path,
-// neither post-step M-step on).
-int enqueue(ddh_state* s, const void* y, float* trace, bool y_host = false, float* phi_host = nullptr) {
+// address space (read in place by the kernel); `phi_copy`, `r_copy`: also write the frame's phi
+// and r there (cluster path, neither post-step M-step on).
+int enqueue(ddh_state* s, const void* y, float* trace, bool y_host = false, float* phi_copy = nullptr,
+            float* r_copy = nullptr) {
   if (s == nullptr || y == nullptr) return DDH_EINVAL;
   if (reinterpret_cast<uintptr_t>(y) % 16 != 0) return DDH_EINVAL;
   DDH_CUDA(cudaSetDevice(s->device));
   if (!cluster_n(s->prm.n)) {
-    if (trace != nullptr || y_host || phi_host != nullptr) return DDH_EINVAL;  // cluster path only
+    if (trace != nullptr || y_host || phi_copy != nullptr || r_copy != nullptr) return DDH_EINVAL;  // cluster path
     ddh::L2Batch lb{};
     lb.prm[0] = s->kp;
     lb.st[0] = l2_view(s, y);
@@ -289,12 +290,13 @@ int enqueue(ddh_state* s, const void* y, float* trace, bool y_host = false, floa
   b.tw = s->tw;
   b.count = 1;
   if (s->aux != nullptr && aux_needed(s->prm)) {
-    if (phi_host != nullptr) return DDH_EINVAL;  // the post kernel changes phi after the step
+    if (phi_copy != nullptr || r_copy != nullptr) return DDH_EINVAL;  // the post kernel changes phi later
     b.fa[0].aux = s->aux;
     b.fa[0].aux_tiles = s->prm.phase_prior > 0.f ? 1 : 0;
   }
   b.fa[0].y_host = y_host ? 1 : 0;
-  b.fa[0].phi_host = phi_host;
+  b.fa[0].phi_copy = phi_copy;
+  b.fa[0].r_copy = r_copy;
   DDH_CUDA(ddh::launch_step(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], b, s->stream, /*pdl=*/true));
   if (b.fa[0].aux != nullptr) DDH_CUDA(ddh::launch_post(post_args(s), s->stream));
   s->frame += 1;
@@ -834,14 +836,16 @@ int ddh_unrolled_forward(ddh_state* s, int k_frames, const void* const* ys, floa
   if (aux_needed(s->prm)) return DDH_EINVAL;  // no adjoint through the post-step M-steps
   DDH_CUDA(cudaSetDevice(s->device));
   const size_t img = image_bytes(s->prm.n);
-  for (int k = 0; k <= k_frames; ++k) {
+  for (int k = 0; k <= k_frames; ++k)
     if (r_ckpt[k] == nullptr || phi_ckpt[k] == nullptr) return DDH_EINVAL;
-    DDH_CUDA(cudaMemcpyAsync(r_ckpt[k], s->r, img, cudaMemcpyDeviceToDevice, s->stream));
-    DDH_CUDA(cudaMemcpyAsync(phi_ckpt[k], s->phi, img, cudaMemcpyDeviceToDevice, s->stream));
-    if (k == k_frames) break;
+  // checkpoint 0 is the entry state; every step writes its outputs into the next checkpoint as
+  // well as the state (no copies between the launches, which keeps them chained)
+  DDH_CUDA(cudaMemcpyAsync(r_ckpt[0], s->r, img, cudaMemcpyDeviceToDevice, s->stream));
+  DDH_CUDA(cudaMemcpyAsync(phi_ckpt[0], s->phi, img, cudaMemcpyDeviceToDevice, s->stream));
+  for (int k = 0; k < k_frames; ++k) {
     float* tr = traces != nullptr ? traces[k] : nullptr;
     if (traces != nullptr && (tr == nullptr || reinterpret_cast<uintptr_t>(tr) % 8 != 0)) return DDH_EINVAL;
-    const int rc = enqueue(s, ys[k], tr);
+    const int rc = cluster_n(s->prm.n) ? enqueue(s, ys[k], tr, false, phi_ckpt[k + 1], r_ckpt[k + 1]) : DDH_EINVAL;
     if (rc != DDH_OK) return rc;
   }
   return DDH_OK;

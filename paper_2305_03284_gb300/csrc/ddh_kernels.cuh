@@ -42,7 +42,9 @@ struct FrameArgs {
   int aux_tiles;   // 1: write the pupil tiles' sums (phase prior), 0: per-CTA residual partials
   int y_host;      // 1: y is pinned host memory mapped into the device's address space, read
                    //    with plain 16-byte loads (not TMA) over the CPU-GPU link
-  float* phi_host; // optional: the frame's phi also written here (pinned, mapped host memory)
+  float* phi_copy; // optional second destination of the frame's phi (device memory, or pinned
+                   //    host memory mapped into the device's address space)
+  float* r_copy;   // optional second destination of the frame's r (device memory)
 };
 
 // Per-stream side buffer of the tile-phase prior and sigma^2 M-steps (aux_floats(n) floats):

@@ -290,6 +290,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   const float tx = glob[3], ty = glob[4];
   if (glob[5] != 0.f) {  // uniform across the cluster: every CTA combined the same partials
     if (A.aux != nullptr && k == 0 && tid == 0) A.aux[1] = 0.f;  // the post kernel keeps the state
+    // the state stays as it was, and so do its second destinations (rows of phi and the r slab
+    // are in shared memory already)
+    if (A.phi_copy != nullptr)
+      for (int i = tid; i < R * N; i += kThreads) {
+        const int l = i / N, x = i - l * N;
+        A.phi_copy[static_cast<size_t>(row_of<C>(k, l, P.g_shift)) * N + x] = phib[i];
+      }
+    if (A.r_copy != nullptr)
+      for (int i = tid; i < N * W; i += kThreads) {
+        const int rho = i / W, cl = i - rho * W;
+        A.r_copy[static_cast<size_t>(rho) * N + W * k + cl] = rS[cl * CS + rho];
+      }
     cluster.sync();
     return;
   }
@@ -524,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
           pr[x] = out;
         }
         phi_out[x] = out;
-        if (A.phi_host != nullptr && it == P.n_k - 1) A.phi_host[static_cast<size_t>(rho) * N + x] = out;
+        if (A.phi_copy != nullptr && it == P.n_k - 1) A.phi_copy[static_cast<size_t>(rho) * N + x] = out;
       }
     }
     __syncthreads();  // the surrogate weights (formed around B3) and phase 4 are complete
@@ -650,7 +662,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_ddh_step(const __grid_constant_
   // ---- write the reflectance slab back (row-major N x N) ---------------------------------
   for (int i = tid; i < N * W; i += kThreads) {
     const int rho = i / W, cl = i - rho * W;
-    A.r[static_cast<size_t>(rho) * N + W * k + cl] = rS[cl * CS + rho];
+    const float v = rS[cl * CS + rho];
+    A.r[static_cast<size_t>(rho) * N + W * k + cl] = v;
+    if (A.r_copy != nullptr) A.r_copy[static_cast<size_t>(rho) * N + W * k + cl] = v;
   }
 }
 

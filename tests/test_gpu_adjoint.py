@@ -273,3 +273,24 @@ def test_autograd_stored_and_recomputed_traces_agree(mods):
 
     a, b = grads(True), grads(False)
     assert all(torch.equal(x, y) for x, y in zip(a, b))
+
+
+def test_unrolled_forward_dropped_frame_keeps_checkpoints(mods):
+    """A non-finite frame inside the unrolled forward leaves the state, so the next checkpoint
+    equals the previous one (the step writes the checkpoints itself)."""
+    ddh, adjoint = mods
+    K, n = 3, 32
+    cfg = sy.config_adjoint(small=True, streams=1, frames=K)[0]
+    ys_np = sy.Stream(cfg).frames(K)[0]
+    ys_np[1, 2, 2] = np.nan
+    ys = torch.from_numpy(ys_np).cuda()
+    p = ddh.default_params(n, 16.0, cfg.snr)
+    L = ddh.lib()
+    ptrs = lambda ts: (c_void_p * len(ts))(*[c_void_p(t.data_ptr()) for t in ts])
+    s = ddh.Stream(p)
+    ck = torch.full((K + 1, 2, n, n), -7.0, device="cuda")
+    ddh.check(L.ddh_unrolled_forward(s._h, K, ptrs([ys[k] for k in range(K)]), ptrs([ck[k, 0] for k in range(K + 1)]),
+                                     ptrs([ck[k, 1] for k in range(K + 1)]), None))
+    with pytest.raises(ddh.DdhError):
+        s.sync()
+    assert torch.equal(ck[2], ck[1]) and not torch.equal(ck[3], ck[2])

@@ -330,6 +330,24 @@ def test_pipelined_host_steps_equal_device_steps(ddh, n):
         b.host_wait(-1)
 
 
+def test_host_step_in_place_dropped_frame(ddh):
+    """A non-finite frame through the in-place host path: the pinned output receives the
+    unchanged phase (as the staged copy of the kept state would), and the error surfaces."""
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 3)
+    s = ddh.Stream(p)
+    out = torch.full((64, 64), -7.0, dtype=torch.float32).pin_memory()
+    s.host_wait(s.step_host_async(torch.from_numpy(ys[0]).pin_memory(), out))
+    before = out.clone()
+    bad = ys[1].copy()
+    bad[5, 9] = np.inf
+    out2 = torch.full((64, 64), -7.0, dtype=torch.float32).pin_memory()
+    s.host_wait(s.step_host_async(torch.from_numpy(bad).pin_memory(), out2))
+    with pytest.raises(ddh.DdhError):
+        s.sync()
+    assert torch.equal(out2, before) and torch.equal(s.phase().cpu(), before)
+
+
 @pytest.mark.parametrize("over", [{}, {"noise_update": 1}, {"phase_block": 2, "phase_prior": 20.0}])
 def test_host_steps_staged_fallbacks(ddh, over):
     """Pinned buffers take the in-place path (the kernel reads the frame and writes phi over the
