@@ -171,13 +171,25 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
   float* pr = S.phi + static_cast<size_t>(rho) * N;
   if (dy2 <= P.ap_lim) {
     const float tyr = ty * (static_cast<float>(rho) - cc);
-    for (int x = lane; x < N; x += 32) {
+    constexpr int PER = N / 32;
+    float pv[PER];
+    float2 yv[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {  // every load before the first store
+      const int x = lane + 32 * j;
+      const bool in = ap_dist2(x, N) + dy2 <= P.ap_lim;
+      pv[j] = in ? pr[x] : 0.f;
+      yv[j] = in ? y[static_cast<size_t>(rho) * N + x] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int x = lane + 32 * j;
       float2 u = make_float2(0.f, 0.f);
       float ph = 0.f;
       if (ap_dist2(x, N) + dy2 <= P.ap_lim) {
-        ph = pr[x];
+        ph = pv[j];
         if (first && P.tilt_mode) ph = wrap_pi(ph - fmaf(tx, static_cast<float>(x) - cc, tyr));
-        const float2 yt = c_scale(c_sub(y[static_cast<size_t>(rho) * N + x], ymean), scale);
+        const float2 yt = c_scale(c_sub(yv[j], ymean), scale);
         float sn, cs;
         sincosf(ph, &sn, &cs);
         u = make_float2(fmaf(yt.x, cs, yt.y * sn), fmaf(yt.y, cs, -yt.x * sn));
@@ -221,14 +233,32 @@ __global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__
   float* stile = rt + kTc * CW;                             // kTc x CW: s
   for (int i = threadIdx.x; i < N; i += kColThreads) tw[i] = b.tw[i];
   const int x0 = kTc * blockIdx.x;
-  for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {
-    const int c = i / N, rho = i - c * N;
-    cols[c * CW + swz(rho)] =
-        ap_dist2(rho, N) <= P.ap_lim ? S.fb[static_cast<size_t>(x0 + c) * N + rho] : make_float2(0.f, 0.f);
-  }
-  for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {  // coalesced 32-byte row segments
-    const int rho = i / kTc, c = i - rho * kTc;
-    rt[c * CW + rho] = S.r[static_cast<size_t>(rho) * N + x0 + c];
+  {
+    // every load of a thread is issued before its first store (the shared-memory stores could
+    // alias the loads' generic addresses otherwise, which would serialise them)
+    constexpr int PER = kTc * N / kColThreads;
+    float2 fv[PER];
+    float rv[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = threadIdx.x + kColThreads * j, c = i / N, rho = i - c * N;
+      fv[j] = ap_dist2(rho, N) <= P.ap_lim ? S.fb[static_cast<size_t>(x0 + c) * N + rho] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {  // coalesced 32-byte row segments
+      const int i = threadIdx.x + kColThreads * j, rho = i / kTc, c = i - rho * kTc;
+      rv[j] = S.r[static_cast<size_t>(rho) * N + x0 + c];
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = threadIdx.x + kColThreads * j, c = i / N, rho = i - c * N;
+      cols[c * CW + swz(rho)] = fv[j];
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = threadIdx.x + kColThreads * j, rho = i / kTc, c = i - rho * kTc;
+      rt[c * CW + rho] = rv[j];
+    }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -286,16 +316,30 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_consta
   const int dy2 = ap_dist2(rho, N);
   const bool row_ap = dy2 <= P.ap_lim;
   float2* rb = rows + warp * RW;
-  if (row_ap)
-    for (int x = lane; x < N; x += 32) rb[swz(x)] = S.fa[static_cast<size_t>(rho) * N + x];
+  constexpr int PER = N / 32;
+  if (row_ap) {
+    float2 fv[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) fv[j] = S.fa[static_cast<size_t>(rho) * N + lane + 32 * j];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) rb[swz(lane + 32 * j)] = fv[j];
+  }
   __syncthreads();
   if (row_ap) fft_row<N, -1, V>(rb, tw, lane);
   const float invN = 1.f / static_cast<float>(N);
-  for (int x = lane; x < N; x += 32) {
+  float2 yv[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int x = lane + 32 * j;
+    yv[j] = row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim ? y[static_cast<size_t>(rho) * N + x] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int x = lane + 32 * j;
     float2 v = make_float2(0.f, 0.f);
     if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
       const float2 z = c_scale(rb[swz(x)], invN);
-      const float2 yt = c_scale(c_sub(y[static_cast<size_t>(rho) * N + x], ymean), scale);
+      const float2 yt = c_scale(c_sub(yv[j], ymean), scale);
       v = make_float2(fmaf(yt.x, z.x, yt.y * z.y), fmaf(yt.y, z.x, -yt.x * z.y));
     }
     for (int o = 1; o < G; o <<= 1) {
