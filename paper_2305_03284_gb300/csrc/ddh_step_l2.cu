@@ -99,16 +99,22 @@ __global__ void __launch_bounds__(kThreads) k_l2_stats(const __grid_constant__ L
   }
 }
 
-// combine the row-block partials in rank order (identical in every block)
+// combine the row-block partials in rank order (identical in every block); called by one warp:
+// its lanes fetch the B records in parallel into `rec`, lane 0 combines them
 template <int N>
-__device__ void l2_combine(const L2Stream& S, const KParams& P, float* g) {
+__device__ void l2_combine(const L2Stream& S, const KParams& P, float* g, float (*rec)[8], int lane) {
   constexpr int B = N / kT;
+  for (int k = lane; k < B; k += 32)
+#pragma unroll
+    for (int j = 0; j < 7; ++j) rec[k][j] = S.part[8 * k + j];
+  __syncwarp();
+  if (lane != 0) return;
   const float nb = static_cast<float>(kT * N);
-  float n_a = nb, q_a = S.part[2];
-  float2 m_a = make_float2(S.part[0], S.part[1]);
-  float t0 = S.part[3], t1 = S.part[4], t2 = S.part[5], t3 = S.part[6];
+  float n_a = nb, q_a = rec[0][2];
+  float2 m_a = make_float2(rec[0][0], rec[0][1]);
+  float t0 = rec[0][3], t1 = rec[0][4], t2 = rec[0][5], t3 = rec[0][6];
   for (int k = 1; k < B; ++k) {
-    const float* o = S.part + 8 * k;
+    const float* o = rec[k];
     const float nn = n_a + nb;
     const float2 d = make_float2(o[0] - m_a.x, o[1] - m_a.y);
     const float f = nb / nn;
@@ -140,12 +146,13 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
   constexpr int RW = N + 4;
   float2* rows = tw + N;  // kTr rows x RW
   __shared__ float g[8];
+  __shared__ float rec[N / kT][8];
   for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = b.tw[i];
   grid_dep_launch();
   grid_dep_wait();
+  if (first && threadIdx.x < 32) l2_combine<N>(S, P, g, rec, threadIdx.x);
   if (threadIdx.x == 0) {
     if (first) {
-      l2_combine<N>(S, P, g);
       if (blockIdx.x == 0) {
         float* st = S.part + 8 * (N / kT);  // combined statistics for the later stages
         for (int k = 0; k < 6; ++k) st[k] = g[k];
@@ -369,15 +376,30 @@ __global__ void __launch_bounds__(256) k_l2_weights(const __grid_constant__ L2Ba
   grid_dep_wait();
   if (frame_dropped(S)) return;
   constexpr int M = N * N;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-    const int rho = i / N, x = i - rho * N;
-    const float a = S.r0[i];
+  auto wgt = [&](float d) { return prior_weight_fast(d, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p); };
+  // kWPx pixels per thread (the grid covers the image once); all their loads are issued
+  // before the first store, which could alias them otherwise
+  constexpr int kWPx = 2;
+  const int i0 = blockIdx.x * blockDim.x * kWPx + threadIdx.x;
+  float a[kWPx], vE[kWPx], vS[kWPx], vSE[kWPx], vSW[kWPx];
+#pragma unroll
+  for (int u = 0; u < kWPx; ++u) {
+    const int i = i0 + u * blockDim.x, rho = i / N, x = i - rho * N;
     const bool rt = x + 1 < N, dn = rho + 1 < N, lf = x > 0;
-    auto wgt = [&](float d) { return prior_weight_fast(d, P.w0, P.inv_tsig, P.q_minus_p, P.q_over_p); };
-    S.beta[i] = rt ? kBnn * wgt(a - S.r0[i + 1]) : 0.f;
-    S.beta[M + i] = dn ? kBnn * wgt(a - S.r0[i + N]) : 0.f;
-    S.beta[2 * M + i] = (rt && dn) ? kBdiag * wgt(a - S.r0[i + N + 1]) : 0.f;
-    S.beta[3 * M + i] = (lf && dn) ? kBdiag * wgt(a - S.r0[i + N - 1]) : 0.f;
+    a[u] = S.r0[i];
+    vE[u] = rt ? S.r0[i + 1] : 0.f;
+    vS[u] = dn ? S.r0[i + N] : 0.f;
+    vSE[u] = (rt && dn) ? S.r0[i + N + 1] : 0.f;
+    vSW[u] = (lf && dn) ? S.r0[i + N - 1] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < kWPx; ++u) {
+    const int i = i0 + u * blockDim.x, rho = i / N, x = i - rho * N;
+    const bool rt = x + 1 < N, dn = rho + 1 < N, lf = x > 0;
+    S.beta[i] = rt ? kBnn * wgt(a[u] - vE[u]) : 0.f;
+    S.beta[M + i] = dn ? kBnn * wgt(a[u] - vS[u]) : 0.f;
+    S.beta[2 * M + i] = (rt && dn) ? kBdiag * wgt(a[u] - vSE[u]) : 0.f;
+    S.beta[3 * M + i] = (lf && dn) ? kBdiag * wgt(a[u] - vSW[u]) : 0.f;
   }
 }
 
