@@ -350,11 +350,15 @@ __global__ void k_bw_tilt_b(BwParams P, BwBuffers B, int blocks) {
   const int n = P.n, M = n * n;
   __shared__ float g[2];
   __shared__ float sh[3][kBwThreads];
+  __shared__ float tp[2 * kBwMaxBlocks];
+  // the tilt partials are fetched in parallel, then summed in block order by one thread
+  for (int i = threadIdx.x; i < 2 * blocks; i += blockDim.x) tp[i] = B.red[i];
+  __syncthreads();
   if (threadIdx.x == 0) {
     float tx = 0.f, ty = 0.f;
     for (int b = 0; b < blocks; ++b) {
-      tx += B.red[2 * b];
-      ty += B.red[2 * b + 1];
+      tx += tp[2 * b];
+      ty += tp[2 * b + 1];
     }
     g[0] = P.tilt_mode ? tx * P.gx_scale : 0.f;
     g[1] = P.tilt_mode ? ty * P.gy_scale : 0.f;
@@ -395,9 +399,13 @@ __global__ void k_bw_tilt_b(BwParams P, BwBuffers B, int blocks) {
 __global__ void k_bw_grads(BwBuffers B, int blocks) {
   grid_dep_launch();
   grid_dep_wait();
+  __shared__ float pp[3 * kBwMaxBlocks];
+  // the partials are fetched in parallel, then each sum runs in block order
+  for (int i = threadIdx.x; i < 3 * blocks; i += blockDim.x) pp[i] = B.red[2 * kBwMaxBlocks + i];
+  __syncthreads();
   if (threadIdx.x < 3) {
     float acc = 0.f;
-    for (int b = 0; b < blocks; ++b) acc += B.red[2 * kBwMaxBlocks + 3 * b + threadIdx.x];
+    for (int b = 0; b < blocks; ++b) acc += pp[3 * b + threadIdx.x];
     B.grads[threadIdx.x] += acc;
   }
 }
@@ -519,7 +527,7 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
   e = launch_bw(k_bw_tilt_a, blocks, kBwThreads, st, P, B);
   if (e == cudaSuccess) e = launch_bw(k_bw_tilt_b, blocks, kBwThreads, st, P, B, blocks);
-  if (e == cudaSuccess) e = launch_bw(k_bw_grads, 1, 32, st, B, blocks);
+  if (e == cudaSuccess) e = launch_bw(k_bw_grads, 1, 128, st, B, blocks);
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
   e = cudaGetLastError();
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);

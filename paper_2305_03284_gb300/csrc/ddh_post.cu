@@ -151,15 +151,21 @@ __global__ void __cluster_dims__(kPostCluster, 1, 1) __launch_bounds__(kPostThre
       cluster.sync();
     }
   }
-  if (a.noise_update && q == 0 && tid == 0) {
-    float sr = 0.f, sc = 0.f;
-    if (a.prior)
-      for (int k = 0; k < kPostCluster; ++k) sr += part[k];
-    for (int k = 0; k < a.ctas; ++k) {
-      if (!a.prior) sr += aux[kAuxPart + 2 * k];
-      sc += aux[kAuxPart + 2 * k + 1];
+  if (a.noise_update && q == 0) {
+    // the step kernel's partial sums are fetched in parallel, then added in CTA order
+    __shared__ float pa[2 * 16];
+    if (tid < 2 * a.ctas) pa[tid] = aux[kAuxPart + tid];
+    __syncthreads();
+    if (tid == 0) {
+      float sr = 0.f, sc = 0.f;
+      if (a.prior)
+        for (int k = 0; k < kPostCluster; ++k) sr += part[k];
+      for (int k = 0; k < a.ctas; ++k) {
+        if (!a.prior) sr += pa[2 * k];
+        sc += pa[2 * k + 1];
+      }
+      aux[0] = fmaxf(fmaf(sr, a.inv_ap_count, sc * a.inv_m), a.nv_floor);
     }
-    aux[0] = fmaxf(fmaf(sr, a.inv_ap_count, sc * a.inv_m), a.nv_floor);
   }
 }
 
