@@ -743,10 +743,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_fft2(const __grid_constant__ Ff
   float2* tw = reinterpret_cast<float2*>(smem + L::tw);
   float2* rowbuf = reinterpret_cast<float2*>(smem + L::rowbuf);
   float2* colbuf = reinterpret_cast<float2*>(smem + L::colbuf);
+  grid_dep_launch();
   for (int i = tid; i < N; i += kThreads) tw[i] = a.tw[i];
-  for (int i = tid; i < R * N; i += kThreads) {
-    const int l = i / N, x = i - l * N;
-    rowbuf[l * N + swz(x)] = a.in[static_cast<size_t>(k + C * l) * N + x];
+  grid_dep_wait();  // `in` may be the previous kernel's output
+  {
+    // every load of a thread before its first store into the row buffer
+    constexpr int PER = R * N / kThreads;
+    float2 v[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = tid + kThreads * j, l = i / N, x = i - l * N;
+      v[j] = a.in[static_cast<size_t>(k + C * l) * N + x];
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = tid + kThreads * j, l = i / N, x = i - l * N;
+      rowbuf[l * N + swz(x)] = v[j];
+    }
   }
   __syncthreads();
   cluster.sync();  // every read of `in` precedes every write of `out`
@@ -899,10 +912,10 @@ cudaError_t launch_strehl(int n, const StrehlArgs& a, cudaStream_t st) {
 
 cudaError_t launch_fft2(int n, const Fft2Args& a, cudaStream_t st) {
   switch (n) {
-    case 32: return launch_cluster(k_fft2<32>, StepLayout<32>::C, 1, StepLayout<32>::total, st, a);
-    case 64: return launch_cluster(k_fft2<64>, StepLayout<64>::C, 1, StepLayout<64>::total, st, a);
-    case 128: return launch_cluster(k_fft2<128>, StepLayout<128>::C, 1, StepLayout<128>::total, st, a);
-    case 256: return launch_cluster(k_fft2<256>, StepLayout<256>::C, 1, StepLayout<256>::total, st, a);
+    case 32: return launch_cluster(k_fft2<32>, StepLayout<32>::C, 1, StepLayout<32>::total, st, a, true);
+    case 64: return launch_cluster(k_fft2<64>, StepLayout<64>::C, 1, StepLayout<64>::total, st, a, true);
+    case 128: return launch_cluster(k_fft2<128>, StepLayout<128>::C, 1, StepLayout<128>::total, st, a, true);
+    case 256: return launch_cluster(k_fft2<256>, StepLayout<256>::C, 1, StepLayout<256>::total, st, a, true);
     default: return cudaErrorInvalidValue;
   }
 }
