@@ -29,6 +29,13 @@ _states: dict = {}
 _lock = threading.Lock()
 
 
+def clear_cache() -> None:
+    """Free the library states kept for reuse (device memory of r, phi and staging buffers per
+    device, stream and grid size); the next call creates them again."""
+    with _lock:
+        _states.clear()
+
+
 def _state(p, stream):
     key = (stream.device.index, stream.cuda_stream, int(p.n))
     s = _states.get(key)
