@@ -290,6 +290,12 @@ int ddh_fft2(const void *in_c64_dev, void *out_c64_dev, int n, int inverse, void
 
 /* Wait for the state's stream; return and clear any latched device error. */
 int ddh_sync(ddh_state *s);
+/* Diagnostic of the device-side failure path, with no fault: a kernel on the state's stream
+ * waits on a device barrier that nothing completes, gives up after `limit_s` seconds of device
+ * time (0 < limit_s <= 1) and latches the same timeout status the step kernel latches when its
+ * frame copy does not arrive in time.  Synchronises; returns DDH_ETIMEOUT (the expected result,
+ * status cleared) and leaves the state usable, or DDH_EINVAL / DDH_ECUDA. */
+int ddh_selftest_wait(ddh_state *s, double limit_s);
 
 /* Checkpoint: `buf` (host) receives ddh_checkpoint_bytes(N) bytes: params, frame index, r,
  * phi.  ddh_load restores a state with the same N. */

@@ -69,6 +69,7 @@ _SIGS = {
     "ddh_frame_index": (c_int64, [c_void_p]),
     "ddh_set_params": (c_int, [c_void_p, POINTER(DdhParams)]),
     "ddh_noise_estimate": (c_int, [c_void_p, POINTER(c_float)]),
+    "ddh_selftest_wait": (c_int, [c_void_p, ctypes.c_double]),
     "ddh_state_stream": (c_void_p, [c_void_p]),
     "ddh_step_host_async": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "ddh_host_wait": (c_int, [c_void_p, c_int64]),

@@ -18,6 +18,10 @@
 #include "ddh_internal.h"
 #include "ddh_kernels.cuh"
 
+namespace ddh {
+cudaError_t launch_wait_selftest(unsigned* status, uint64_t limit_ns, cudaStream_t st);  // ddh_selftest.cu
+}  // namespace ddh
+
 struct ddh_state {
   ddh_params prm;
   ddh::KParams kp;
@@ -649,6 +653,13 @@ int ddh_set_params(ddh_state* s, const ddh_params* p) {
   s->kp = derive(*p);
   s->ap_count = aperture_count(p->n, aperture_limit(p->aperture_diam));
   return aux_reset(s, p->noise_var);
+}
+
+int ddh_selftest_wait(ddh_state* s, double limit_s) {
+  if (s == nullptr || !(limit_s > 0.0) || limit_s > 1.0) return DDH_EINVAL;
+  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_CUDA(ddh::launch_wait_selftest(s->status, static_cast<uint64_t>(limit_s * 1e9), s->stream));
+  return check_status(s);
 }
 
 int ddh_noise_estimate(ddh_state* s, float* out) {

@@ -91,5 +91,6 @@ def test_host_helpers(lib):
     assert lib.ddh_step_batch(None, None, 0) == -1
     assert lib.ddh_set_params(None, None) == -1
     assert lib.ddh_noise_estimate(None, None) == -1
+    assert lib.ddh_selftest_wait(None, 0.001) == -1
     assert lib.ddh_unrolled_forward(None, 1, None, None, None, None) == -1
     assert lib.ddh_unrolled_backward(None, 1, None, None, None, None, None, None, None, None, None, None, 0) == -1

@@ -409,6 +409,27 @@ def test_nonfinite_frame_is_rejected_and_state_kept(ddh):
     assert not torch.equal(s.phase(), phi0)
 
 
+def test_bounded_device_wait_expires_and_state_stays_usable(ddh):
+    """Failure detection without a fault: a device wait that nothing completes gives up after
+    its time limit and latches the timeout status, the host reads DDH_ETIMEOUT, and the same
+    state then steps exactly like a fresh one."""
+    import ctypes
+    import time
+    from paper_2305_03284_gb300._lib import DDH_EINVAL, DDH_ETIMEOUT
+    cfg = sy.config_single_64()
+    st, ys, ph, p = make(ddh, cfg, 2)
+    s, ref = ddh.Stream(p), ddh.Stream(p)
+    t0 = time.perf_counter()
+    assert ddh.lib().ddh_selftest_wait(s._h, ctypes.c_double(0.002)) == DDH_ETIMEOUT
+    assert time.perf_counter() - t0 >= 0.002
+    assert ddh.lib().ddh_selftest_wait(s._h, ctypes.c_double(5.0)) == DDH_EINVAL  # limit above 1 s
+    s.sync()  # the latched status was cleared by the self-test call
+    for i in range(2):
+        s.step(cu(ys[i]))
+        ref.step(cu(ys[i]))
+    assert torch.equal(s.phase(), ref.phase()) and torch.equal(s.reflectance(), ref.reflectance())
+
+
 def test_argument_errors(ddh):
     p = ddh.default_params(64, 32.0, 10.0)
     s = ddh.Stream(p)
