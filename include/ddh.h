@@ -101,9 +101,10 @@ int ddh_step(ddh_state *s, const void *y_c64_dev);
 int ddh_step_trace(ddh_state *s, const void *y_c64_dev, float *trace_dev);
 size_t ddh_trace_floats(int n);
 
-/* One step from HOST memory: copies the frame in from `y_c64_host` (pinned for overlap),
- * runs ddh_step, copies phi out to `phi_host_out` (N*N float32), and waits for completion.
- * The device staging buffer is owned by the state. */
+/* One step from HOST memory: the frame from `y_c64_host`, phi (N*N float32) to `phi_host_out`,
+ * and waits for completion.  Pinned, mapped buffers are read and written in place by the step
+ * kernel (the conditions of ddh_step_host_async); otherwise the frame is copied into a device
+ * staging buffer owned by the state and phi copied out after the step. */
 int ddh_step_host(ddh_state *s, const void *y_c64_host, float *phi_host_out);
 
 /* Pipelined form of ddh_step_host: enqueues the frame's step and returns at once with
@@ -114,10 +115,10 @@ int ddh_step_host(ddh_state *s, const void *y_c64_host, float *phi_host_out);
  * same results bit for bit).  Otherwise the frame is copied in on a library copy stream into
  * one of two device staging slots, so that frame n+1's copy overlaps frame n's step, and phi is
  * copied out after the step.  Both buffers stay untouched until ddh_host_wait(s, ticket) or
- * ddh_sync(s) returns (pageable memory makes the staged copies synchronous).  ddh_step_host
- * takes the in-place route under the same conditions.  Errors latched by the step (non-finite frame, timeout) surface at ddh_sync.
- * Steps of one state must not be enqueued from several threads at once.  The paper has no
- * counterpart (it describes a frame loop, not its host interface). */
+ * ddh_sync(s) returns (pageable memory makes the staged copies synchronous).  Errors latched
+ * by the step (non-finite frame, timeout) surface at ddh_sync.  Steps of one state must not be
+ * enqueued from several threads at once.  The paper has no counterpart (it describes a frame
+ * loop, not its host interface). */
 int ddh_step_host_async(ddh_state *s, const void *y_c64_host, float *phi_host_out, int64_t *ticket);
 /* Block until frame `ticket` of ddh_step_host_async has its phi in host memory (DDH_EINVAL
  * for a ticket not issued on s). */
