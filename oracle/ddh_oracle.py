@@ -32,8 +32,12 @@ phase M-step and Strehl functions are each pinned by tests against closed forms,
 the exact posterior (see the oracle tests).  The prior-weighted tile-phase M-step is pinned by
 monotone descent of its per-pixel cost, stationarity at its fixed point (finite differences)
 and a two-tile closed form; the sigma^2 M-step by the exact-fit case, the sample noise power
-over the pupil, and convergence of EM to the maximum-likelihood variance.  The multi-frame trajectory as a whole has no
-printed values in the paper: beyond those pins it is *parity unpinned*.
+over the pupil, and convergence of EM to the maximum-likelihood variance.  The r-init blend is
+pinned by hand-computed values with a non-zero previous state; one whole frame (Normalize,
+tip/tilt, back-projection, Eq. 3, N_k = 1 and 2 EM iterations, the sigma^2 M-step and its use
+in the next frame) by a hand-unrolled dense-matrix frame on an 8 x 8 grid.  The multi-frame
+trajectory as a whole has no printed values in the paper: beyond those pins it is *parity
+unpinned*.
 """
 from __future__ import annotations
 

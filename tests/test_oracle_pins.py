@@ -648,3 +648,175 @@ def test_noise_mstep_residual_is_the_pupil_noise_power():
     y = np.where(a, np.exp(1j * phi) * z + math.sqrt(v0) * _crandn(rng, n, n), 5.0 * _crandn(rng, n, n))
     est = o.noise_mstep(y, z, phi, a, np.zeros((n, n)))
     assert abs(est - v0) < 4 * v0 / math.sqrt(a.sum()), (est, v0)
+
+
+# ---------------------------------------------------------------------------- Eq. 3 blend
+def test_r_init_blend_with_previous_state_hand_values():
+    """Eq. 3 with r_{n-1} != 0: (1 - lambda) r_{n-1} + lambda alpha |b|^2, floored.  Expected
+    values computed by hand for lambda 0.45 / alpha 0.025 (the paper's, Sec. 5.B) and for
+    lambda 0.3 / alpha 0.5."""
+    r_prev = np.array([[0.2, 1.0], [0.0, 3.0]])
+    b = np.array([[1 + 1j, 0.5], [2j, 0.0]])  # |b|^2 = 2, 0.25, 4, 0
+    got = o.r_init(r_prev, b, o.Params(n=2, aperture_diam=2, lam=0.45, alpha=0.025, r_floor=1e-10))
+    # 0.55*0.2 + 0.01125*2 = 0.1325; 0.55*1 + 0.01125*0.25 = 0.5528125; 0.01125*4 = 0.045; 0.55*3 = 1.65
+    assert np.allclose(got, [[0.1325, 0.5528125], [0.045, 1.65]], rtol=0, atol=1e-15)
+    got = o.r_init(r_prev, b, o.Params(n=2, aperture_diam=2, lam=0.3, alpha=0.5, r_floor=1e-10))
+    # 0.7*0.2 + 0.15*2 = 0.44; 0.7 + 0.15*0.25 = 0.7375; 0.15*4 = 0.6; 0.7*3 = 2.1
+    assert np.allclose(got, [[0.44, 0.7375], [0.6, 2.1]], rtol=0, atol=1e-15)
+    # the floor applies where both terms vanish
+    got = o.r_init(np.zeros((1, 2)), np.array([[0.0, 1.0]]), o.Params(n=2, aperture_diam=2, r_floor=1e-6))
+    assert got[0, 0] == 1e-6 and got[0, 1] == pytest.approx(0.45 * 0.025)
+
+
+# ---------------------------------------------------------------------------- phase M-step branch
+def test_phase_mstep_keeps_old_phase_where_the_product_is_zero():
+    """Where y~_i conj(z_i) = 0 the angle is undefined and the old phase stays (per pixel), and
+    a tile whose summed product is 0 keeps its pixels' old phases (tiled)."""
+    rng = _rng(31)
+    n = 8
+    a = o.aperture(n, 8.0)
+    y = _crandn(rng, n, n)
+    mu = _crandn(rng, n, n)
+    old = np.where(a, rng.uniform(-3, 3, (n, n)), 0.0)
+    zero = np.zeros((n, n), bool)
+    zero[2, 3] = zero[4, 4] = zero[5, 1] = True
+    assert np.all(a[zero])
+    y0 = np.where(zero, 0.0, y)
+    phi, z = o.phase_mstep(y0, mu, old, a)
+    assert np.array_equal(phi[zero], old[zero])
+    expect = np.angle(y0 * np.conj(np.fft.fft2(mu, norm="ortho")))
+    on = a & ~zero
+    assert np.allclose(phi[on], expect[on], atol=1e-12)
+    # tiled: zero the whole 2x2 tile (rows 2-3, cols 2-3) of y
+    y1 = y.copy()
+    y1[2:4, 2:4] = 0.0
+    phi_t, _ = o.phase_mstep(y1, mu, old, a, block=2)
+    assert np.array_equal(phi_t[2:4, 2:4], old[2:4, 2:4])
+    assert not np.array_equal(phi_t[0:2, 2:4][a[0:2, 2:4]], old[0:2, 2:4][a[0:2, 2:4]])
+
+
+# ---------------------------------------------------------------------------- frame orchestration
+def _icd_bruteforce(r0, s, prm):
+    """One 4-colour ICD sweep by dense scan plus golden-section refinement of every pixel's
+    surrogate, neighbours and weights enumerated explicitly (weights at the sweep's entry
+    values, neighbour values as updated so far)."""
+    n = r0.shape[0]
+    r = r0.copy()
+    grid = np.logspace(-8, 2, 100_001)
+    for cx, cy in [(0, 0), (1, 0), (0, 1), (1, 1)]:
+        for yy in range(n):
+            for xx in range(n):
+                if xx % 2 != cx or yy % 2 != cy:
+                    continue
+                terms = []
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        y1, x1 = yy + dy, xx + dx
+                        if (dy, dx) == (0, 0) or not (0 <= y1 < n and 0 <= x1 < n):
+                            continue
+                        bij = 1 / (4 + 2 * math.sqrt(2)) / (math.sqrt(2) if dy and dx else 1.0)
+                        beta = bij * float(o.qggmrf_weight(np.array([r0[yy, xx] - r0[y1, x1]]), prm)[0])
+                        terms.append((beta, r[y1, x1]))
+
+                def h(v):
+                    return np.log(v) + s[yy, xx] / v + sum(0.5 * b_ * (v - rj) ** 2 for b_, rj in terms)
+                k = int(np.argmin(h(grid)))
+                lo, hi = grid[max(k - 1, 0)], grid[min(k + 1, grid.size - 1)]
+                for _ in range(200):
+                    m1, m2 = lo + 0.382 * (hi - lo), hi - 0.382 * (hi - lo)
+                    lo, hi = (lo, m2) if h(m1) < h(m2) else (m1, hi)
+                r[yy, xx] = max(0.5 * (lo + hi), prm.r_floor)
+    return r
+
+
+def _hand_frame(r_prev, phi_prev, y, prm, s2):
+    """One frame of Fig. 1 unrolled by hand on a tiny grid with dense matrices: Normalize
+    (Eq. 4), the tip/tilt fit over explicitly enumerated aperture pairs, the back-projection
+    through the dense operator, Eq. 3, then N_k EM iterations in which the first E-step uses
+    the r-init back-projection and later ones recompute it with the current phase, the phase
+    M-step uses that iteration's E-step mean (not the updated r), and the r M-step is the ICD
+    sweep from the iteration's entry r.  Returns (r, phi, z and C of the last iteration)."""
+    n = prm.n
+    M = n * n
+    Fm = _dft_matrix_2d(n)
+    c = (n - 1) / 2.0
+    a = np.array([[(x - c) ** 2 + (yy - c) ** 2 <= (prm.aperture_diam / 2) ** 2 for x in range(n)]
+                  for yy in range(n)])
+    d = y - y.sum() / M
+    yt = math.sqrt(M) * d / math.sqrt(float(np.sum(np.abs(d) ** 2)))
+    dxs, dys = [], []
+    for yy in range(n):
+        for x in range(n):
+            if x + 1 < n and a[yy, x] and a[yy, x + 1]:
+                dxs.append(math.remainder(phi_prev[yy, x + 1] - phi_prev[yy, x], 2 * math.pi))
+            if yy + 1 < n and a[yy, x] and a[yy + 1, x]:
+                dys.append(math.remainder(phi_prev[yy + 1, x] - phi_prev[yy, x], 2 * math.pi))
+    tx, ty = float(np.mean(dxs)), float(np.mean(dys))
+    phi = np.zeros((n, n))
+    for yy in range(n):
+        for x in range(n):
+            if a[yy, x]:
+                phi[yy, x] = math.remainder(phi_prev[yy, x] - tx * (x - c) - ty * (yy - c), 2 * math.pi)
+
+    def backproject(ph):
+        A = np.diag((a * np.exp(1j * ph)).ravel()) @ Fm
+        return (A.conj().T @ yt.ravel()).reshape(n, n)
+    b = backproject(phi)
+    r = np.maximum((1 - prm.lam) * r_prev + prm.lam * prm.alpha * np.abs(b) ** 2, prm.r_floor)
+    for it in range(prm.n_k):
+        if it > 0:
+            b = backproject(phi)
+        w = r / (r + s2)
+        mu = w * b
+        cvar = s2 * w
+        s = np.abs(mu) ** 2 + cvar
+        z = (Fm @ mu.ravel()).reshape(n, n)
+        v = yt * np.conj(z)
+        phi = np.where(a & (v != 0), np.angle(v), phi)
+        r = _icd_bruteforce(r, s, prm)
+    return r, phi, z, cvar, yt, a
+
+
+@pytest.mark.parametrize("n_k", [1, 2])
+def test_frame_step_matches_a_hand_unrolled_dense_frame(n_k):
+    rng = _rng(40 + n_k)
+    n = 8
+    prm = o.Params(n=n, aperture_diam=6.0, n_k=n_k, noise_var=0.4, prior_sigma=0.3)
+    a = o.aperture(n, 6.0)
+    y = (3.0 * _crandn(rng, n, n) + 0.5).astype(np.complex64).astype(np.complex128)
+    r_prev = rng.uniform(0.05, 1.5, (n, n))
+    phi_prev = np.where(a, rng.uniform(-math.pi, math.pi, (n, n)), 0.0)
+    st, _ = o.step(o.State(r=r_prev.copy(), phi=phi_prev.copy(), n=3), y, prm)
+    r_h, phi_h, _, _, _, _ = _hand_frame(r_prev, phi_prev, y, prm, prm.noise_var)
+    assert st.n == 4
+    assert np.allclose(st.r, r_h, rtol=2e-7)
+    assert np.allclose(o.wrap(st.phi - phi_h)[a], 0.0, atol=1e-7)  # r by golden section: ~1e-8
+    assert np.all(st.phi[~a] == 0.0)
+    if n_k == 1:
+        # the discriminating power of this pin: phi from the updated r's posterior mean differs
+        yt, _ = o.normalize(y)
+        phi_t, _ = o.remove_tip_tilt(phi_prev, a)
+        b = o.adjoint_op(yt, phi_t, a)
+        alt, _ = o.phase_mstep(yt, st.r / (st.r + prm.noise_var) * b, phi_t, a)
+        assert np.max(np.abs(o.wrap(alt - phi_h)[a])) > 1e-3
+
+
+def test_noise_mstep_runs_after_the_last_em_iteration_and_feeds_the_next_frame():
+    """With the sigma^2 M-step on: after frame 1's last EM iteration sigma^2 becomes
+    mean_P |y~ - e^{j phi} z|^2 + mean(C) at the new phase (z, C of that iteration), and
+    frame 2's E-steps use it."""
+    rng = _rng(50)
+    n = 8
+    prm = o.Params(n=n, aperture_diam=6.0, n_k=2, noise_var=0.4, prior_sigma=0.3, noise_update=1)
+    a = o.aperture(n, 6.0)
+    ys = [(3.0 * _crandn(rng, n, n) + 0.5) for _ in range(2)]
+    r_prev = rng.uniform(0.05, 1.5, (n, n))
+    phi_prev = np.where(a, rng.uniform(-math.pi, math.pi, (n, n)), 0.0)
+    st1, _ = o.step(o.State(r=r_prev.copy(), phi=phi_prev.copy(), n=0), ys[0], prm)
+    r1, phi1, z1, c1, yt1, a1 = _hand_frame(r_prev, phi_prev, ys[0], prm, prm.noise_var)
+    s2 = float(np.sum(np.abs(yt1 - np.exp(1j * phi1) * z1)[a1] ** 2)) / float(a1.sum()) + float(c1.mean())
+    assert st1.noise_var == pytest.approx(s2, rel=1e-7)  # r by golden section: ~1e-8
+    st2, _ = o.step(st1, ys[1], prm)
+    r2, phi2, _, _, _, _ = _hand_frame(st1.r, st1.phi, ys[1], prm, s2)
+    assert np.allclose(st2.r, r2, rtol=2e-7)
+    assert np.allclose(o.wrap(st2.phi - phi2)[a], 0.0, atol=1e-7)
