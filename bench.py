@@ -129,6 +129,33 @@ def profiled_traffic():
 
 # Nominal FP32 rate of the part: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Nominal warp-instruction issue rate: 152 SMs x 4 schedulers x 1 instruction per cycle x 2.07 GHz.
+ISSUE_PEAK_WIPS = 152 * 4 * 2.07e9
+
+
+def issue_bound(frames_per_s, inst_per_frame=None):
+    """The instruction-issue ceiling of the step kernel: warp instructions per frame (ncu, from
+    the committed summary when it was taken on this kernel source) times frames/s, against the
+    whole GPU's nominal issue rate; `max_frames_per_s` is the rate at which every scheduler of
+    every SM would issue one of these instructions each cycle."""
+    if inst_per_frame is None:
+        inst_per_frame = profiled_value("warp_inst_per_launch")
+    if inst_per_frame is None:
+        return None
+    achieved = inst_per_frame * frames_per_s
+    return {"bound": "issue", "achieved": achieved / 1e12, "peak": ISSUE_PEAK_WIPS / 1e12,
+            "unit": "T warp instructions/s", "frac": achieved / ISSUE_PEAK_WIPS,
+            "warp_inst_per_frame": inst_per_frame, "max_frames_per_s": ISSUE_PEAK_WIPS / inst_per_frame,
+            "peak_source": "nominal: 152 SMs x 4 schedulers x 2.07 GHz"}
+
+
+def queue_ahead(stream, us=150.0):
+    """Hold `stream` busy for about `us` microseconds (torch's spin kernel, outside the timed
+    region) so that the timed launches are all queued before the first of them can start: the
+    events then bracket device work only, not the host's first-launch latency."""
+    import torch
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(int(us * 1e-6 * 2.07e9))
 
 
 class ClockSampler:
@@ -349,14 +376,123 @@ def batched_measure(ddh, peak_gbs, timesteps=200, ring=10, warm=5):
     return out
 
 
-def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
+def batched_256_measure(ddh, peak_gbs, streams, timesteps=200, ring=8, warm=5):
+    """The plain one-frame-per-launch path against the batched form on `streams` independent
+    256^2 streams (the single-stream workload, one seeded stream each): per time step every
+    stream advances one frame.  "plain": one ddh_step launch per stream, all on one CUDA stream;
+    "plain_streams": the same launches spread over one CUDA stream per sensor stream (the GPU
+    may overlap them); "graph_cluster" / "graph_staged": one captured graph per time step with
+    the streams on the cluster kernel / the L2-staged kernels; "graph": the one of the two the
+    committed tuning table recommends for this many 256^2 streams.  Per-frame latency counts
+    from the start of the time step on the device to that frame's completion event."""
+    from paper_2305_03284_gb300 import autotune
+    import torch
+    from synth import ddh_synth as sy
+    cfgs = [sy.replace(sy.config_single_256(frames=ring), stream_id=i) for i in range(streams)]
+    frames = torch.empty((ring, streams, 256, 256), dtype=torch.complex64)
+    for i, c in enumerate(cfgs):
+        frames[:, i] = torch.from_numpy(sy.Stream(c).frames(ring)[0])
+    frames = frames.cuda()
+    lib = ddh.lib()
+    main = torch.cuda.Stream()
+    side = [torch.cuda.Stream() for _ in range(streams)]
+    ptrs = [[ddh.c_void_p(frames[t, i].data_ptr()) for i in range(streams)] for t in range(ring)]
+    arrs = [(ddh.c_void_p * streams)(*row) for row in ptrs]
+    px = streams * 256 * 256
+    out = {"workload": f"{streams} independent 256^2 streams (128 px pupil, D/r0 15, 1 px/frame, SNR 5, "
+                       "seeded per stream), 1 EM iteration per frame",
+           "streams": streams, "timesteps": timesteps, "frames_ring_per_stream": ring}
+
+    def measure(kind, path=1):
+        with torch.cuda.stream(main):
+            prm = ddh.default_params(256, 128.0, 5.0, exec_path=path)
+            if kind == "plain_streams":
+                sts = [ddh.Stream(prm, stream=side[i]) for i in range(streams)]
+            else:
+                sts = [ddh.Stream(prm, stream=main) for _ in range(streams)]
+            hs = [s._h for s in sts]
+            g = ddh.BatchGraph(sts) if kind == "graph" else None
+            ev_start = torch.cuda.Event(enable_timing=True)
+            fork = torch.cuda.Event()
+
+            def one(t, per_frame_events=None):
+                if g is not None:
+                    g.run_ptrs(arrs[t % ring])
+                    if per_frame_events is not None:
+                        per_frame_events[0].record(main)
+                    return
+                if kind == "plain_streams":
+                    fork.record(main)
+                    for i, (h, ptr) in enumerate(zip(hs, ptrs[t % ring])):
+                        side[i].wait_event(fork)
+                        lib.ddh_step(h, ptr)
+                        if per_frame_events is not None:
+                            per_frame_events[i].record(side[i])
+                    for i in range(streams):
+                        main.wait_stream(side[i])
+                    return
+                for i, (h, ptr) in enumerate(zip(hs, ptrs[t % ring])):
+                    lib.ddh_step(h, ptr)
+                    if per_frame_events is not None:
+                        per_frame_events[i].record(main)
+            for t in range(warm):
+                one(t)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            queue_ahead(main)
+            e0.record(main)
+            for t in range(timesteps):
+                one(warm + t)
+            e1.record(main)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            lat = []
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(streams)]
+            for t in range(min(timesteps, 100)):
+                torch.cuda.synchronize()
+                queue_ahead(main, 100.0)
+                ev_start.record(main)
+                one(t, evs)
+                torch.cuda.synchronize()
+                lat.extend(ev_start.elapsed_time(evs[i if g is None else 0]) * 1e3 for i in range(streams))
+            for s in sts:
+                s.sync()
+            if g is not None:
+                g.close()
+            for s in sts:
+                s.close()
+        lat.sort()
+        per_step_s = ms * 1e-3 / timesteps
+        return {"frames_per_s": streams / per_step_s, "us_per_timestep": per_step_s * 1e6,
+                "frame_latency_us_p50": lat[len(lat) // 2],
+                "frame_latency_us_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "hbm_gbs_algorithmic": BYTES_PER_PX * px / per_step_s / 1e9,
+                "hbm_frac": BYTES_PER_PX * px / per_step_s / 1e9 / peak_gbs,
+                "launches_per_timestep": streams if g is None else "1 graph",
+                "exec_path": {1: "cluster", 2: "staged"}[path]}
+    out["plain"] = measure("plain")
+    out["plain_streams"] = measure("plain_streams")
+    out["graph_cluster"] = measure("graph", 1)
+    out["graph_staged"] = measure("graph", 2)
+    out["graph"] = dict(out["graph_staged" if autotune.recommend_path(256, streams) == 2 else "graph_cluster"])
+    out["graph_over_plain_frames_per_s"] = out["graph"]["frames_per_s"] / out["plain"]["frames_per_s"]
+    out["graph_over_plain_streams_frames_per_s"] = (out["graph"]["frames_per_s"]
+                                                    / out["plain_streams"]["frames_per_s"])
+    out["latency"] = ("per frame, from the time step's start on the device to the frame's completion "
+                      "(all frames of a time step arrive together), frames resident in HBM")
+    return out
+
+
+def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=None):
     """Streaming service (continuous batching) against the same scheduler launching every
-    frame on its own, replaying one seeded Poisson arrival trace of the sensor mix."""
+    frame on its own, replaying one seeded Poisson arrival trace of the sensor mix (the
+    32-sensor mix of 128^2, 256^2 and 512^2 grids, or `cfgs`)."""
     import numpy as np
     import torch
     from paper_2305_03284_gb300 import serve
     from synth import ddh_synth as sy
-    cfgs = sy.config_service(frames_total=total_frames)
+    if cfgs is None:
+        cfgs = sy.config_service(frames_total=total_frames)
     rates = np.array([c.rate_khz * 1e3 for c in cfgs])
     horizon = total_frames / rates.sum()
     rng = np.random.default_rng(seed)
@@ -374,7 +510,7 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
     out = {"workload": f"{len(cfgs)} sensors ({sum(c.n == 128 for c in cfgs)} x 128^2, "
                        f"{sum(c.n == 256 for c in cfgs)} x 256^2, {sum(c.n == 512 for c in cfgs)} x 512^2), "
                        "Poisson arrivals at 0.5-5 kHz per sensor, "
-                       f"{len(arrivals)} frames over {horizon * 1e3:.1f} ms",
+                       f"{len(arrivals)} frames over {horizon * 1e3:.1f} ms" + (f" ({label})" if label else ""),
            "offered_frames_per_s": len(arrivals) / horizon}
 
     def one(per_frame, trace):
@@ -401,6 +537,13 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5):
     out["scheduler"] = "libddh native scheduler thread (ddh_service_*), batches via ddh_step_batch"
     out["latency"] = "scheduled arrival to completion event observed by the scheduler"
     return out
+
+
+def service_256_configs(sensors=32, frames_total=10_000):
+    """The service workload with every sensor at 256^2 (the headline grid): the 32 sensors'
+    seeded rates (0.5-5 kHz), turbulence and wind, grids all 256 x 256 with a 128 px pupil."""
+    from synth import ddh_synth as sy
+    return [sy.replace(c, n=256, aperture_diam=128.0) for c in sy.config_service(sensors, frames_total)]
 
 
 def adjoint_measure(ddh, streams=16, frames=8, reps=3, store_traces=True):
@@ -502,6 +645,7 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         with ClockSampler(local_rank) as clk:
+            queue_ahead(stream)
             e0.record(stream)
             for i in range(args.steps):
                 lib.ddh_step(h, ptrs[(args.warmup + i) % args.ring])
@@ -594,11 +738,13 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_PX * n * n
     avg_launch_s = ms * 1e-3 / args.steps
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    batched = None
+    batched = b256 = service_256 = None
     if not args.no_batched and world == 1:
         # the service trace runs first: it is a latency measurement near the fastest sensors'
         # capacity, and it should not inherit the state the 64-stream throughput run leaves
         service = service_measure(ddh)
+        service_256 = service_measure(ddh, cfgs=service_256_configs(), label="all sensors at 256^2")
+        b256 = {str(k): batched_256_measure(ddh, peak, k) for k in (7, 32)}
         batched = batched_measure(ddh, peak)
         batched["service"] = service
         batched["adjoint"] = adjoint_measure(ddh)
@@ -618,6 +764,7 @@ def run_ours(args):
                      "traffic": profiled_traffic(), "kernel": "k_ddh_step<256>",
                      "bytes_per_launch": bytes_per_launch, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
         "roofline_fp32": fp32_cobound(avg_launch_s),
+        "roofline_issue": issue_bound(value),
         "e2e": {"value": ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 4,
                 "steps": ke},
         "static_mode": static,
@@ -627,6 +774,8 @@ def run_ours(args):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "batched": batched,
+        "batched_256": b256,
+        "service_256": service_256,
     }
     print(json.dumps(line))
 

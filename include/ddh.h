@@ -5,7 +5,9 @@
  * kernels; there is no CPU path.  All calls are asynchronous on the CUDA stream given to
  * ddh_init() unless stated otherwise; errors found by the device (non-finite frame, a bounded
  * wait that expired) are latched in a device status word and returned by the next call that
- * synchronises (ddh_sync, ddh_phase/ddh_reflectance to host memory, ddh_strehl).
+ * synchronises (ddh_sync, ddh_phase/ddh_reflectance to host memory, ddh_strehl).  A call
+ * that works on a state makes the state's device current for its duration and restores the
+ * calling thread's current device before it returns.
  *
  * Method: Sheikh, Pellizzari, Kisner, Buzzard, Bouman, "Dynamic DH-MBIR for Phase-Error
  * Estimation from Streaming Digital-Holography Data" (arXiv:2305.03284).  Per frame (Fig. 1):
@@ -65,14 +67,29 @@ typedef struct ddh_params {
                            its EM M-step (1/|P|) sum_pupil |y~ - e^{j phi} F mu|^2 + mean(C);
                            floored at 1e-6.  N <= 256, outside batches and the service, no
                            adjoint.  0 (default): sigma^2 fixed */
+  int exec_path;        /* which kernels run this stream's steps (same method, same readings;
+                           results agree within FP32 rounding, not bit for bit):
+                           DDH_PATH_DEFAULT (0): the cluster kernel for N <= 256, the L2-staged
+                           kernels for N = 512; DDH_PATH_CLUSTER (1): one thread-block cluster
+                           per stream holds the whole frame in shared memory (N <= 256; lowest
+                           latency for one stream); DDH_PATH_STAGED (2): a sequence of batched
+                           kernels over per-stream global scratch that stays in L2 (N = 128,
+                           256 or 512; uses every SM when many streams step together, so the
+                           higher throughput for large batches).  Fixed for the state's
+                           lifetime: a stream steps the same way alone and in any batch.  The
+                           staged path has no trace output, host-buffer in-place steps,
+                           tile-phase prior, sigma^2 M-step or adjoint (DDH_EINVAL) */
 } ddh_params;
+#define DDH_PATH_DEFAULT 0
+#define DDH_PATH_CLUSTER 1
+#define DDH_PATH_STAGED 2
 
 typedef struct ddh_state ddh_state; /* opaque; owned by the library */
 
 /* Fill `p` with the defaults for grid `n`, pupil `aperture_diam` and a linear SNR over the
  * pupil: lambda 0.45, alpha 0.025 (Sec. 5.B), n_k 1, noise_var 1/(1 + f SNR) with f the
  * pupil fill fraction, prior p 1.1, q 2, T 1, sigma_r 0.1, r_floor 1e-10, tilt_mode 1,
- * phase_block 1, phase_prior 0, phase_sweeps 2, noise_update 0. */
+ * phase_block 1, phase_prior 0, phase_sweeps 2, noise_update 0, exec_path DDH_PATH_DEFAULT. */
 int ddh_default_params(ddh_params *p, int n, float aperture_diam, float snr);
 
 /* Static DH-MBIR (Sec. 3: EM iterated on one frame, the reflectance reset to a back-projected
@@ -226,9 +243,11 @@ int ddh_unrolled_backward(ddh_state *s, int k_frames, const void *const *ys, con
  * unbounded latency and possible device-wide synchronisation would break the frame deadline,
  * or a host whose device memory is fully budgeted up front.  The call itself never calls
  * cudaMalloc or cudaFree.  The first call on a device looks up the array's device address
- * (with that device current) and caches it; make that first call before any stream capture.
- * Every call shares the one array, and each call initialises what it reads; calls whose work
- * overlaps on the GPU (other streams, other threads) race on it, so serialise them. */
+ * (with that device current) and caches it per device and CUDA context (a call after a device
+ * reset, in the new context, looks it up again); make that first call before any stream
+ * capture.  Every call shares the one array, and each call initialises what it reads; calls
+ * whose work overlaps on the GPU (other streams, other threads) race on it, so serialise them.
+ * Argument checks are those of ddh_step_backward; each DDH_EINVAL sets a message. */
 int ddh_step_backward_noalloc(ddh_state *s, const void *y_c64_dev, const float *r_prev, const float *phi_prev,
                               const float *trace, const float *r_new, const float *r_bar, const float *phi_bar,
                               float *r_prev_bar, float *phi_prev_bar, float *grads);
@@ -238,8 +257,7 @@ int ddh_step_backward_noalloc(ddh_state *s, const void *y_c64_dev, const float *
  * are queued per sensor; a scheduler (a library thread after ddh_service_start, or each
  * ddh_service_poll call otherwise) resolves finished batches and launches the next queued
  * frame of every sensor that has one, as one ddh_step_batch, without waiting for batches still
- * running (at most `max_in_flight`; a batch starts behind a running one only if it holds at
- * least half of the admitted sensors).  A batch holds at most one frame per sensor; a sensor's
+ * running (at most `max_in_flight`; when a batch starts is decided by ddh_sched_pick below).  A batch holds at most one frame per sensor; a sensor's
  * next frame may go into a later batch while its previous one still runs, since batches
  * execute in order on the service's stream.  A sensor's results do not depend on which
  * other sensors share its launches.  The paper has a frame loop per sensor
@@ -278,12 +296,42 @@ int ddh_service_start(ddh_service *s);      /* run the scheduler on a library th
 int ddh_service_stop(ddh_service *s);
 int ddh_service_free(ddh_service *s);        /* stops, waits for the stream, frees the states */
 
+/* The service's batch-formation policy as a pure host function (no CUDA; the scheduler calls it
+ * every iteration, and it can be exercised on its own, e.g. in a simulation).  Input: per
+ * admitted sensor the number of queued frames and the arrival time (ddh_service_now clock) of
+ * the oldest one; the number of the service's batches on the device and its limit.  Output:
+ * pick[i] = 1 for the sensors whose next frame goes into a batch launched now; returns their
+ * number (0: launch nothing now) or DDH_EINVAL.  Rule: nothing while `max_in_flight` batches
+ * run; with no batch running, every sensor with a queued frame; behind a running batch only if
+ * at least half of the sensors have a frame queued, or (flag DDH_SCHED_BACKLOG) some sensor has
+ * two or more queued (its frames arrive faster than batches complete, and it advances one
+ * frame per batch), or (flag DDH_SCHED_AGE) some queued frame is at least `age_limit_s` old.
+ * The paper has no counterpart (its loop serves one sensor). */
+#define DDH_SCHED_BACKLOG 1u
+#define DDH_SCHED_AGE 2u
+typedef struct ddh_sched_sensor {
+  int queued;              /* frames waiting in the sensor's queue */
+  double oldest_arrival_s; /* arrival time of the oldest of them (unused when queued == 0) */
+} ddh_sched_sensor;
+int ddh_sched_pick(const ddh_sched_sensor *sensors, int count, int batches_in_flight, int max_in_flight,
+                   double now_s, double age_limit_s, unsigned flags, unsigned char *pick);
+/* Select the policy's optional rules (DDH_SCHED_* flags; default both, age limit 1 ms). */
+int ddh_service_set_policy(ddh_service *s, unsigned flags, double age_limit_s);
+
 /* FFT radix schedule used for grid size n on the current device (the autotuner's choice):
  * count of schedules, select one (affects later launches and later ddh_batch_create), query.
  * Schedules differ only in rounding. */
 int ddh_fft_schedule_count(int n);
 int ddh_set_fft_schedule(int n, int schedule);
 int ddh_get_fft_schedule(int n);
+/* Streams per launch chunk of the L2-staged kernels for grid size n (128, 256, 512) on the
+ * current device, 1..32 (default 16): a batch's staged streams of one size run as consecutive
+ * launch sequences of this many streams, so that one chunk's working images (about 2.6 MB per
+ * 256^2 stream, 10 MB per 512^2 stream) stay in L2 between its stages.  Affects later launches
+ * and later ddh_batch_create; results do not depend on it (every stream's arithmetic is its
+ * own).  The autotuner's knob. */
+int ddh_set_staged_chunk(int n, int chunk);
+int ddh_get_staged_chunk(int n);
 
 /* Unitary 2D DFT (Sec. 2, F) or its inverse (inverse != 0) of one N x N complex64 image,
  * device in/out (may alias), on `cuda_stream`.  N = 32 ... 256. */

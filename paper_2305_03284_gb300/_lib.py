@@ -14,6 +14,9 @@ DDH_ECUDA = -3
 DDH_ETIMEOUT = -4
 DDH_ENONFINITE = -5
 DDH_EBUDGET = -6
+DDH_PATH_DEFAULT = 0
+DDH_PATH_CLUSTER = 1
+DDH_PATH_STAGED = 2
 
 
 class DdhParams(ctypes.Structure):
@@ -35,6 +38,7 @@ class DdhParams(ctypes.Structure):
         ("phase_prior", c_float),
         ("phase_sweeps", c_int),
         ("noise_update", c_int),
+        ("exec_path", c_int),
     ]
 
 
@@ -47,6 +51,15 @@ class DdhCompletion(ctypes.Structure):
         ("arrival_s", ctypes.c_double),
         ("done_s", ctypes.c_double),
     ]
+
+
+class DdhSchedSensor(ctypes.Structure):
+    """Mirror of ``ddh_sched_sensor``."""
+    _fields_ = [("queued", c_int), ("oldest_arrival_s", ctypes.c_double)]
+
+
+DDH_SCHED_BACKLOG = 1
+DDH_SCHED_AGE = 2
 
 
 class DdhError(RuntimeError):
@@ -88,6 +101,9 @@ _SIGS = {
     "ddh_service_pending": (c_int64, [c_void_p]),
     "ddh_service_stats": (c_int, [c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_size_t)]),
     "ddh_service_now": (ctypes.c_double, []),
+    "ddh_sched_pick": (c_int, [POINTER(DdhSchedSensor), c_int, c_int, c_int, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_uint, POINTER(ctypes.c_ubyte)]),
+    "ddh_service_set_policy": (c_int, [c_void_p, ctypes.c_uint, ctypes.c_double]),
     "ddh_service_start": (c_int, [c_void_p]),
     "ddh_service_stop": (c_int, [c_void_p]),
     "ddh_service_free": (c_int, [c_void_p]),
@@ -103,6 +119,8 @@ _SIGS = {
     "ddh_fft_schedule_count": (c_int, [c_int]),
     "ddh_set_fft_schedule": (c_int, [c_int, c_int]),
     "ddh_get_fft_schedule": (c_int, [c_int]),
+    "ddh_set_staged_chunk": (c_int, [c_int, c_int]),
+    "ddh_get_staged_chunk": (c_int, [c_int]),
     "ddh_fft2": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "ddh_sync": (c_int, [c_void_p]),
     "ddh_checkpoint_bytes": (c_size_t, [c_int]),

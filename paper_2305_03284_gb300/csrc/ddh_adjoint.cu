@@ -538,47 +538,88 @@ int ddh_internal_step_backward(int n, const ddh_params* prm, const void* twiddle
 // Scratch for ddh_step_backward_noalloc: a file-scope device array, present on every device
 // that loads the library until the process exits.  It holds the backward workspace of grids up
 // to 128 x 128 (28 N^2 + 1024 floats = 1796 KiB).  Host code must not pass the array's name to a
-// kernel (on the host it is only a stand-in); its device address is looked up once per device.
+// kernel (on the host it is only a stand-in); its device address is looked up with the device
+// current, once per device and CUDA context: a context created after a device reset (a new
+// context ID) gets a fresh lookup, so a stale address is never passed to the kernels.
 namespace {
 constexpr int kNoAllocMaxN = 128;
+constexpr int kNoAllocDevices = 64;
 constexpr size_t kNoAllocScratchFloats = 28 * static_cast<size_t>(kNoAllocMaxN) * kNoAllocMaxN + ddh::kBwRedFloats;
 static __device__ __align__(256) float g_backward_scratch[kNoAllocScratchFloats];
 std::mutex g_scratch_mu;
-void* g_scratch_addr[64] = {};
+void* g_scratch_addr[kNoAllocDevices] = {};
+unsigned long long g_scratch_ctx[kNoAllocDevices] = {};
+
+// The unique ID of the calling thread's current CUDA context (driver cuCtxGetCurrent and
+// cuCtxGetId, reached through the runtime's driver entry points), or 0 if unavailable.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current == nullptr || get_id == nullptr || get_current(&ctx) != 0 || ctx == nullptr) return 0;
+  return get_id(ctx, &id) == 0 ? id : 0;
+}
 }  // namespace
 
 extern "C" int ddh_step_backward_noalloc(ddh_state* s, const void* y, const float* r_prev, const float* phi_prev,
                                          const float* trace, const float* r_new, const float* r_bar,
                                          const float* phi_bar, float* r_prev_bar, float* phi_prev_bar,
                                          float* grads) {
+  DdhNvtxRange nv("ddh_step_backward_noalloc");
   const ddh_params* prm = nullptr;
   const void* tw = nullptr;
   void* stream = nullptr;
   int dev = 0;
   if (ddh_internal_state_info(s, &prm, &tw, &stream, &dev) != DDH_OK) return DDH_EINVAL;
-  if (y == nullptr || r_prev == nullptr || phi_prev == nullptr || trace == nullptr || r_new == nullptr ||
-      r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr || phi_prev_bar == nullptr || grads == nullptr)
+  if (r_prev == nullptr || phi_prev == nullptr || r_new == nullptr || r_bar == nullptr || phi_bar == nullptr ||
+      r_prev_bar == nullptr || phi_prev_bar == nullptr || grads == nullptr) {
+    ddh_internal_set_error("ddh_step_backward_noalloc: null buffer argument");
     return DDH_EINVAL;
+  }
+  int rc = ddh_internal_backward_check(s, y, trace);
+  if (rc != DDH_OK) return rc;
   if (prm->n > kNoAllocMaxN) {
     ddh_internal_set_error("ddh_step_backward_noalloc: grid larger than 128 x 128 (its static scratch is 1796 KiB); "
                            "use ddh_step_backward with a caller workspace");
     return DDH_EINVAL;
   }
-  if (prm->n_k != 1 || prm->phase_block != 1 || prm->phase_prior > 0.f || prm->noise_update) return DDH_EINVAL;
-  if (reinterpret_cast<uintptr_t>(y) % 16 != 0 || reinterpret_cast<uintptr_t>(trace) % 8 != 0) return DDH_EINVAL;
-  if (dev < 0 || dev >= 64) return DDH_EINVAL;
-  cudaError_t e = cudaSetDevice(dev);
+  if (dev < 0 || dev >= kNoAllocDevices) {
+    ddh_internal_set_error("ddh_step_backward_noalloc: device ordinal beyond the supported 64");
+    return DDH_EINVAL;
+  }
+  DdhDeviceGuard guard(dev);
+  cudaError_t e = guard.error();
   if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (g_scratch_addr[dev] == nullptr) {
-      // first call on this device (with it current): the array's device address
-      e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_backward_scratch);
+    const unsigned long long ctx = current_context_id();
+    if (g_scratch_addr[dev] == nullptr || ctx == 0 || ctx != g_scratch_ctx[dev]) {
+      // first call on this device (or in a new context), with the device current
+      void* addr = nullptr;
+      e = cudaGetSymbolAddress(&addr, g_backward_scratch);
       if (e != cudaSuccess) {
         g_scratch_addr[dev] = nullptr;
         return ddh_internal_cuda_fail(e);
       }
+      g_scratch_addr[dev] = addr;
+      g_scratch_ctx[dev] = ctx;
     }
     scratch = g_scratch_addr[dev];
   }

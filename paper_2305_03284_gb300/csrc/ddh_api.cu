@@ -32,7 +32,8 @@ struct ddh_state {
   unsigned* status;
   float2* ystage;
   float* scalar;
-  void* l2scratch;  // working images of the L2-staged kernels (512 x 512 grids only)
+  bool staged;      // steps run on the L2-staged kernels (exec_path), else the cluster kernel
+  void* l2scratch;  // working images of the L2-staged kernels (staged states only)
   const float2* tw;
   int64_t frame;
   int64_t ap_count;
@@ -65,21 +66,38 @@ int cuda_fail(cudaError_t e) {
     cudaError_t e_ = (call);                   \
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
+// `dev` current until the enclosing scope ends (the caller's device is restored then)
+#define DDH_ON_DEVICE(dev)                 \
+  DdhDeviceGuard ddh_dev_guard_(dev);      \
+  DDH_CUDA(ddh_dev_guard_.error())
 
 bool supported_n(int n) { return n == 32 || n == 64 || n == 128 || n == 256 || n == 512; }
-bool cluster_n(int n) { return n != 512; }  // 512 uses the L2-staged kernels
+bool cluster_n(int n) { return n != 512; }  // grids the cluster kernel (and k_strehl, k_fft2) handles
+bool staged_n(int n) { return n == 128 || n == 256 || n == 512; }  // grids of the L2-staged kernels
 int n_slot(int n) { return n == 32 ? 3 : n == 64 ? 0 : n == 128 ? 1 : n == 256 ? 2 : 4; }
+// the kernels a state with parameters `p` steps on (exec_path resolved)
+bool staged_path(const ddh_params& p) {
+  return p.exec_path == DDH_PATH_STAGED || (p.exec_path == DDH_PATH_DEFAULT && !cluster_n(p.n));
+}
 
 std::mutex g_mu;
-bool g_configured[kMaxDevices][5] = {};
+bool g_configured[kMaxDevices][5] = {};     // cluster kernels (N <= 256) and the twiddle table
+bool g_configured_l2[kMaxDevices][5] = {};  // L2-staged kernels
 float2* g_twiddle[kMaxDevices][5] = {};
 int g_schedule[kMaxDevices][5] = {};  // FFT radix schedule used for each grid size
+// streams per launch chunk of the L2-staged kernels, per grid size (0: the default, 16)
+int g_chunk[kMaxDevices][5] = {};
+int staged_chunk(int dev, int n) {
+  const int c = g_chunk[dev][n_slot(n)];
+  return c > 0 ? c : 16;
+}
 
 // Library-owned side streams that let the grid-size groups of one batch run concurrently.
+constexpr int kGroups = 7;  // (grid, path) groups of a batch: 4 cluster sizes, 3 staged sizes
 struct SideStreams {
   bool ready = false;
-  cudaStream_t s[5] = {};
-  cudaEvent_t fork = nullptr, join[5] = {};
+  cudaStream_t s[kGroups] = {};
+  cudaEvent_t fork = nullptr, join[kGroups] = {};
 };
 SideStreams g_side[kMaxDevices];
 
@@ -87,7 +105,7 @@ int side_streams(int dev, SideStreams** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   SideStreams& ss = g_side[dev];
   if (!ss.ready) {
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < kGroups; ++i) {
       DDH_CUDA(cudaStreamCreateWithFlags(&ss.s[i], cudaStreamNonBlocking));
       DDH_CUDA(cudaEventCreateWithFlags(&ss.join[i], cudaEventDisableTiming));
     }
@@ -99,15 +117,19 @@ int side_streams(int dev, SideStreams** out) {
 }
 
 // Per-device, per-N setup: kernel attributes and the twiddle table exp(-2 pi i t / N),
-// evaluated in double precision and rounded once to float.
-int device_setup(int dev, int n, const float2** tw) {
+// evaluated in double precision and rounded once to float; `staged`: also the L2-staged
+// kernels' attributes.
+int device_setup(int dev, int n, const float2** tw, bool staged = false) {
   if (dev < 0 || dev >= kMaxDevices) return DDH_EINVAL;
   std::lock_guard<std::mutex> lock(g_mu);
   const int s = n_slot(n);
+  if (staged && !g_configured_l2[dev][s]) {
+    DDH_CUDA(ddh::configure_l2(n));
+    g_configured_l2[dev][s] = true;
+  }
   if (!g_configured[dev][s]) {
     int active = 1;
     if (cluster_n(n)) DDH_CUDA(ddh::configure(n, &active));
-    else DDH_CUDA(ddh::configure_l2(n));
     if (active < 1) {
       std::snprintf(g_cuda_err, sizeof(g_cuda_err), "no resident cluster of %d CTAs x %zu B shared memory", n / 16,
                     ddh::step_smem_bytes(n));
@@ -158,6 +180,9 @@ int validate(const ddh_params* p) {
   if (p->noise_update != 0 && p->noise_update != 1) return DDH_EINVAL;
   if (p->phase_prior > 0.f && (p->phase_block == 1 || p->n_k != 1 || p->n > 256)) return DDH_EINVAL;
   if (p->noise_update && p->n > 256) return DDH_EINVAL;
+  if (p->exec_path < DDH_PATH_DEFAULT || p->exec_path > DDH_PATH_STAGED) return DDH_EINVAL;
+  if (p->exec_path == DDH_PATH_CLUSTER && !cluster_n(p->n)) return DDH_EINVAL;
+  if (staged_path(*p) && (!staged_n(p->n) || p->phase_prior > 0.f || p->noise_update)) return DDH_EINVAL;
   return DDH_OK;
 }
 
@@ -276,8 +301,8 @@ int enqueue(ddh_state* s, const void* y, float* trace, bool y_host = false, floa
             float* r_copy = nullptr) {
   if (s == nullptr || y == nullptr) return DDH_EINVAL;
   if (reinterpret_cast<uintptr_t>(y) % 16 != 0) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
-  if (!cluster_n(s->prm.n)) {
+  DDH_ON_DEVICE(s->device);
+  if (s->staged) {
     if (trace != nullptr || y_host || phi_copy != nullptr || r_copy != nullptr) return DDH_EINVAL;  // cluster path
     ddh::L2Batch lb{};
     lb.prm[0] = s->kp;
@@ -307,16 +332,23 @@ int enqueue(ddh_state* s, const void* y, float* trace, bool y_host = false, floa
   return DDH_OK;
 }
 
-// Enqueue one step of every state (all on `main`'s device): states are grouped by grid size,
-// each group (chunks of kMaxBatch) on its own side stream, forked from and joined back into
-// `main`.  Frames come from `ys[i]` or, when `ytab` is set, from ytab[i] on the device.
+// Enqueue one step of every state (all on `main`'s device): states are grouped by grid size
+// and path, each group (chunks of kMaxBatch, or kMaxBatchL2 on the staged path) on its own side
+// stream, forked from and joined back into `main`.  Frames come from `ys[i]` or, when `ytab` is
+// set, from ytab[i] on the device (then the states of one launch must be consecutive).
 int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2* const* ytab, int count,
                   cudaStream_t main, int dev) {
-  const int sizes[5] = {512, 32, 64, 128, 256};
+  struct Group {
+    int n;
+    bool staged;
+  };
+  const Group order[kGroups] = {{512, true}, {256, true}, {128, true}, {32, false},
+                                {64, false}, {128, false}, {256, false}};
+  auto member = [&](int i, const Group& gr) { return states[i]->prm.n == gr.n && states[i]->staged == gr.staged; };
   int groups = 0;
-  for (int n : sizes)
+  for (const Group& gr : order)
     for (int i = 0; i < count; ++i)
-      if (states[i]->prm.n == n) { ++groups; break; }
+      if (member(i, gr)) { ++groups; break; }
   SideStreams* ss = nullptr;
   if (groups > 1) {
     int rc = side_streams(dev, &ss);
@@ -324,12 +356,10 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
     DDH_CUDA(cudaEventRecord(ss->fork, main));
   }
   int g = 0;
-  for (int n : sizes) {
-    ddh::StepBatch b{};
-    b.ytab = ytab;
-    int first = -1, members = 0;
-    for (int i = 0; i < count; ++i)
-      if (states[i]->prm.n == n) { if (first < 0) first = i; ++members; }
+  for (const Group& gr : order) {
+    const int n = gr.n;
+    int members = 0;
+    for (int i = 0; i < count; ++i) members += member(i, gr) ? 1 : 0;
     if (members == 0) continue;
     cudaStream_t st = main;
     if (ss != nullptr) {
@@ -337,13 +367,13 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
       DDH_CUDA(cudaStreamWaitEvent(st, ss->fork, 0));
     }
     const int sched = g_schedule[dev][n_slot(n)];
-    if (!cluster_n(n)) {
+    if (gr.staged) {
       ddh::L2Batch lb{};
       lb.ytab = ytab;
       lb.count = 0;
       for (int i = 0; i < count; ++i) {
         ddh_state* s = states[i];
-        if (s->prm.n != n) continue;
+        if (!member(i, gr)) continue;
         if (lb.count > 0 && s->kp.n_k != lb.prm[0].n_k) {  // one EM-iteration count per launch
           DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
           lb.count = 0;
@@ -353,36 +383,33 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
         lb.st[lb.count] = l2_view(s, ys != nullptr ? ys[i] : nullptr);
         lb.tw = s->tw;
         ++lb.count;
-        const bool next_same = i + 1 < count && states[i + 1]->prm.n == n;
-        if (lb.count == ddh::kMaxBatchL2 || (ytab != nullptr && !next_same)) {
+        const bool next_same = i + 1 < count && member(i + 1, gr);
+        if (lb.count == staged_chunk(dev, n) || (ytab != nullptr && !next_same)) {
           DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
           lb.count = 0;
         }
       }
       if (lb.count > 0) DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
-      if (ss != nullptr) {
-        DDH_CUDA(cudaEventRecord(ss->join[g], st));
-        DDH_CUDA(cudaStreamWaitEvent(main, ss->join[g], 0));
+    } else {
+      ddh::StepBatch b{};
+      b.ytab = ytab;
+      b.count = 0;
+      for (int i = 0; i < count; ++i) {
+        ddh_state* s = states[i];
+        if (!member(i, gr)) continue;
+        if (b.count == 0) b.ytab_base = i;  // ytab rows of one launch must be consecutive
+        b.prm[b.count] = s->kp;
+        b.fa[b.count] = frame_args(s, ys != nullptr ? ys[i] : nullptr, nullptr);
+        b.tw = s->tw;
+        ++b.count;
+        const bool next_same = i + 1 < count && member(i + 1, gr);
+        if (b.count == ddh::kMaxBatch || (ytab != nullptr && !next_same)) {
+          DDH_CUDA(ddh::launch_step(n, sched, b, st));
+          b.count = 0;
+        }
       }
-      ++g;
-      continue;
+      if (b.count > 0) DDH_CUDA(ddh::launch_step(n, sched, b, st));
     }
-    b.count = 0;
-    for (int i = 0; i < count; ++i) {
-      ddh_state* s = states[i];
-      if (s->prm.n != n) continue;
-      if (b.count == 0) b.ytab_base = i;  // ytab rows of one launch must be consecutive
-      b.prm[b.count] = s->kp;
-      b.fa[b.count] = frame_args(s, ys != nullptr ? ys[i] : nullptr, nullptr);
-      b.tw = s->tw;
-      ++b.count;
-      const bool next_same = i + 1 < count && states[i + 1]->prm.n == n;
-      if (b.count == ddh::kMaxBatch || (ytab != nullptr && !next_same)) {
-        DDH_CUDA(ddh::launch_step(n, sched, b, st));
-        b.count = 0;
-      }
-    }
-    if (b.count > 0) DDH_CUDA(ddh::launch_step(n, sched, b, st));
     if (ss != nullptr) {
       DDH_CUDA(cudaEventRecord(ss->join[g], st));
       DDH_CUDA(cudaStreamWaitEvent(main, ss->join[g], 0));
@@ -418,6 +445,32 @@ int ddh_internal_state_info(const ddh_state* s, const ddh_params** prm, const vo
 }
 
 void ddh_internal_set_error(const char* msg) { std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", msg); }
+
+size_t ddh_internal_state_bytes(const ddh_params* p) {
+  if (p == nullptr || !supported_n(p->n)) return 0;
+  const size_t img = image_bytes(p->n);
+  // r, phi, 2-image staging buffer, status and scalar words (+ the L2-staged working images)
+  return 4 * img + 512 + (staged_path(*p) ? ddh::l2_scratch_bytes(p->n) : 0);
+}
+
+int ddh_internal_backward_check(const ddh_state* s, const void* y, const float* trace) {
+  const char* why = nullptr;
+  if (s == nullptr)
+    why = "frame-step adjoint: null state";
+  else if (s->prm.n_k != 1 || s->prm.phase_block != 1)
+    why = "frame-step adjoint: only one EM iteration per frame with the per-pixel phase is differentiated";
+  else if (s->staged)
+    why = "frame-step adjoint: grids up to 256 x 256 on the cluster path only";
+  else if (aux_needed(s->prm))
+    why = "frame-step adjoint: no adjoint through the tile-phase prior or the sigma^2 M-step";
+  else if (y == nullptr || reinterpret_cast<uintptr_t>(y) % 16 != 0)
+    why = "frame-step adjoint: frame pointer null or not 16-byte aligned";
+  else if (trace == nullptr || reinterpret_cast<uintptr_t>(trace) % 8 != 0)
+    why = "frame-step adjoint: trace pointer null or not 8-byte aligned";
+  if (why == nullptr) return DDH_OK;
+  ddh_internal_set_error(why);
+  return DDH_EINVAL;
+}
 
 extern "C" {
 
@@ -481,9 +534,11 @@ int ddh_init(ddh_state** out, const ddh_params* p, void* cuda_stream) {
   int dev = 0;
   DDH_CUDA(cudaGetDevice(&dev));
   const float2* tw = nullptr;
-  rc = device_setup(dev, p->n, &tw);
+  const bool staged = staged_path(*p);
+  rc = device_setup(dev, p->n, &tw, staged);
   if (rc != DDH_OK) return rc;
   ddh_state* s = new ddh_state{};
+  s->staged = staged;
   s->prm = *p;
   s->kp = derive(*p);
   s->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -496,7 +551,7 @@ int ddh_init(ddh_state** out, const ddh_params* p, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaMalloc(&s->status, 256);
   if (e == cudaSuccess) e = cudaMalloc(&s->ystage, 2 * img);
   if (e == cudaSuccess) e = cudaMalloc(&s->scalar, 256);
-  if (e == cudaSuccess && !cluster_n(p->n)) e = cudaMalloc(&s->l2scratch, ddh::l2_scratch_bytes(p->n));
+  if (e == cudaSuccess && staged) e = cudaMalloc(&s->l2scratch, ddh::l2_scratch_bytes(p->n));
   if (e == cudaSuccess) e = cudaMemsetAsync(s->r, 0, img, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->phi, 0, img, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->status, 0, 256, s->stream);
@@ -540,7 +595,7 @@ static void* mapped_host(const void* p) {
 // Host frames in place: where both buffers are pinned and mapped, the step kernel reads the frame
 // and writes phi over the CPU-GPU link itself (no staging copies, one launch per frame).
 static bool zero_copy(const ddh_state* s, const void* y_host, float* phi_host, const void** yd, float** pd) {
-  if (!cluster_n(s->prm.n) || aux_needed(s->prm)) return false;
+  if (s->staged || aux_needed(s->prm)) return false;
   *yd = mapped_host(y_host);
   *pd = static_cast<float*>(mapped_host(phi_host));
   return *yd != nullptr && *pd != nullptr && reinterpret_cast<uintptr_t>(*yd) % 16 == 0 &&
@@ -564,7 +619,7 @@ static int host_async_setup(ddh_state* s) {
 int ddh_step_host_async(ddh_state* s, const void* y_host, float* phi_host_out, int64_t* ticket) {
   DdhNvtxRange nv("ddh_step_host_async");
   if (s == nullptr || y_host == nullptr || phi_host_out == nullptr || ticket == nullptr) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   int rc = host_async_setup(s);
   if (rc != DDH_OK) return rc;
   const void* yd = nullptr;
@@ -596,7 +651,7 @@ int ddh_step_host_async(ddh_state* s, const void* y_host, float* phi_host_out, i
 
 int ddh_host_wait(ddh_state* s, int64_t ticket) {
   if (s == nullptr || ticket < 0 || ticket >= s->hcount) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   // the slot holds this frame's event or a later frame's, which completes after it
   DDH_CUDA(cudaEventSynchronize(s->ev_done[ticket & 7]));
   return DDH_OK;
@@ -605,7 +660,7 @@ int ddh_host_wait(ddh_state* s, int64_t ticket) {
 int ddh_step_host(ddh_state* s, const void* y_host, float* phi_host_out) {
   DdhNvtxRange nv("ddh_step_host");
   if (s == nullptr || y_host == nullptr || phi_host_out == nullptr) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   const void* yd = nullptr;
   float* pd = nullptr;
   if (zero_copy(s, y_host, phi_host_out, &yd, &pd)) {
@@ -624,7 +679,7 @@ int ddh_step_host(ddh_state* s, const void* y_host, float* phi_host_out) {
 static int copy_out(const ddh_state* cs, const float* src, float* out) {
   ddh_state* s = const_cast<ddh_state*>(cs);
   if (s == nullptr || out == nullptr) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   DDH_CUDA(cudaMemcpyAsync(out, src, image_bytes(s->prm.n), cudaMemcpyDefault, s->stream));
   if (is_host_pointer(out)) return check_status(s);
   return DDH_OK;
@@ -635,7 +690,7 @@ int ddh_reflectance(const ddh_state* s, float* out) { return s ? copy_out(s, s->
 
 int ddh_set_state(ddh_state* s, const float* r, const float* phi, int64_t frame_index) {
   if (s == nullptr || r == nullptr || phi == nullptr || frame_index < 0) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   const size_t img = image_bytes(s->prm.n);
   DDH_CUDA(cudaMemcpyAsync(s->r, r, img, cudaMemcpyDefault, s->stream));
   DDH_CUDA(cudaMemcpyAsync(s->phi, phi, img, cudaMemcpyDefault, s->stream));
@@ -648,7 +703,8 @@ int64_t ddh_frame_index(const ddh_state* s) { return s ? s->frame : -1; }
 
 int ddh_set_params(ddh_state* s, const ddh_params* p) {
   if (s == nullptr || p == nullptr || validate(p) != DDH_OK || p->n != s->prm.n) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  if (staged_path(*p) != s->staged) return DDH_EINVAL;  // the path is fixed for the state's lifetime
+  DDH_ON_DEVICE(s->device);
   s->prm = *p;
   s->kp = derive(*p);
   s->ap_count = aperture_count(p->n, aperture_limit(p->aperture_diam));
@@ -657,7 +713,7 @@ int ddh_set_params(ddh_state* s, const ddh_params* p) {
 
 int ddh_selftest_wait(ddh_state* s, double limit_s) {
   if (s == nullptr || !(limit_s > 0.0) || limit_s > 1.0) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   DDH_CUDA(ddh::launch_wait_selftest(s->status, static_cast<uint64_t>(limit_s * 1e9), s->stream));
   return check_status(s);
 }
@@ -668,7 +724,7 @@ int ddh_noise_estimate(ddh_state* s, float* out) {
     *out = s->prm.noise_var;
     return DDH_OK;
   }
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   float h = 0.f;
   DDH_CUDA(cudaMemcpyAsync(&h, s->aux, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
   DDH_CUDA(cudaStreamSynchronize(s->stream));
@@ -679,7 +735,7 @@ void* ddh_state_stream(const ddh_state* s) { return s ? static_cast<void*>(s->st
 
 int ddh_strehl(ddh_state* s, const float* phi_true_dev, float* out) {
   if (s == nullptr || phi_true_dev == nullptr || out == nullptr || !cluster_n(s->prm.n)) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   ddh::StrehlArgs a{};
   a.phi_est = s->phi;
   a.phi_true = phi_true_dev;
@@ -712,7 +768,7 @@ int ddh_step_batch(ddh_state* const* states, const void* const* ys, int count) {
   if (count == 0) return DDH_OK;
   for (int i = 0; i < count; ++i)
     if (ys[i] == nullptr || reinterpret_cast<uintptr_t>(ys[i]) % 16 != 0) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(states[0]->device));
+  DDH_ON_DEVICE(states[0]->device);
   rc = enqueue_batch(states, ys, nullptr, count, states[0]->stream, states[0]->device);
   if (rc != DDH_OK) return rc;
   for (int i = 0; i < count; ++i) states[i]->frame += 1;
@@ -735,7 +791,7 @@ struct ddh_batch {
 
 int ddh_batch_free(ddh_batch* b) {
   if (b == nullptr) return DDH_OK;
-  cudaSetDevice(b->device);
+  DdhDeviceGuard dg(b->device);
   cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -755,7 +811,7 @@ int ddh_batch_create(ddh_batch** out, ddh_state* const* states, int count) {
   int rc = validate_batch(states, count);
   if (rc != DDH_OK) return rc;
   if (count == 0) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(states[0]->device));
+  DDH_ON_DEVICE(states[0]->device);
   ddh_batch* b = new ddh_batch{};
   b->count = count;
   b->device = states[0]->device;
@@ -800,7 +856,7 @@ int ddh_batch_run(ddh_batch* b, const void* const* ys) {
   if (b == nullptr || ys == nullptr) return DDH_EINVAL;
   for (int i = 0; i < b->count; ++i)
     if (ys[i] == nullptr || reinterpret_cast<uintptr_t>(ys[i]) % 16 != 0) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(b->device));
+  DDH_ON_DEVICE(b->device);
   const int slot = b->run & 3;
   DDH_CUDA(cudaEventSynchronize(b->slot_done[slot]));  // that slot's previous upload has run
   std::memcpy(b->staging[slot], ys, sizeof(void*) * b->count);
@@ -821,12 +877,14 @@ int ddh_step_backward(ddh_state* s, const void* y, const float* r_prev, const fl
       r_new == nullptr || r_bar == nullptr || phi_bar == nullptr || r_prev_bar == nullptr ||
       phi_prev_bar == nullptr || grads == nullptr || workspace == nullptr)
     return DDH_EINVAL;
-  if (s->prm.n_k != 1 || s->prm.phase_block != 1 || !cluster_n(s->prm.n) || aux_needed(s->prm)) return DDH_EINVAL;
-  if (workspace_bytes < ddh_backward_workspace_bytes(s->prm.n)) return DDH_EINVAL;
-  if (reinterpret_cast<uintptr_t>(y) % 16 != 0 || reinterpret_cast<uintptr_t>(workspace) % 16 != 0 ||
-      reinterpret_cast<uintptr_t>(trace) % 8 != 0)
+  int rc = ddh_internal_backward_check(s, y, trace);
+  if (rc != DDH_OK) return rc;
+  if (workspace_bytes < ddh_backward_workspace_bytes(s->prm.n) || reinterpret_cast<uintptr_t>(workspace) % 16 != 0) {
+    ddh_internal_set_error("ddh_step_backward: workspace smaller than ddh_backward_workspace_bytes(n) or not "
+                           "16-byte aligned");
     return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  }
+  DDH_ON_DEVICE(s->device);
   return ddh_internal_step_backward(s->prm.n, &s->prm, s->tw, s->stream, y, r_prev, phi_prev, trace, r_new, r_bar,
                                     phi_bar, r_prev_bar, phi_prev_bar, grads, workspace);
 }
@@ -845,7 +903,7 @@ int ddh_unrolled_forward(ddh_state* s, int k_frames, const void* const* ys, floa
   DdhNvtxRange nv("ddh_unrolled_forward");
   if (s == nullptr || ys == nullptr || r_ckpt == nullptr || phi_ckpt == nullptr || k_frames < 1) return DDH_EINVAL;
   if (aux_needed(s->prm)) return DDH_EINVAL;  // no adjoint through the post-step M-steps
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   const size_t img = image_bytes(s->prm.n);
   for (int k = 0; k <= k_frames; ++k)
     if (r_ckpt[k] == nullptr || phi_ckpt[k] == nullptr) return DDH_EINVAL;
@@ -856,7 +914,7 @@ int ddh_unrolled_forward(ddh_state* s, int k_frames, const void* const* ys, floa
   for (int k = 0; k < k_frames; ++k) {
     float* tr = traces != nullptr ? traces[k] : nullptr;
     if (traces != nullptr && (tr == nullptr || reinterpret_cast<uintptr_t>(tr) % 8 != 0)) return DDH_EINVAL;
-    const int rc = cluster_n(s->prm.n) ? enqueue(s, ys[k], tr, false, phi_ckpt[k + 1], r_ckpt[k + 1]) : DDH_EINVAL;
+    const int rc = !s->staged ? enqueue(s, ys[k], tr, false, phi_ckpt[k + 1], r_ckpt[k + 1]) : DDH_EINVAL;
     if (rc != DDH_OK) return rc;
   }
   return DDH_OK;
@@ -921,6 +979,23 @@ int ddh_set_fft_schedule(int n, int schedule) {
   return DDH_OK;
 }
 
+int ddh_set_staged_chunk(int n, int chunk) {
+  if (!staged_n(n) || chunk < 1 || chunk > ddh::kMaxBatchL2) return DDH_EINVAL;
+  int dev = 0;
+  DDH_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return DDH_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_chunk[dev][n_slot(n)] = chunk;
+  return DDH_OK;
+}
+
+int ddh_get_staged_chunk(int n) {
+  if (!staged_n(n)) return DDH_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DDH_ECUDA;
+  return staged_chunk(dev, n);
+}
+
 int ddh_get_fft_schedule(int n) {
   if (!supported_n(n)) return DDH_EINVAL;
   int dev = 0;
@@ -946,7 +1021,7 @@ int ddh_fft2(const void* in, void* out, int n, int inverse, void* cuda_stream) {
 
 int ddh_sync(ddh_state* s) {
   if (s == nullptr) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   return check_status(s);
 }
 
@@ -957,7 +1032,7 @@ size_t ddh_checkpoint_bytes(int n) {
 
 int ddh_save(ddh_state* s, void* buf, size_t bytes) {
   if (s == nullptr || buf == nullptr || bytes < ddh_checkpoint_bytes(s->prm.n)) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  DDH_ON_DEVICE(s->device);
   CkptHeader h{};
   h.magic = kMagic;
   h.version = kVersion;
@@ -980,8 +1055,8 @@ int ddh_load(ddh_state* s, const void* buf, size_t bytes) {
   CkptHeader h{};
   std::memcpy(&h, buf, sizeof(h));
   if (h.magic != kMagic || h.prm.n != s->prm.n || bytes < ddh_checkpoint_bytes(s->prm.n)) return DDH_EINVAL;
-  if (validate(&h.prm) != DDH_OK) return DDH_EINVAL;
-  DDH_CUDA(cudaSetDevice(s->device));
+  if (validate(&h.prm) != DDH_OK || staged_path(h.prm) != s->staged) return DDH_EINVAL;
+  DDH_ON_DEVICE(s->device);
   const char* p = static_cast<const char*>(buf) + sizeof(h);
   const size_t img = image_bytes(s->prm.n);
   DDH_CUDA(cudaMemcpyAsync(s->r, p, img, cudaMemcpyHostToDevice, s->stream));
@@ -999,7 +1074,7 @@ int ddh_load(ddh_state* s, const void* buf, size_t bytes) {
 
 int ddh_free(ddh_state* s) {
   if (s == nullptr) return DDH_OK;
-  cudaSetDevice(s->device);
+  DdhDeviceGuard dg(s->device);
   cudaStreamSynchronize(s->stream);
   cudaFree(s->r);
   cudaFree(s->phi);

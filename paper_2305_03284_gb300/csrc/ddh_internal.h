@@ -14,6 +14,31 @@ struct DdhNvtxRange {
   DdhNvtxRange& operator=(const DdhNvtxRange&) = delete;
 };
 
+// Makes `dev` the calling thread's current device for the guard's lifetime and restores the
+// caller's current device when the guard goes out of scope, so that no library call changes
+// which device the caller's thread has current.
+class DdhDeviceGuard {
+ public:
+  explicit DdhDeviceGuard(int dev) {
+    err_ = cudaGetDevice(&prev_);
+    if (err_ == cudaSuccess && prev_ != dev) {
+      err_ = cudaSetDevice(dev);
+      switched_ = err_ == cudaSuccess;
+    }
+  }
+  ~DdhDeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  cudaError_t error() const { return err_; }
+  DdhDeviceGuard(const DdhDeviceGuard&) = delete;
+  DdhDeviceGuard& operator=(const DdhDeviceGuard&) = delete;
+
+ private:
+  int prev_ = 0;
+  bool switched_ = false;
+  cudaError_t err_ = cudaSuccess;
+};
+
 // Record `e` as the library's last CUDA error and map it to DDH_ENOMEM / DDH_ECUDA.
 int ddh_internal_cuda_fail(cudaError_t e);
 
@@ -30,3 +55,9 @@ int ddh_internal_state_info(const ddh_state* s, const ddh_params** prm, const vo
                             int* device);
 // Set the library's last error message (returned by ddh_last_cuda_error).
 void ddh_internal_set_error(const char* msg);
+// The state and argument checks shared by every frame-step adjoint entry point: DDH_OK, or
+// DDH_EINVAL with the reason set as the library's last error message.
+int ddh_internal_backward_check(const ddh_state* s, const void* y, const float* trace);
+// Device bytes a state with parameters `p` holds (its path's working images included); 0 if
+// the grid size is unsupported.
+size_t ddh_internal_state_bytes(const ddh_params* p);

@@ -79,9 +79,10 @@ struct StepBatch {
   int count;
 };
 
-// L2-staged path (grids beyond a cluster's shared memory): per-stream views of the global
-// scratch the stages exchange data through.
-constexpr int kMaxBatchL2 = 16;
+// L2-staged path (grids beyond a cluster's shared memory, or any batch run for throughput):
+// per-stream views of the global scratch the stages exchange data through.  A batch is cut
+// into launch chunks of at most kMaxBatchL2 streams (the chunk size is a tuning knob).
+constexpr int kMaxBatchL2 = 32;
 
 struct L2Stream {
   const float2* y;

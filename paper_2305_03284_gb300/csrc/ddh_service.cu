@@ -3,16 +3,12 @@
 // One scheduler thread per service.  Sensors (ddh_state each, admitted against a memory
 // budget) own FIFOs of submitted frames.  The thread loops: (1) resolve the oldest in-flight
 // batches whose completion event has fired (completion timestamp, latency from arrival);
-// (2) if fewer than `max_in_flight` batches are on the device, launch one batch holding the
-// next queued frame of every sensor that has one.  A batch holds at most one frame per sensor;
-// frames n and n+1 of a sensor are dependent, and they may sit in consecutive batches on the
-// device at the same time because every batch runs in order on the service's one stream (a
-// batch's side-stream branches fork from and join back into it).  A batch may start behind a
-// running one only if it holds at least half of the sensors: under a backlog the device then
-// never idles between batches, while light traffic still collects every frame that arrived
-// during the running batch into the next one (small batches behind a large one would each
-// spend a full launch sequence on a few frames).  Host code only: the batch itself is
-// enqueue_batch() of ddh_api.cu.
+// (2) if the batch-formation policy (ddh_sched_pick, a pure function of the queue state) says
+// so, launch one batch holding the next queued frame of every sensor that has one.  A batch
+// holds at most one frame per sensor; frames n and n+1 of a sensor are dependent, and they may
+// sit in consecutive batches on the device at the same time because every batch runs in order
+// on the service's one stream (a batch's side-stream branches fork from and join back into
+// it).  Host code only: the batch itself is enqueue_batch() of ddh_api.cu.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -79,6 +75,10 @@ struct ddh_service {
   int64_t frames_launched = 0;
   std::vector<ddh_state*> scratch_states;
   std::vector<const void*> scratch_ys;
+  std::vector<ddh_sched_sensor> view;  // the policy's view of the sensors (map order)
+  std::vector<unsigned char> pick;
+  double age_limit_s = 1e-3;
+  unsigned sched_flags = DDH_SCHED_BACKLOG | DDH_SCHED_AGE;
 };
 
 namespace {
@@ -97,53 +97,72 @@ void reap_locked(ddh_service* s) {
   }
 }
 
-// One scheduler iteration; returns the number of frames launched (or a negative error).
+// One scheduler iteration; returns the number of frames launched (or a negative error).  The
+// batch is formed under the service lock (frames popped, their sensors' in-flight counts
+// raised, so that no release frees those states) and launched outside it, so that callers
+// submitting frames never wait for a launch sequence.  Only one thread runs this function.
 int service_step(ddh_service* s) {
-  std::lock_guard<std::mutex> lock(s->mu);
-  while (!s->in_flight.empty()) {
-    Batch& b = s->in_flight.front();
-    const cudaError_t q = cudaEventQuery(b.ev);
-    if (q == cudaErrorNotReady) break;
-    if (q != cudaSuccess) return ddh_internal_cuda_fail(q);
-    const double t = now_s();
-    for (auto& it : b.items) {
-      Sensor* se = it.first;
-      se->in_flight -= 1;
-      se->done += 1;
-      ddh_completion c{};
-      c.tag = it.second.tag;
-      c.sensor = se->id;
-      c.frame_index = se->done;
-      c.arrival_s = it.second.arrival;
-      c.done_s = t;
-      s->completed.push_back(c);
-    }
-    s->free_events.push_back(b.ev);
-    s->in_flight.pop_front();
-  }
-  reap_locked(s);
-  if (static_cast<int>(s->in_flight.size()) >= s->max_in_flight) return 0;
-  int ready = 0;
-  for (auto& kv : s->sensors) ready += kv.second->queue.empty() ? 0 : 1;
-  if (ready == 0) return 0;
-  // behind a running batch only a batch of at least half of the sensors goes out: under a
-  // backlog the device never waits for the scheduler, and no launch sequence is spent on a
-  // few frames that would otherwise join the next full batch
-  if (!s->in_flight.empty() && 2 * ready < static_cast<int>(s->sensors.size())) return 0;
-  s->scratch_states.clear();
-  s->scratch_ys.clear();
   Batch b;
-  for (auto& kv : s->sensors) {
-    Sensor* se = kv.second;
-    if (se->queue.empty()) continue;
-    Pending p = se->queue.front();
-    se->queue.pop_front();
-    se->in_flight += 1;
-    s->scratch_states.push_back(se->state);
-    s->scratch_ys.push_back(p.y);
-    b.items.emplace_back(se, p);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    while (!s->in_flight.empty()) {
+      Batch& done = s->in_flight.front();
+      const cudaError_t q = cudaEventQuery(done.ev);
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) return ddh_internal_cuda_fail(q);
+      const double t = now_s();
+      for (auto& it : done.items) {
+        Sensor* se = it.first;
+        se->in_flight -= 1;
+        se->done += 1;
+        ddh_completion c{};
+        c.tag = it.second.tag;
+        c.sensor = se->id;
+        c.frame_index = se->done;
+        c.arrival_s = it.second.arrival;
+        c.done_s = t;
+        s->completed.push_back(c);
+      }
+      s->free_events.push_back(done.ev);
+      s->in_flight.pop_front();
+    }
+    reap_locked(s);
+    s->view.clear();
+    for (auto& kv : s->sensors) {
+      const Sensor* se = kv.second;
+      ddh_sched_sensor v{};
+      v.queued = static_cast<int>(se->queue.size());
+      v.oldest_arrival_s = se->queue.empty() ? 0.0 : se->queue.front().arrival;
+      s->view.push_back(v);
+    }
+    s->pick.assign(s->view.size(), 0);
+    const int picked = ddh_sched_pick(s->view.data(), static_cast<int>(s->view.size()),
+                                      static_cast<int>(s->in_flight.size()), s->max_in_flight, now_s(),
+                                      s->age_limit_s, s->sched_flags, s->pick.data());
+    if (picked <= 0) return picked < 0 ? picked : 0;
+    s->scratch_states.clear();
+    s->scratch_ys.clear();
+    size_t k = 0;
+    for (auto& kv : s->sensors) {
+      Sensor* se = kv.second;
+      if (!s->pick[k++] || se->queue.empty()) continue;
+      Pending p = se->queue.front();
+      se->queue.pop_front();
+      se->in_flight += 1;
+      s->scratch_states.push_back(se->state);
+      s->scratch_ys.push_back(p.y);
+      b.items.emplace_back(se, p);
+    }
+    if (b.items.empty()) return 0;
+    if (s->free_events.empty()) {
+      cudaEvent_t ev;
+      const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
+      s->free_events.push_back(ev);
+    }
+    b.ev = s->free_events.back();
+    s->free_events.pop_back();
   }
-  if (b.items.empty()) return 0;
   DdhNvtxRange nv("ddh_service_batch");
   int rc = DDH_OK;
   if (s->flags & DDH_SERVICE_PER_FRAME_LAUNCH) {
@@ -151,17 +170,16 @@ int service_step(ddh_service* s) {
   } else {
     rc = ddh_step_batch(s->scratch_states.data(), s->scratch_ys.data(), static_cast<int>(b.items.size()));
   }
-  if (rc != DDH_OK) return rc;
-  if (s->free_events.empty()) {
-    cudaEvent_t ev;
-    const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
-    s->free_events.push_back(ev);
+  if (rc == DDH_OK) {
+    const cudaError_t e = cudaEventRecord(b.ev, s->stream);
+    if (e != cudaSuccess) rc = ddh_internal_cuda_fail(e);
   }
-  b.ev = s->free_events.back();
-  s->free_events.pop_back();
-  const cudaError_t e = cudaEventRecord(b.ev, s->stream);
-  if (e != cudaSuccess) return ddh_internal_cuda_fail(e);
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (rc != DDH_OK) {
+    for (auto& it : b.items) it.first->in_flight -= 1;  // the frames are lost with the error
+    s->free_events.push_back(b.ev);
+    return rc;
+  }
   const int launched = static_cast<int>(b.items.size());
   s->in_flight.push_back(std::move(b));
   s->batches += 1;
@@ -186,6 +204,40 @@ void service_loop(ddh_service* s) {
 extern "C" {
 
 double ddh_service_now(void) { return now_s(); }
+
+int ddh_sched_pick(const ddh_sched_sensor* sensors, int count, int batches_in_flight, int max_in_flight,
+                   double now, double age_limit_s, unsigned flags, unsigned char* pick) {
+  if (count < 0 || (count > 0 && (sensors == nullptr || pick == nullptr)) || max_in_flight < 1) return DDH_EINVAL;
+  int ready = 0;
+  bool backlog = false, aged = false;
+  for (int i = 0; i < count; ++i) {
+    pick[i] = 0;
+    if (sensors[i].queued <= 0) continue;
+    ++ready;
+    backlog = backlog || sensors[i].queued >= 2;
+    aged = aged || now - sensors[i].oldest_arrival_s >= age_limit_s;
+  }
+  if (ready == 0 || batches_in_flight >= max_in_flight) return 0;
+  // behind a running batch a new one goes out only if it holds at least half of the sensors
+  // (light traffic gathers into full batches instead of spending a launch sequence on a few
+  // frames), or a sensor has frames waiting beyond the one this batch takes (its frames
+  // arrive faster than batches complete: it advances one frame per batch, so the next batch
+  // must not wait for the running one), or a frame has waited longer than the age limit
+  if (batches_in_flight > 0 && 2 * ready < count && !((flags & DDH_SCHED_BACKLOG) && backlog) &&
+      !((flags & DDH_SCHED_AGE) && aged))
+    return 0;
+  for (int i = 0; i < count; ++i) pick[i] = sensors[i].queued > 0 ? 1 : 0;
+  return ready;
+}
+
+int ddh_service_set_policy(ddh_service* s, unsigned flags, double age_limit_s) {
+  if (s == nullptr || (flags & ~static_cast<unsigned>(DDH_SCHED_BACKLOG | DDH_SCHED_AGE)) || !(age_limit_s > 0.0))
+    return DDH_EINVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->sched_flags = flags;
+  s->age_limit_s = age_limit_s;
+  return DDH_OK;
+}
 
 int ddh_service_create(ddh_service** out, void* cuda_stream, size_t mem_budget_bytes, int max_in_flight,
                        unsigned flags) {
@@ -217,15 +269,16 @@ int ddh_service_create(ddh_service** out, void* cuda_stream, size_t mem_budget_b
 
 size_t ddh_state_bytes(int n) {
   if (n != 32 && n != 64 && n != 128 && n != 256 && n != 512) return 0;
-  const size_t img = sizeof(float) * static_cast<size_t>(n) * n;
-  // r, phi, 2-image staging buffer, status and scalar words (+ L2-staged working images)
-  return 4 * img + 512 + ddh::l2_scratch_bytes(n);
+  ddh_params p{};
+  p.n = n;
+  p.exec_path = DDH_PATH_DEFAULT;
+  return ddh_internal_state_bytes(&p);
 }
 
 int ddh_service_admit(ddh_service* s, int sensor_id, const ddh_params* p) {
   if (s == nullptr || p == nullptr) return DDH_EINVAL;
   if (p->phase_prior > 0.f || p->noise_update) return DDH_EINVAL;  // per-stream post-step M-steps
-  const size_t need = ddh_state_bytes(p->n);
+  const size_t need = ddh_internal_state_bytes(p);
   if (need == 0) return DDH_EINVAL;
   std::lock_guard<std::mutex> lock(s->mu);
   if (s->sensors.count(sensor_id)) return DDH_EINVAL;
@@ -320,7 +373,7 @@ int ddh_service_stop(ddh_service* s) {
 int ddh_service_free(ddh_service* s) {
   if (s == nullptr) return DDH_OK;
   ddh_service_stop(s);  // the scheduler thread has exited: nothing else touches `s`
-  cudaSetDevice(s->device);
+  DdhDeviceGuard dg(s->device);
   cudaStreamSynchronize(s->stream);
   for (auto& kv : s->sensors) {
     ddh_free(kv.second->state);

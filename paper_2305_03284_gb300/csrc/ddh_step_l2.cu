@@ -501,7 +501,7 @@ cudaError_t l2_configure() {
 }  // namespace
 
 size_t l2_scratch_bytes(int n) {
-  if (n != 512) return 0;
+  if (n != 128 && n != 256 && n != 512) return 0;
   const size_t M = static_cast<size_t>(n) * n;
   // fa, fb (complex), r-init, s, 4 weight images, row-block partials + combined stats, flag
   return 2 * M * sizeof(float2) + 6 * M * sizeof(float) + (8 * (n / kT) + 16) * sizeof(float) + 256;
@@ -522,13 +522,22 @@ L2Stream l2_stream_view(void* scratch, int n) {
 }
 
 cudaError_t configure_l2(int n) {
-  if (n != 512) return cudaErrorInvalidValue;
-  return l2_configure<512, 0>();
+  switch (n) {
+    case 128: return l2_configure<128, 0>();
+    case 256: return l2_configure<256, 0>();
+    case 512: return l2_configure<512, 0>();
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_step_l2(int n, int schedule, const L2Batch& b, int n_k, cudaStream_t st) {
-  if (n != 512 || schedule != 0) return cudaErrorInvalidValue;
-  return l2_step<512, 0>(b, n_k, st);
+  (void)schedule;  // the staged kernels use one radix schedule per grid size
+  switch (n) {
+    case 128: return l2_step<128, 0>(b, n_k, st);
+    case 256: return l2_step<256, 0>(b, n_k, st);
+    case 512: return l2_step<512, 0>(b, n_k, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace ddh

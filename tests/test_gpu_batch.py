@@ -109,10 +109,28 @@ def test_every_fft_schedule_matches_oracle(ddh, n):
 
 
 def test_autotune_small(ddh, tmp_path):
+    """The tuner on a reduced search (128^2: FFT schedules, two staged chunks, the path at two
+    batch sizes) writes a table whose winners it leaves selected and that apply() restores."""
     from paper_2305_03284_gb300 import autotune
-    old = ddh.get_fft_schedule(64)
-    table = autotune.tune(sizes=(64,), streams_for={64: 2}, path=str(tmp_path / "t.json"))
-    assert set(table) == {"64"} and 0 <= table["64"]["schedule"] < ddh.fft_schedule_count(64)
-    assert ddh.get_fft_schedule(64) == table["64"]["schedule"]
-    assert autotune.apply(str(tmp_path / "t.json"))["64"]["schedule"] == table["64"]["schedule"]
-    ddh.set_fft_schedule(64, old)
+    L = ddh.lib()
+    old_s, old_c = ddh.get_fft_schedule(128), L.ddh_get_staged_chunk(128)
+    try:
+        out = str(tmp_path / "t.json")
+        table = autotune.tune(path=out, sizes=(128,), batch_sizes=(1, 4), big={128: 4}, chunks=(2, 4),
+                              schedule_streams={128: 2})
+        row = table["128"]
+        assert 0 <= row["schedule"] < ddh.fft_schedule_count(128)
+        assert row["staged_chunk"] in (2, 4) and set(row["path_us_per_step"]) == {"1", "4"}
+        assert ddh.get_fft_schedule(128) == row["schedule"]
+        assert L.ddh_get_staged_chunk(128) == row["staged_chunk"]
+        ddh.set_fft_schedule(128, old_s)
+        L.ddh_set_staged_chunk(128, 3)
+        assert autotune.apply(out)["128"]["staged_chunk"] == row["staged_chunk"]
+        assert L.ddh_get_staged_chunk(128) == row["staged_chunk"] and ddh.get_fft_schedule(128) == row["schedule"]
+        start = row["staged_from_streams"]
+        assert autotune.recommend_path(128, 1000, out) == (2 if start is not None else 1)
+        assert autotune.recommend_path(512, 3, out) == 0
+        assert L.ddh_set_staged_chunk(64, 4) == -1 and L.ddh_set_staged_chunk(256, 33) == -1
+    finally:
+        ddh.set_fft_schedule(128, old_s)
+        L.ddh_set_staged_chunk(128, old_c)

@@ -481,6 +481,72 @@ def test_parity_512_l2_staged(ddh, over):
     assert np.all(gphi[-1][~a] == 0.0)
 
 
+# ------------------------------------------- 128^2 and 256^2 on the L2-staged path (exec_path)
+@pytest.mark.parametrize("which", ["128", "256", "256-tiled", "256-nk2"])
+def test_parity_staged_path_smaller_grids(ddh, which):
+    """The staged kernels (the throughput path of large batches) on the cluster kernel's grid
+    sizes: free-running against the oracle, then teacher-forced frame by frame."""
+    cfg = sy.config_single_256(frames=8) if which.startswith("256") else sy.config_batched(frames=8)[0]
+    over = {"exec_path": 2}
+    if which.endswith("tiled"):
+        over["phase_block"] = 2
+    if which.endswith("nk2"):
+        over["n_k"] = 2
+    st, ys, ph, p = make(ddh, cfg, 8, **over)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    gphi, gr, gS = _run_free(ddh, p, ys[:5], ph[:5])
+    ophi, orr, oS = _run_oracle(prm, ys[:5], ph[:5])
+    assert rel_l2_phase(gphi[-1], ophi[-1], a) < TOL
+    assert rel_l2(gr[-1], orr[-1]) < TOL
+    assert rel_l2(gS, oS) < TOL
+    assert np.all(gphi[-1][~a] == 0.0)
+    s = ddh.Stream(p)
+    ost = o.State(r=orr[-1], phi=ophi[-1], n=5)
+    for i in range(5, 8):
+        r32, p32 = ost.r.astype(np.float32), ost.phi.astype(np.float32)
+        s.set_state(cu(r32), cu(p32), i)
+        s.step(cu(ys[i]))
+        nxt, _ = o.step(o.State(r=r32.astype(np.float64), phi=p32.astype(np.float64), n=i), ys[i], prm)
+        assert rel_l2_phase(np32(s.phase()), nxt.phi, a) < TOL
+        assert rel_l2(np32(s.reflectance()), nxt.r) < TOL
+        ost = nxt
+
+
+def test_staged_and_cluster_paths_agree_and_batches_keep_each_path(ddh):
+    """A 256^2 stream on either path gives the same estimate within the tolerance; in a batch
+    that mixes both paths (and a 512^2 and a 128^2 stream), every stream equals its solo run
+    bit for bit."""
+    cfgs = [sy.config_single_256(4), sy.config_single_256(4), sy.config_batched(4)[0], sy.config_batched(4)[56]]
+    paths = [1, 2, 2, 0]
+    data = [make(ddh, c, 4, exec_path=pa) for c, pa in zip(cfgs, paths)]
+    solo = [ddh.Stream(d[3]) for d in data]
+    batch = [ddh.Stream(d[3]) for d in data]
+    for f in range(4):
+        ys = [cu(d[1][f]) for d in data]
+        for s_, y in zip(solo, ys):
+            s_.step(y)
+        ddh.step_batch(batch, ys)
+    for s1, s2 in zip(solo, batch):
+        assert torch.equal(s1.phase(), s2.phase())
+        assert torch.equal(s1.reflectance(), s2.reflectance())
+    a = o.aperture(256, 128.0)
+    p_cl, p_st = np32(solo[0].phase()).astype(np.float64), np32(solo[1].phase()).astype(np.float64)
+    assert rel_l2_phase(p_st, p_cl, a) < TOL
+    assert rel_l2(np32(solo[1].reflectance()), np32(solo[0].reflectance()).astype(np.float64)) < TOL
+    # the path is fixed for the state's lifetime
+    with pytest.raises(ddh.DdhError):
+        solo[0].set_params(ddh.default_params(256, 128.0, 5.0, exec_path=2))
+    # the staged path has no trace output and no adjoint
+    tr = torch.zeros(ddh.lib().ddh_trace_floats(256), device="cuda")
+    assert ddh.lib().ddh_step_trace(solo[1]._h, ddh.c_void_p(cu(data[1][1][0]).data_ptr()),
+                                    ddh.c_void_p(tr.data_ptr())) == -1
+    with pytest.raises(ddh.DdhError):
+        ddh.Stream(ddh.default_params(64, 32.0, 10.0, exec_path=2))
+    with pytest.raises(ddh.DdhError):
+        ddh.Stream(ddh.default_params(512, 256.0, 10.0, exec_path=1))
+
+
 def test_512_rejects_nonfinite_frame(ddh):
     cfg = sy.config_batched(frames=2)[56]
     st, ys, ph, p = make(ddh, cfg, 2)
