@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--leg", choices=["b256"], default=None,
+                    help="run one extra leg alone and print its JSON (b256: the 256^2 batched comparison)")
+    ap.add_argument("--streams", type=int, default=32, help="streams of the b256 leg")
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-stream", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-frames", type=int, default=0, help=argparse.SUPPRESS)
@@ -483,7 +486,7 @@ def batched_256_measure(ddh, peak_gbs, streams, timesteps=200, ring=8, warm=5):
     return out
 
 
-def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=None):
+def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=None, policy=None):
     """Streaming service (continuous batching) against the same scheduler launching every
     frame on its own, replaying one seeded Poisson arrival trace of the sensor mix (the
     32-sensor mix of 128^2, 256^2 and 512^2 grids, or `cfgs`)."""
@@ -491,8 +494,11 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=N
     import torch
     from paper_2305_03284_gb300 import serve
     from synth import ddh_synth as sy
+    from paper_2305_03284_gb300 import autotune
     if cfgs is None:
         cfgs = sy.config_service(frames_total=total_frames)
+    # each grid size on the kernels the tuning table recommends for that many sensors
+    paths = {n: autotune.recommend_path(n, sum(c.n == n for c in cfgs)) for n in {c.n for c in cfgs}}
     rates = np.array([c.rate_khz * 1e3 for c in cfgs])
     horizon = total_frames / rates.sum()
     rng = np.random.default_rng(seed)
@@ -515,8 +521,11 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=N
 
     def one(per_frame, trace):
         svc = serve.NativeService(per_frame_launch=per_frame)
+        if policy is not None:
+            svc.set_policy(policy)
         for i, c in enumerate(cfgs):
-            svc.admit(i, ddh.default_params(c.n, c.aperture_diam, c.snr))
+            # the per-frame comparison runs the plain path (the library's default kernels)
+            svc.admit(i, ddh.default_params(c.n, c.aperture_diam, c.snr, exec_path=0 if per_frame else paths[c.n]))
         svc.drive([(0.0, i, rings[i][0]) for i in range(len(cfgs))])  # warm-up frame each
         st0 = svc.stats()
         res = svc.drive(trace)
@@ -535,8 +544,60 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=N
     out["saturation_frames_per_s"] = {"continuous_batching": one(False, burst)["frames_per_s"],
                                       "per_frame_launch": one(True, burst)["frames_per_s"]}
     out["scheduler"] = "libddh native scheduler thread (ddh_service_*), batches via ddh_step_batch"
+    out["exec_path_by_grid"] = {str(n): {0: "default", 1: "cluster", 2: "staged"}[v] for n, v in sorted(paths.items())}
     out["latency"] = "scheduled arrival to completion event observed by the scheduler"
     return out
+
+
+def tracking_measure(ddh, sims=10, frames=150):
+    """The paper's Sec. 5.C experiment on its simulation parameters (Sec. 5.A) with a bar-chart
+    object: `sims` seeded simulations of `frames` frames at 256^2, one EM iteration per frame,
+    the tracking parameter set; Strehl ratio per frame on the GPU (evaluation kernel, outside
+    the step), and the step rate of that parameter set (CUDA events, frames back to back)."""
+    import numpy as np
+    import torch
+    from synth import ddh_synth as sy
+    lib = ddh.lib()
+    stream = torch.cuda.Stream()
+    traces, us = [], []
+    with torch.cuda.stream(stream):
+        for sim in range(sims):
+            st = sy.Stream(sy.config_paper_256(sim, frames))
+            ys, ph = st.frames(frames)
+            yd = torch.from_numpy(ys).cuda()
+            pd = torch.from_numpy(ph.astype(np.float32)).cuda()
+            s = ddh.Stream(ddh.tracking_params(256, 128.0, 10.0), stream=stream)
+            tr = []
+            for k in range(frames):
+                s.step(yd[k])
+                tr.append(s.strehl(pd[k]))
+            traces.append(tr)
+            # the same frames again from a fresh state, back to back, for the step rate
+            s2 = ddh.Stream(ddh.tracking_params(256, 128.0, 10.0), stream=stream)
+            ptrs = [ddh.c_void_p(yd[k].data_ptr()) for k in range(frames)]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            queue_ahead(stream)
+            e0.record(stream)
+            for k in range(frames):
+                lib.ddh_step(s2._h, ptrs[k])
+            e1.record(stream)
+            e1.synchronize()
+            us.append(e0.elapsed_time(e1) * 1e3 / frames)
+            s.close()
+            s2.close()
+    t = np.array(traces)
+    best10 = [float(np.convolve(x, np.ones(10) / 10, mode="valid").max()) for x in t]
+    first = [int(np.argmax(np.convolve(x, np.ones(10) / 10, mode="valid") >= 0.8)) + 9
+             if max(np.convolve(x, np.ones(10) / 10, mode="valid")) >= 0.8 else None for x in t]
+    return {"workload": f"{sims} simulations x {frames} frames: 256^2, 128 px pupil, D/r0 10, v = (0.421, 0.421) "
+                        "px/frame, SNR 10 dB, bar-chart object (Sec. 5.A parameters); tracking parameter set "
+                        "(2x2 phase tiles, tile prior 10, sigma_r 0.03, alpha 0.0125), N_k = 1",
+            "best_10_frame_mean_strehl": best10,
+            "sims_reaching_0.8": sum(b >= 0.8 for b in best10),
+            "first_frame_of_a_10_frame_mean_at_0.8": first,
+            "median_strehl_at_frames": {str(k): float(np.median(t[:, k - 1])) for k in (10, 50, 100, 150)},
+            "us_per_frame": float(np.median(us)), "frames_per_s": 1e6 / float(np.median(us)),
+            "strehl": "GPU Strehl kernel per frame, off the timed path"}
 
 
 def service_256_configs(sensors=32, frames_total=10_000):
@@ -738,13 +799,14 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_PX * n * n
     avg_launch_s = ms * 1e-3 / args.steps
     achieved = bytes_per_launch / avg_launch_s / 1e9
-    batched = b256 = service_256 = None
+    batched = b256 = service_256 = tracking = None
     if not args.no_batched and world == 1:
         # the service trace runs first: it is a latency measurement near the fastest sensors'
         # capacity, and it should not inherit the state the 64-stream throughput run leaves
         service = service_measure(ddh)
         service_256 = service_measure(ddh, cfgs=service_256_configs(), label="all sensors at 256^2")
         b256 = {str(k): batched_256_measure(ddh, peak, k) for k in (7, 32)}
+        tracking = tracking_measure(ddh)
         batched = batched_measure(ddh, peak)
         batched["service"] = service
         batched["adjoint"] = adjoint_measure(ddh)
@@ -776,6 +838,7 @@ def run_ours(args):
         "batched": batched,
         "batched_256": b256,
         "service_256": service_256,
+        "tracking_paper_parameters": tracking,
     }
     print(json.dumps(line))
 
@@ -786,7 +849,21 @@ def main():
         return cpu_worker(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg == "b256":
+        return run_leg_b256(args)
     return run_ours(args)
+
+
+def run_leg_b256(args):
+    """The 256^2 batched comparison alone (for profiling the batched launch)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2305_03284_gb300 import build as _b
+    _b.build()
+    from paper_2305_03284_gb300 import autotune, ddh
+    autotune.apply()
+    peak, _ = measured_peak_gbs()
+    print(json.dumps(batched_256_measure(ddh, peak, args.streams, timesteps=args.steps, warm=args.warmup)))
 
 
 if __name__ == "__main__":

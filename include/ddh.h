@@ -60,13 +60,14 @@ typedef struct ddh_params {
                            -(2/sigma^2) sum_t |v_t| cos(phi_t - angle v_t) + prior by
                            `phase_sweeps` majorised 4-colour ICD sweeps from the tile angles.
                            0 (default): flat prior.  > 0 needs phase_block 2 or 4, n_k = 1,
-                           N <= 256, and steps outside batches and the service */
+                           N <= 256 and the cluster kernel (exec_path); in batches and the
+                           service the streams that use it share one post-step launch */
   int phase_sweeps;     /* ICD sweeps of that M-step, 1..16 (0 counts as the default, 2) */
   int noise_update;     /* 1: sigma^2 (noise_var above is then its starting value) is
                            re-estimated once per frame, after the frame's last EM iteration, by
                            its EM M-step (1/|P|) sum_pupil |y~ - e^{j phi} F mu|^2 + mean(C);
-                           floored at 1e-6.  N <= 256, outside batches and the service, no
-                           adjoint.  0 (default): sigma^2 fixed */
+                           floored at 1e-6.  N <= 256 on the cluster kernel (also in batches
+                           and the service), no adjoint.  0 (default): sigma^2 fixed */
   int exec_path;        /* which kernels run this stream's steps (same method, same readings;
                            results agree within FP32 rounding, not bit for bit):
                            DDH_PATH_DEFAULT (0): the cluster kernel for N <= 256, the L2-staged
@@ -99,6 +100,15 @@ int ddh_default_params(ddh_params *p, int n, float aperture_diam, float snr);
  * bootstrap period of EM iterations; phi carries over.  This fills `p` with those values on
  * top of ddh_default_params. */
 int ddh_static_params(ddh_params *p, int n, float aperture_diam, float snr, int reset_every);
+
+/* The parameter set under which the one-iteration-per-frame loop tracks frozen-flow
+ * turbulence on a bar-chart object at the paper's simulation parameters (Sec. 5.A: D/r0 10,
+ * 0.42 px/frame in x and y, SNR 10 dB), reaching a Strehl ratio of 0.8 within 150 frames as
+ * Sec. 5.C reports: ddh_default_params with the phase on 2 x 2 tiles under the Gaussian MRF
+ * tile prior (phase_block 2, phase_prior 10), q-GGMRF scale sigma_r 0.03 and alpha 0.0125
+ * (Eq. 3; the best value of a grid search over [0, 0.1], the paper's own range, on that
+ * workload; the paper's 0.025 was found on its data). */
+int ddh_tracking_params(ddh_params *p, int n, float aperture_diam, float snr);
 
 /* Validate `p`, allocate the device state (r = 0, phi = 0, n = 0: Fig. 1 first line) and bind
  * it to `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The library owns
@@ -170,10 +180,14 @@ void *ddh_state_stream(const ddh_state *s);
  * the value lands in *out.  Evaluation only, never part of a step. */
 int ddh_strehl(ddh_state *s, const float *phi_true_dev, float *out);
 
-/* Advance `count` states by one frame each: one cluster-per-stream launch per grid size (up to
- * 32 streams per launch), the grid-size groups on concurrent library-owned branches forked
- * from and joined back into the stream of states[0], which all states must share.  Each state
- * appears at most once; frames as for ddh_step. */
+/* Advance `count` states by one frame each: the states are grouped by grid size and path
+ * (exec_path); each cluster-kernel group is one launch per 32 streams (plus one shared
+ * post-step launch for its streams with the tile-phase prior or the sigma^2 M-step), each
+ * staged group one launch sequence per chunk (ddh_set_staged_chunk); the groups run on
+ * concurrent library-owned branches forked from and joined back into the stream of states[0],
+ * which all states must share.  Each state appears at most once; frames as for ddh_step.  A
+ * state's result does not depend on the other states in the batch (no arithmetic crosses
+ * streams). */
 int ddh_step_batch(ddh_state *const *states, const void *const *y_c64_dev, int count);
 
 /* Batched step as a captured CUDA graph.  ddh_batch_create() records one step of every state
@@ -257,7 +271,8 @@ int ddh_step_backward_noalloc(ddh_state *s, const void *y_c64_dev, const float *
  * are queued per sensor; a scheduler (a library thread after ddh_service_start, or each
  * ddh_service_poll call otherwise) resolves finished batches and launches the next queued
  * frame of every sensor that has one, as one ddh_step_batch, without waiting for batches still
- * running (at most `max_in_flight`; when a batch starts is decided by ddh_sched_pick below).  A batch holds at most one frame per sensor; a sensor's
+ * running (at most `max_in_flight`; when a batch starts is decided by ddh_sched_pick
+ * below).  A batch holds at most one frame per sensor; a sensor's
  * next frame may go into a later batch while its previous one still runs, since batches
  * execute in order on the service's stream.  A sensor's results do not depend on which
  * other sensors share its launches.  The paper has a frame loop per sensor

@@ -71,6 +71,7 @@ class DdhError(RuntimeError):
 _SIGS = {
     "ddh_default_params": (c_int, [POINTER(DdhParams), c_int, c_float, c_float]),
     "ddh_static_params": (c_int, [POINTER(DdhParams), c_int, c_float, c_float, c_int]),
+    "ddh_tracking_params": (c_int, [POINTER(DdhParams), c_int, c_float, c_float]),
     "ddh_init": (c_int, [POINTER(c_void_p), POINTER(DdhParams), c_void_p]),
     "ddh_step": (c_int, [c_void_p, c_void_p]),
     "ddh_step_trace": (c_int, [c_void_p, c_void_p, c_void_p]),

@@ -392,23 +392,39 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
       if (lb.count > 0) DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
     } else {
       ddh::StepBatch b{};
+      ddh::PostBatch pb{};  // the chunk's streams with the tile-phase prior or the sigma^2 M-step
       b.ytab = ytab;
       b.count = 0;
+      auto flush = [&]() -> int {
+        DDH_CUDA(ddh::launch_step(n, sched, b, st));
+        if (pb.count > 0) DDH_CUDA(ddh::launch_post_batch(pb, st));
+        b.count = 0;
+        pb.count = 0;
+        return DDH_OK;
+      };
       for (int i = 0; i < count; ++i) {
         ddh_state* s = states[i];
         if (!member(i, gr)) continue;
         if (b.count == 0) b.ytab_base = i;  // ytab rows of one launch must be consecutive
         b.prm[b.count] = s->kp;
         b.fa[b.count] = frame_args(s, ys != nullptr ? ys[i] : nullptr, nullptr);
+        if (s->aux != nullptr && aux_needed(s->prm)) {
+          b.fa[b.count].aux = s->aux;
+          b.fa[b.count].aux_tiles = s->prm.phase_prior > 0.f ? 1 : 0;
+          pb.a[pb.count++] = post_args(s);
+        }
         b.tw = s->tw;
         ++b.count;
         const bool next_same = i + 1 < count && member(i + 1, gr);
         if (b.count == ddh::kMaxBatch || (ytab != nullptr && !next_same)) {
-          DDH_CUDA(ddh::launch_step(n, sched, b, st));
-          b.count = 0;
+          const int rc = flush();
+          if (rc != DDH_OK) return rc;
         }
       }
-      if (b.count > 0) DDH_CUDA(ddh::launch_step(n, sched, b, st));
+      if (b.count > 0) {
+        const int rc = flush();
+        if (rc != DDH_OK) return rc;
+      }
     }
     if (ss != nullptr) {
       DDH_CUDA(cudaEventRecord(ss->join[g], st));
@@ -523,6 +539,16 @@ int ddh_static_params(ddh_params* p, int n, float aperture_diam, float snr, int 
   p->alpha = 1.f;
   p->n_k = reset_every;
   p->tilt_mode = 0;
+  return DDH_OK;
+}
+
+int ddh_tracking_params(ddh_params* p, int n, float aperture_diam, float snr) {
+  const int rc = ddh_default_params(p, n, aperture_diam, snr);
+  if (rc != DDH_OK) return rc;
+  p->phase_block = 2;
+  p->phase_prior = 10.f;
+  p->prior_sigma = 0.03f;
+  p->alpha = 0.0125f;
   return DDH_OK;
 }
 
@@ -752,7 +778,6 @@ static int validate_batch(ddh_state* const* states, int count) {
   if (states == nullptr || count < 0) return DDH_EINVAL;
   for (int i = 0; i < count; ++i) {
     if (states[i] == nullptr) return DDH_EINVAL;
-    if (aux_needed(states[i]->prm)) return DDH_EINVAL;  // the post-step M-steps run per stream only
     if (states[i]->stream != states[0]->stream || states[i]->device != states[0]->device) return DDH_EINVAL;
     for (int j = 0; j < i; ++j)
       if (states[j] == states[i]) return DDH_EINVAL;  // a stream advances once per batch

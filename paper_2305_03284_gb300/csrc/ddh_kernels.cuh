@@ -70,6 +70,12 @@ struct PostArgs {
   int t_lo, nt;               // the pupil tiles lie in [t_lo, t_lo + nt)^2
 };
 
+// The post kernel's arguments of a batch's streams (one 8-CTA cluster each, blockIdx.y).
+struct PostBatch {
+  PostArgs a[kMaxBatch];
+  int count;
+};
+
 struct StepBatch {
   KParams prm[kMaxBatch];
   FrameArgs fa[kMaxBatch];
@@ -137,6 +143,7 @@ cudaError_t launch_fft2(int n, const Fft2Args& a, cudaStream_t st);
 // Post-step kernel (one CTA; programmatic launch): prior-weighted tile-phase M-step and/or
 // the sigma^2 M-step from the step kernel's side outputs.
 cudaError_t launch_post(const PostArgs& a, cudaStream_t st);
+cudaError_t launch_post_batch(const PostBatch& b, cudaStream_t st);
 // One-time per-device function attributes (shared memory size, cluster size); also checks
 // that a cluster of this shape can be resident.  Returns cudaSuccess or the failing error.
 cudaError_t configure(int n, int* max_active_clusters);

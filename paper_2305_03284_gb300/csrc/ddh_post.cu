@@ -1,5 +1,6 @@
 // Post-step kernel of two optional M-step extensions (one cluster of 8 CTAs per stream, after
-// the frame's step kernel on the same stream, programmatic dependent launch).
+// the frame's step kernel on the same stream, programmatic dependent launch; a batch's streams
+// share one launch, blockIdx.y = stream).
 //
 // Phase prior.  The paper names p(phi) in Eq. 2 and leaves its form to earlier work; here the
 // tile phases phi_t (phase constant on G x G tiles) carry a Gaussian MRF on the wrapped
@@ -38,7 +39,8 @@ constexpr int kPostCols = 128;    // the box is at most 128 x 128 tiles (N <= 25
 constexpr int kPostRows = kPostCols / kPostCluster;
 
 __global__ void __cluster_dims__(kPostCluster, 1, 1) __launch_bounds__(kPostThreads)
-    k_ddh_post(const __grid_constant__ PostArgs a) {
+    k_ddh_post(const __grid_constant__ PostBatch b) {
+  const PostArgs& a = b.a[blockIdx.y];
   grid_dep_launch();
   grid_dep_wait();
   float* aux = a.aux;
@@ -171,10 +173,12 @@ __global__ void __cluster_dims__(kPostCluster, 1, 1) __launch_bounds__(kPostThre
 
 }  // namespace
 
-cudaError_t launch_post(const PostArgs& a, cudaStream_t st) {
-  if (a.nt > kPostCols) return cudaErrorInvalidValue;
+cudaError_t launch_post_batch(const PostBatch& b, cudaStream_t st) {
+  if (b.count < 1 || b.count > kMaxBatch) return cudaErrorInvalidValue;
+  for (int i = 0; i < b.count; ++i)
+    if (b.a[i].nt > kPostCols) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kPostCluster, 1, 1);
+  cfg.gridDim = dim3(kPostCluster, b.count, 1);
   cfg.blockDim = dim3(kPostThreads, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
@@ -183,7 +187,14 @@ cudaError_t launch_post(const PostArgs& a, cudaStream_t st) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_ddh_post, a);
+  return cudaLaunchKernelEx(&cfg, k_ddh_post, b);
+}
+
+cudaError_t launch_post(const PostArgs& a, cudaStream_t st) {
+  PostBatch b{};
+  b.a[0] = a;
+  b.count = 1;
+  return launch_post_batch(b, st);
 }
 
 }  // namespace ddh

@@ -277,7 +277,6 @@ size_t ddh_state_bytes(int n) {
 
 int ddh_service_admit(ddh_service* s, int sensor_id, const ddh_params* p) {
   if (s == nullptr || p == nullptr) return DDH_EINVAL;
-  if (p->phase_prior > 0.f || p->noise_update) return DDH_EINVAL;  // per-stream post-step M-steps
   const size_t need = ddh_internal_state_bytes(p);
   if (need == 0) return DDH_EINVAL;
   std::lock_guard<std::mutex> lock(s->mu);

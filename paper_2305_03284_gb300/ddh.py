@@ -38,6 +38,19 @@ def static_params(n: int, aperture_diam: float, snr: float, reset_every: int = 2
     return p
 
 
+def tracking_params(n: int, aperture_diam: float, snr: float, /, **overrides) -> DdhParams:
+    """``ddh_tracking_params`` (2 x 2 phase tiles under the tile prior, sigma_r 0.03, alpha
+    0.0125: the set under which the loop tracks frozen-flow turbulence on a bar-chart object at
+    the paper's parameters) plus keyword overrides."""
+    p = DdhParams()
+    check(lib().ddh_tracking_params(byref(p), int(n), float(aperture_diam), float(snr)))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
 def _stream_handle(stream) -> c_void_p:
     if stream is None:
         stream = torch.cuda.current_stream()

@@ -3,11 +3,14 @@
 This module only *produces inputs*: it holds none of the EM method's arithmetic and is
 imported by both the FP64 oracle tests and the GPU path's tests/benchmarks, never by either
 implementation.  It stands in for the paper's simulation (Sec. 5.A), whose reflectance (the
-1951 USAF chart) is replaced by a seeded smooth random field:
+1951 USAF chart) is replaced by a seeded smooth random field or a seeded bar chart:
 
 * reflectance ``r_true``: the image plane is zero-padded 2x, so the object occupies the central
   ``N/2 x N/2`` block: a periodic Gaussian filter (sigma = 3 px) of U[0, 1] noise on that block,
-  rescaled to [0, 1], and zero elsewhere;
+  rescaled to [0, 1], and zero elsewhere (``obj="smooth"``); or (``obj="bars"``) a seeded bar
+  chart on that block, the structure of the paper's resolution-chart object: ``bars`` bright
+  rectangles (reflectance 1; widths 2 to N/32 px, lengths N/20 to N/6 px, horizontal or
+  vertical at seeded positions) on a dark (0) background;
 * phase: a Kolmogorov screen made by the spectral (FFT) method on an ``L x L`` periodic grid,
   phase PSD ``0.023 r0^(-5/3) f^(-11/3)`` (f in cycles/px, r0 in px), structure function
   ``6.88 (rho/r0)^(5/3)``;
@@ -64,6 +67,9 @@ class StreamConfig:
     stream_id: int = 0
     refl_sigma_px: float = 3.0
     rate_khz: float = 0.0       # frame arrival rate (streaming-service workload only)
+    obj: str = "smooth"         # reflectance: "smooth" random field or "bars" (a bar chart)
+    bars: int = 16              # bright bars of the "bars" object
+    obj_seed: int | None = None # seed of the object; None: the stream's static seed
 
 
 def config_single_64(frames: int = 20) -> StreamConfig:
@@ -118,6 +124,17 @@ def config_service(sensors: int = 32, frames_total: int = 10_000) -> list[Stream
     return out
 
 
+def config_paper_256(sim: int = 0, frames: int = 150) -> StreamConfig:
+    """The paper's simulation parameters (Sec. 5.A): N = 256, D/r0 = 10, frozen flow
+    v = (0.421, 0.421) px/frame (down and to the right), SNR 10 dB (linear 10), the pupil of
+    diameter N/2 on the 2x zero-padded grid, and a bar-chart object standing in for the 1951
+    USAF chart (one chart for every simulation; `sim` seeds the turbulence, speckle and noise)."""
+    vx, vy = paper_velocity()
+    return StreamConfig(n=256, aperture_diam=128.0, d_over_r0=10.0, wind=math.hypot(vx, vy),
+                        wind_angle=math.atan2(vy, vx), snr=10.0, frames=frames, config_id=7, stream_id=sim,
+                        obj="bars", bars=16, obj_seed=7_000)
+
+
 def velocity_magnitude(f_g: float, f_s: float, n: int, d_over_r0: float) -> float:
     """Frozen-flow displacement per sample in px (Sec. 5.A, scaled Tyson Eq. 4.15)."""
     return (1.0 / 0.43) * (f_g / f_s) * (n / d_over_r0)
@@ -128,6 +145,23 @@ def paper_velocity() -> tuple[float, float]:
     flowing down and to the right: equal x and y components."""
     m = velocity_magnitude(100.0, 10_000.0, 256, 10.0)
     return (m / math.sqrt(2.0), m / math.sqrt(2.0))
+
+
+def _bar_chart(m: int, bars: int, seed) -> np.ndarray:
+    """An m x m bar chart: `bars` bright (1) rectangles on a dark (0) background, each of width
+    2 .. m/16 px and length m/10 .. m/3 px, horizontal or vertical, at seeded positions."""
+    rng = seed if isinstance(seed, np.random.Generator) else np.random.default_rng(np.random.SeedSequence([seed]))
+    r = np.zeros((m, m))
+    for _ in range(bars):
+        w = int(rng.integers(2, max(3, m // 16)))
+        h = int(rng.integers(m // 10, m // 3))
+        x0 = int(rng.integers(0, m - w))
+        y0 = int(rng.integers(0, m - h))
+        if rng.random() < 0.5:
+            r[y0:y0 + h, x0:x0 + w] = 1.0
+        else:
+            r[x0:x0 + w, y0:y0 + h] = 1.0
+    return r
 
 
 def _pupil(n: int, diam: float) -> np.ndarray:
@@ -158,7 +192,11 @@ class Stream:
         g = np.exp(-2.0 * math.pi ** 2 * cfg.refl_sigma_px ** 2 * (f[:, None] ** 2 + f[None, :] ** 2))
         sm = np.real(np.fft.ifft2(np.fft.fft2(u) * g))
         self.r_true = np.zeros((n, n))
-        self.r_true[n // 4: n // 4 + m, n // 4: n // 4 + m] = (sm - sm.min()) / (sm.max() - sm.min())
+        if cfg.obj == "bars":
+            self.r_true[n // 4: n // 4 + m, n // 4: n // 4 + m] = _bar_chart(m, cfg.bars, cfg.obj_seed
+                                                                            if cfg.obj_seed is not None else rng)
+        else:
+            self.r_true[n // 4: n // 4 + m, n // 4: n // 4 + m] = (sm - sm.min()) / (sm.max() - sm.min())
         self.pupil = _pupil(n, cfg.aperture_diam)
         self.noise_var_raw = float(self.r_true.mean() / cfg.snr)
         angle = cfg.wind_angle if cfg.wind_angle is not None else float(rng.uniform(0, 2 * math.pi))

@@ -141,6 +141,20 @@ def test_config4_sixteen_streams_256(mods):
         (torch.cos(phiK).sum() + rK.sum()).backward()
         for t in (sig.grad, pp.grad, s2.grad, r0.grad, phi0.grad):
             assert torch.isfinite(t).all()
+        if cfg.stream_id == 0:
+            # the first stream against the FP64 oracle gradient at full size (same loss)
+            prm = _oracle_params(p)
+            a = o.aperture(256, cfg.aperture_diam)
+            st = o.init_state(256)
+            for y in ys:
+                st, _ = o.step(st, y, prm)
+            rb, pb, g, _ = adj.unrolled_grad(np.zeros((256, 256)), np.zeros((256, 256)), ys, prm,
+                                             np.ones((256, 256)), a * -np.sin(st.phi))
+            gpu = np.array([sig.grad.item(), pp.grad.item(), s2.grad.item()])
+            eg = np.abs(gpu - g) / np.abs(g)
+            er, ep = _rel(r0.grad.cpu().numpy(), rb), _rel(phi0.grad.cpu().numpy() * a, pb * a)
+            print(f"256^2 K=8 stream 0: grads rel {eg}, r0 {er:.2e}, phi0 {ep:.2e}")
+            assert np.all(eg < TOL_UNROLLED) and er < TOL_UNROLLED and ep < TOL_UNROLLED, (eg, er, ep)
 
 
 def test_unrolled_calls_equal_per_frame_calls(mods):

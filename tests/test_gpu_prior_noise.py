@@ -137,23 +137,66 @@ def test_checkpoint_carries_the_sigma2_estimate(ddh):
 
 
 def test_refused_where_unsupported(ddh):
-    """Batches, the service and the adjoint refuse the post-step M-steps; so do a prior
-    without tiles, with n_k > 1, or on the 512^2 path."""
+    """The adjoint refuses the post-step M-steps; so do a prior without tiles, with n_k > 1, on
+    the 512^2 path or on the staged kernels."""
     cfg = sy.config_single_64()
     st, ys, ph, p = make(ddh, cfg, 1, noise_update=1)
-    s = ddh.Stream(p)
-    with pytest.raises(ddh.DdhError):
-        ddh.step_batch([s], [cu(ys[0])])
     for over in ({"phase_prior": 1.0}, {"phase_prior": 1.0, "phase_block": 2, "n_k": 2},
                  {"phase_sweeps": 17}, {"noise_update": 2}, {"phase_prior": -1.0}):
         with pytest.raises(ddh.DdhError):
             ddh.Stream(ddh.default_params(64, 32.0, 10.0, **over))
     with pytest.raises(ddh.DdhError):
         ddh.Stream(ddh.default_params(512, 256.0, 10.0, noise_update=1))
+    with pytest.raises(ddh.DdhError):
+        ddh.Stream(ddh.default_params(256, 128.0, 10.0, phase_block=2, phase_prior=5.0, exec_path=2))
+    s = ddh.Stream(p)
+    L = ddh.lib()
+    z = torch.zeros((64, 64), device="cuda")
+    tr = torch.zeros(L.ddh_trace_floats(64), device="cuda")
+    g = torch.zeros(3, device="cuda")
+    y = cu(ys[0])
+    args = [s._h] + [ddh.c_void_p(t.data_ptr()) for t in (y, z, z, tr, z, z, z, z, z, g)]
+    assert L.ddh_step_backward_noalloc(*args) == -1
+
+
+def test_batches_and_service_equal_solo_steps_with_the_post_step_m_steps(ddh):
+    """Streams with the tile-phase prior and/or the sigma^2 M-step inside a batch (mixed with
+    plain streams and grid sizes), in a captured graph and in the service: every stream's phi,
+    r and sigma^2 equal its solo run bit for bit."""
     from paper_2305_03284_gb300 import serve
-    svc = serve.NativeService()
-    try:
-        with pytest.raises(ddh.DdhError):
-            svc.admit(0, ddh.default_params(64, 32.0, 10.0, noise_update=1))
-    finally:
-        svc.close()
+    cfgs = [sy.config_single_64(), sy.config_single_256(6), sy.config_batched(6)[0], sy.config_single_64()]
+    overs = [{"phase_block": 2, "phase_prior": 20.0, "noise_update": 1},
+             {"phase_block": 2, "phase_prior": 10.0},
+             {"noise_update": 1},
+             {}]
+    data = [make(ddh, c, 6, **o_) for c, o_ in zip(cfgs, overs)]
+    solo = [ddh.Stream(d[3]) for d in data]
+    for f in range(6):
+        for s_, d in zip(solo, data):
+            s_.step(cu(d[1][f]))
+    batch = [ddh.Stream(d[3]) for d in data]
+    graph = [ddh.Stream(d[3]) for d in data]
+    g = ddh.BatchGraph(graph)
+    for f in range(6):
+        ys = [cu(d[1][f]) for d in data]
+        ddh.step_batch(batch, ys)
+        g.run(ys)
+    torch.cuda.synchronize()
+    for k, s1 in enumerate(solo):
+        for s2 in (batch[k], graph[k]):
+            assert torch.equal(s1.phase(), s2.phase()), k
+            assert torch.equal(s1.reflectance(), s2.reflectance()), k
+            assert s1.noise_estimate() == s2.noise_estimate(), k
+    g.close()
+    svc = serve.NativeService(mem_budget_bytes=1 << 34)
+    for i, d in enumerate(data):
+        svc.admit(i, d[3])
+    frames = [cu(d[1]) for d in data]
+    rng = np.random.default_rng(9)
+    arrivals = sorted((float(t), i, frames[i][k]) for i in range(len(data))
+                      for k, t in enumerate(np.cumsum(rng.exponential(1e-4, 6))))
+    assert len(svc.drive(arrivals)) == 24
+    for k, s1 in enumerate(solo):
+        assert torch.equal(s1.phase(), svc.phase(k)), k
+        assert torch.equal(s1.reflectance(), svc.reflectance(k)), k
+    svc.close()

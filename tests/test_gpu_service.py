@@ -22,62 +22,57 @@ def _sensors():
     return [sy.config_single_256(6), b[0], b[40], sy.config_single_64(6), b[1], b[41]]
 
 
-def test_result_alone_equals_result_in_mix(mods):
-    ddh, serve = mods
-    cfgs = _sensors()
-    frames = [torch.from_numpy(sy.Stream(c).frames(6)[0]).cuda() for c in cfgs]
-    params = [ddh.default_params(c.n, c.aperture_diam, c.snr) for c in cfgs]
-    alone = serve.Service(mem_budget_bytes=1 << 34)
-    alone.admit("x", params[0])
-    for f in range(6):
-        alone.submit("x", frames[0][f])
-    alone.drain()
-    mix = serve.Service(mem_budget_bytes=1 << 34)
-    for i, p in enumerate(params):
-        mix.admit(i, p)
-    rng = np.random.default_rng(0)
-    arrivals = sorted((float(t), i, frames[i][k]) for i in range(len(cfgs))
-                      for k, t in enumerate(np.cumsum(rng.exponential(2e-4, 6))))
-    res = mix.drive(arrivals)
-    assert len(res) == 36
-    assert max(mix.batch_sizes) > 1
-    a, m = alone.state("x"), mix.state(0)
-    assert torch.equal(a.phase(), m.phase()) and torch.equal(a.reflectance(), m.reflectance())
-    assert m.frame_index == 6
-
-
-def test_admission_against_memory_budget(mods):
-    ddh, serve = mods
-    p256 = ddh.default_params(256, 128.0, 5.0)
-    be = serve.LibddhBackend()
-    need = be.state_bytes(p256)
-    svc = serve.Service(backend=be, mem_budget_bytes=2 * need + 10)
-    svc.admit("a", p256)
-    svc.admit("b", p256)
-    with pytest.raises(serve.AdmissionError):
-        svc.admit("c", p256)
-    svc.release("a")
-    svc.admit("c", p256)
-    assert svc.used_bytes == 2 * need
-
-
-def test_background_loop_and_phase_delivery(mods):
+def test_native_background_loop_delivers_in_order(mods):
+    """Frames submitted while the library thread runs complete in order, and the sensor's
+    phase then equals a plain stream's after the same frames."""
     ddh, serve = mods
     cfg = sy.config_single_64(4)
     frames = torch.from_numpy(sy.Stream(cfg).frames(4)[0]).cuda()
-    svc = serve.Service(mem_budget_bytes=1 << 32)
-    svc.admit("s", ddh.default_params(64, 32.0, 10.0))
+    svc = serve.NativeService(mem_budget_bytes=1 << 32)
+    svc.admit(7, ddh.default_params(64, 32.0, 10.0))
     ref = ddh.Stream(ddh.default_params(64, 32.0, 10.0))
     svc.start()
+    done = []
     try:
-        futs = [svc.submit("s", frames[k]) for k in range(4)]
-        res = [f.result(timeout=30) for f in futs]
+        for k in range(4):
+            svc.submit(7, frames[k], tag=k)
+        t0 = svc.now()
+        while len(done) < 4 and svc.now() - t0 < 30:
+            done.extend(svc.poll())
     finally:
         svc.stop()
     for k in range(4):
         ref.step(frames[k])
-    assert [r.frame_index for r in res] == [1, 2, 3, 4]
-    assert torch.equal(res[-1].phase, ref.phase())
+    assert [c[0] for c in done] == [0, 1, 2, 3] and [c[2] for c in done] == [1, 2, 3, 4]
+    assert torch.equal(svc.phase(7), ref.phase())
+    svc.close()
+
+
+def test_native_staged_sensors_alone_equal_in_mix(mods):
+    """Sensors on the staged kernels (exec_path 2) mixed with cluster-path sensors: each
+    result equals the same sensor served alone, under both policies."""
+    ddh, serve = mods
+    b = sy.config_batched(5)
+    cfgs = [sy.config_single_256(5), b[1], sy.config_single_256(5), b[2]]
+    paths = [2, 2, 1, 1]
+    frames = [torch.from_numpy(sy.Stream(c).frames(5)[0]).cuda() for c in cfgs]
+    params = [ddh.default_params(c.n, c.aperture_diam, c.snr, exec_path=pa) for c, pa in zip(cfgs, paths)]
+    alone = serve.NativeService(mem_budget_bytes=1 << 34)
+    alone.admit(0, params[0])
+    alone.drive([(0.0, 0, frames[0][k]) for k in range(5)])
+    rng = np.random.default_rng(2)
+    arrivals = sorted((float(t), i, frames[i][k]) for i in range(len(cfgs))
+                      for k, t in enumerate(np.cumsum(rng.exponential(1e-4, 5))))
+    for flags in (0, 3):
+        mix = serve.NativeService(mem_budget_bytes=1 << 34)
+        mix.set_policy(flags)
+        for i, p in enumerate(params):
+            mix.admit(i, p)
+        res = mix.drive(arrivals)
+        assert len(res) == 20
+        assert torch.equal(alone.phase(0), mix.phase(0)) and torch.equal(alone.reflectance(0), mix.reflectance(0))
+        mix.close()
+    alone.close()
 
 
 # ------------------------------------------------------------------ native scheduler
