@@ -35,6 +35,8 @@ WORKLOAD = ("single stream 256x256 grid, 128 px pupil, D/r0 15, 1 px/frame froze
             "1 EM iteration per frame")
 PROFILE = os.path.join(ROOT, "profiles", "k_ddh_step_256_single_stream.md")
 KERNEL_SOURCES = ["ddh_step.cu", "ddh_device.cuh", "ddh_kernels.cuh"]
+PROFILE_STAGED = os.path.join(ROOT, "profiles", "k_l2_step_256_batch32.md")
+KERNEL_SOURCES_STAGED = ["ddh_step_l2.cu", "ddh_device.cuh", "ddh_kernels.cuh"]
 
 
 def parse_args():
@@ -103,24 +105,24 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def kernel_source_sha():
+def kernel_source_sha(sources=None):
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2305_03284_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_value(key):
-    """A per-launch figure (`key: value`) from the committed ncu summary, if it was taken on
+def profiled_value(key, profile=PROFILE, sources=None):
+    """A per-launch figure (`key: value`) from a committed ncu summary, if it was taken on
     this kernel source; None otherwise."""
     try:
-        txt = open(PROFILE).read()
+        txt = open(profile).read()
     except OSError:
         return None
     m = re.search(key + r":\s*([0-9.eE+]+)", txt)
     s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
-    if not m or not s or s.group(1) != kernel_source_sha():
+    if not m or not s or s.group(1) != kernel_source_sha(sources):
         return None
     return float(m.group(1))
 
@@ -136,13 +138,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 ISSUE_PEAK_WIPS = 152 * 4 * 2.07e9
 
 
-def issue_bound(frames_per_s, inst_per_frame=None):
+def issue_bound(frames_per_s, inst_per_frame):
     """The instruction-issue ceiling of the step kernel: warp instructions per frame (ncu, from
     the committed summary when it was taken on this kernel source) times frames/s, against the
     whole GPU's nominal issue rate; `max_frames_per_s` is the rate at which every scheduler of
     every SM would issue one of these instructions each cycle."""
-    if inst_per_frame is None:
-        inst_per_frame = profiled_value("warp_inst_per_launch")
     if inst_per_frame is None:
         return None
     achieved = inst_per_frame * frames_per_s
@@ -414,13 +414,17 @@ def batched_256_measure(ddh, peak_gbs, streams, timesteps=200, ring=8, warm=5):
             else:
                 sts = [ddh.Stream(prm, stream=main) for _ in range(streams)]
             hs = [s._h for s in sts]
+            hs_arr = (ddh.c_void_p * streams)(*hs)
             g = ddh.BatchGraph(sts) if kind == "graph" else None
             ev_start = torch.cuda.Event(enable_timing=True)
             fork = torch.cuda.Event()
 
             def one(t, per_frame_events=None):
-                if g is not None:
-                    g.run_ptrs(arrs[t % ring])
+                if g is not None or kind == "batch":
+                    if g is not None:
+                        g.run_ptrs(arrs[t % ring])
+                    else:
+                        ddh.check(lib.ddh_step_batch(hs_arr, arrs[t % ring], streams))
                     if per_frame_events is not None:
                         per_frame_events[0].record(main)
                     return
@@ -457,7 +461,8 @@ def batched_256_measure(ddh, peak_gbs, streams, timesteps=200, ring=8, warm=5):
                 ev_start.record(main)
                 one(t, evs)
                 torch.cuda.synchronize()
-                lat.extend(ev_start.elapsed_time(evs[i if g is None else 0]) * 1e3 for i in range(streams))
+                lat.extend(ev_start.elapsed_time(evs[i if kind in ("plain", "plain_streams") else 0]) * 1e3
+                           for i in range(streams))
             for s in sts:
                 s.sync()
             if g is not None:
@@ -471,13 +476,18 @@ def batched_256_measure(ddh, peak_gbs, streams, timesteps=200, ring=8, warm=5):
                 "frame_latency_us_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                 "hbm_gbs_algorithmic": BYTES_PER_PX * px / per_step_s / 1e9,
                 "hbm_frac": BYTES_PER_PX * px / per_step_s / 1e9 / peak_gbs,
-                "launches_per_timestep": streams if g is None else "1 graph",
+                "launches_per_timestep": {"graph": "1 graph", "batch": "one ddh_step_batch call"}.get(kind, streams),
                 "exec_path": {1: "cluster", 2: "staged"}[path]}
     out["plain"] = measure("plain")
     out["plain_streams"] = measure("plain_streams")
     out["graph_cluster"] = measure("graph", 1)
     out["graph_staged"] = measure("graph", 2)
+    out["batch_call_staged"] = measure("batch", 2)
     out["graph"] = dict(out["graph_staged" if autotune.recommend_path(256, streams) == 2 else "graph_cluster"])
+    inst = {"cluster": profiled_value("warp_inst_per_launch"),
+            "staged": profiled_value("warp_inst_per_frame", PROFILE_STAGED, KERNEL_SOURCES_STAGED)}
+    for k in ("graph_cluster", "graph_staged", "batch_call_staged", "graph"):
+        out[k]["roofline_issue"] = issue_bound(out[k]["frames_per_s"], inst[out[k]["exec_path"]])
     out["graph_over_plain_frames_per_s"] = out["graph"]["frames_per_s"] / out["plain"]["frames_per_s"]
     out["graph_over_plain_streams_frames_per_s"] = (out["graph"]["frames_per_s"]
                                                     / out["plain_streams"]["frames_per_s"])
@@ -526,7 +536,9 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=N
         for i, c in enumerate(cfgs):
             # the per-frame comparison runs the plain path (the library's default kernels)
             svc.admit(i, ddh.default_params(c.n, c.aperture_diam, c.snr, exec_path=0 if per_frame else paths[c.n]))
-        svc.drive([(0.0, i, rings[i][0]) for i in range(len(cfgs))])  # warm-up frame each
+        # warm-up: 20 frames per sensor queued at once (the GPU leaves its idle clocks and every
+        # kernel of the mix is loaded before the trace starts)
+        svc.drive([(0.0, i, rings[i][k % ring]) for k in range(20) for i in range(len(cfgs))])
         st0 = svc.stats()
         res = svc.drive(trace)
         st1 = svc.stats()
@@ -826,7 +838,7 @@ def run_ours(args):
                      "traffic": profiled_traffic(), "kernel": "k_ddh_step<256>",
                      "bytes_per_launch": bytes_per_launch, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
         "roofline_fp32": fp32_cobound(avg_launch_s),
-        "roofline_issue": issue_bound(value),
+        "roofline_issue": issue_bound(value, profiled_value("warp_inst_per_launch")),
         "e2e": {"value": ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": n * n * 4,
                 "steps": ke},
         "static_mode": static,

@@ -116,7 +116,13 @@ class NativeService:
 
     def drive(self, arrivals, timeout_s: float = 120.0) -> list:
         """Replay ``arrivals`` = sorted ``(t_seconds, sensor, frame)`` on the library thread;
-        returns completions (tag = index into ``arrivals``)."""
+        returns completions (tag = index into ``arrivals``).  The replaying Python loop runs
+        with the garbage collector paused: a collection pass over a large heap stops this
+        thread for tens of milliseconds, which would delay submissions past their scheduled
+        arrival times and be counted as service latency."""
+        import gc
+        gc_was_on = gc.isenabled()
+        gc.disable()
         self.start()
         done = []
         try:
@@ -135,6 +141,8 @@ class NativeService:
                     raise TimeoutError("service did not finish the trace")
         finally:
             self.stop()
+            if gc_was_on:
+                gc.enable()
         return done
 
     def close(self) -> None:
