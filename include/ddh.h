@@ -340,13 +340,24 @@ int ddh_fft_schedule_count(int n);
 int ddh_set_fft_schedule(int n, int schedule);
 int ddh_get_fft_schedule(int n);
 /* Streams per launch chunk of the L2-staged kernels for grid size n (128, 256, 512) on the
- * current device, 1..32 (default 16): a batch's staged streams of one size run as consecutive
+ * current device, 1..64 (default 16): a batch's staged streams of one size run as consecutive
  * launch sequences of this many streams, so that one chunk's working images (about 2.6 MB per
  * 256^2 stream, 10 MB per 512^2 stream) stay in L2 between its stages.  Affects later launches
  * and later ddh_batch_create; results do not depend on it (every stream's arithmetic is its
  * own).  The autotuner's knob. */
 int ddh_set_staged_chunk(int n, int chunk);
 int ddh_get_staged_chunk(int n);
+/* on = 1: on the current device, every later batched step (ddh_step_batch, ddh_batch_create)
+ * runs all its L2-staged streams -- of every staged grid size -- as one persistent cooperative
+ * launch per step (or a few, when more than 64 streams, differing n_k or, with a graph, streams
+ * interleaved with cluster-kernel streams split it): the grid's blocks take the stages' work
+ * items (stream, block) in turn, with a grid-wide barrier between stages.  Results are bit for
+ * bit those of the chained launches (on = 0, the default; the autotuner picks).  A barrier wait
+ * is bounded (200 ms of device time); if one expires, every stream of that launch reports
+ * DDH_ETIMEOUT and its state is left part-way through the step (restore it from a checkpoint).
+ * Single-stream steps always use the chained launches. */
+int ddh_set_staged_persistent(int on);
+int ddh_get_staged_persistent(void);
 
 /* Unitary 2D DFT (Sec. 2, F) or its inverse (inverse != 0) of one N x N complex64 image,
  * device in/out (may alias), on `cuda_stream`.  N = 32 ... 256. */

@@ -122,6 +122,8 @@ _SIGS = {
     "ddh_get_fft_schedule": (c_int, [c_int]),
     "ddh_set_staged_chunk": (c_int, [c_int, c_int]),
     "ddh_get_staged_chunk": (c_int, [c_int]),
+    "ddh_set_staged_persistent": (c_int, [c_int]),
+    "ddh_get_staged_persistent": (c_int, []),
     "ddh_fft2": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p]),
     "ddh_sync": (c_int, [c_void_p]),
     "ddh_checkpoint_bytes": (c_size_t, [c_int]),

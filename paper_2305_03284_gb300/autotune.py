@@ -8,7 +8,10 @@ Knobs, per grid size N:
 * which kernels a batch of B streams of size N should run on (``exec_path``): the cluster
   kernel (one thread-block cluster per stream; at most 7 resident 16-CTA clusters at 256^2, so
   112 of the 152 SMs) or the staged kernels (every stage spread over all SMs), timed at
-  several batch sizes; ``recommend_path(n, streams)`` reads the result.
+  several batch sizes; ``recommend_path(n, streams)`` reads the result;
+* whether a batch's staged streams run as chained stage launches or as one persistent launch
+  per step (``ddh_set_staged_persistent``), timed on the 64-stream mix of 128^2, 256^2 and
+  512^2 streams all on the staged kernels, and on 32 streams of 256^2.
 
 Each candidate is timed on seeded synthetic frames with CUDA events, one batched step per time
 step, after warm-up.  The table (``{"<n>": {...}}``) is committed as ``tuning_gb300.json``;
@@ -69,7 +72,8 @@ def time_batch(n: int, streams: int, path: int = DDH_PATH_DEFAULT, frames: int =
 
 
 def tune(path: str | None = DEFAULT_TABLE, sizes=(64, 128, 256, 512), batch_sizes=(1, 2, 4, 7, 8, 16, 32, 64),
-         big: dict | None = None, chunks=(4, 8, 16, 32), schedule_streams: dict | None = None) -> dict:
+         big: dict | None = None, chunks=(4, 8, 16, 32), schedule_streams: dict | None = None,
+         persistent_mix: bool = True) -> dict:
     """Time every knob; `big` gives the batch size (per N) the staged chunk is tuned at and
     `schedule_streams` the batch the FFT schedules are compared at (as many clusters as can
     be resident).  Leaves the winners selected in the library."""
@@ -111,10 +115,49 @@ def tune(path: str | None = DEFAULT_TABLE, sizes=(64, 128, 256, 512), batch_size
                     break
             row["staged_from_streams"] = start
         table[str(n)] = row
+    if persistent_mix:
+        table["persistent"] = tune_persistent()
     if path:
         with open(path, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
     return table
+
+
+def time_mixed(sizes, persistent: int, frames: int = 4, reps: int = 30) -> float:
+    """Microseconds per time step of a captured-graph batch of staged streams of the given grid
+    sizes, with the persistent launch on or off."""
+    check(lib().ddh_set_staged_persistent(int(persistent)))
+    cuda_stream = torch.cuda.Stream()
+    rings = {n: _frames(n, 4, frames) for n in set(sizes)}
+    with torch.cuda.stream(cuda_stream):
+        sts = [ddh.Stream(ddh.default_params(n, n / 2, 10.0, exec_path=DDH_PATH_STAGED), stream=cuda_stream)
+               for n in sizes]
+        g = ddh.BatchGraph(sts)
+        ys = lambda t: [rings[n][i % 4][t % frames] for i, n in enumerate(sizes)]
+        for t in range(3):
+            g.run(ys(t))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cuda_stream)
+        for t in range(reps):
+            g.run(ys(t))
+        e1.record(cuda_stream)
+        e1.synchronize()
+        g.close()
+        for s in sts:
+            s.sync()
+            s.close()
+    return e0.elapsed_time(e1) * 1e3 / reps
+
+
+def tune_persistent() -> dict:
+    mix = [128] * 32 + [256] * 24 + [512] * 8
+    out = {}
+    for name, sizes in (("mix64", mix), ("256x32", [256] * 32)):
+        out[name] = {"chained_us_per_step": time_mixed(sizes, 0), "persistent_us_per_step": time_mixed(sizes, 1)}
+    # persistent only where it wins on both workloads
+    out["persistent"] = int(all(v["persistent_us_per_step"] < v["chained_us_per_step"] for v in out.values()))
+    check(lib().ddh_set_staged_persistent(out["persistent"]))
+    return out
 
 
 def _load(table):
@@ -131,6 +174,9 @@ def apply(table: dict | str | None = DEFAULT_TABLE) -> dict:
     on the current device."""
     table = _load(table)
     for n, row in table.items():
+        if n == "persistent":
+            check(lib().ddh_set_staged_persistent(int(row.get("persistent", 0))))
+            continue
         if "schedule" in row:
             ddh.set_fft_schedule(int(n), int(row["schedule"]))
         if "staged_chunk" in row:

@@ -87,6 +87,8 @@ float2* g_twiddle[kMaxDevices][5] = {};
 int g_schedule[kMaxDevices][5] = {};  // FFT radix schedule used for each grid size
 // streams per launch chunk of the L2-staged kernels, per grid size (0: the default, 16)
 int g_chunk[kMaxDevices][5] = {};
+// 1: a batch's staged streams run as one persistent launch per step (ddh_set_staged_persistent)
+int g_persistent[kMaxDevices] = {};
 int staged_chunk(int dev, int n) {
   const int c = g_chunk[dev][n_slot(n)];
   return c > 0 ? c : 16;
@@ -270,6 +272,8 @@ int check_status(ddh_state* s) {
   DDH_CUDA(cudaStreamSynchronize(s->stream));
   if (h == 0) return DDH_OK;
   DDH_CUDA(cudaMemsetAsync(s->status, 0, sizeof(unsigned), s->stream));
+  if ((h & ddh::kStatusTimeout) && s->staged)  // an abandoned persistent launch: fresh barrier words
+    DDH_CUDA(cudaMemsetAsync(ddh::l2_stream_view(s->l2scratch, s->prm.n).bar, 0, 3 * sizeof(unsigned), s->stream));
   DDH_CUDA(cudaStreamSynchronize(s->stream));
   if (h & ddh::kStatusTimeout) return DDH_ETIMEOUT;
   return DDH_ENONFINITE;
@@ -345,10 +349,20 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
   const Group order[kGroups] = {{512, true}, {256, true}, {128, true}, {32, false},
                                 {64, false}, {128, false}, {256, false}};
   auto member = [&](int i, const Group& gr) { return states[i]->prm.n == gr.n && states[i]->staged == gr.staged; };
+  const bool persist = g_persistent[dev] != 0;
   int groups = 0;
+  bool any_staged = false;
   for (const Group& gr : order)
     for (int i = 0; i < count; ++i)
-      if (member(i, gr)) { ++groups; break; }
+      if (member(i, gr)) {
+        if (gr.staged && persist) {
+          if (!any_staged) ++groups;  // every staged stream shares the persistent branch
+          any_staged = true;
+        } else {
+          ++groups;
+        }
+        break;
+      }
   SideStreams* ss = nullptr;
   if (groups > 1) {
     int rc = side_streams(dev, &ss);
@@ -356,7 +370,60 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
     DDH_CUDA(cudaEventRecord(ss->fork, main));
   }
   int g = 0;
+  if (persist && any_staged) {
+    cudaStream_t st = main;
+    if (ss != nullptr) {
+      st = ss->s[g];
+      DDH_CUDA(cudaStreamWaitEvent(st, ss->fork, 0));
+    }
+    // the staged streams in runs of one grid size, as few persistent launches as the launch
+    // limits allow (one when they are consecutive, share n_k and number at most 64)
+    ddh::L2Persist lp{};
+    auto flush = [&]() -> int {
+      if (lp.b.count == 0) return DDH_OK;
+      lp.bar = lp.b.st[0].bar;
+      DDH_CUDA(ddh::launch_step_l2_persistent(lp, st));
+      lp = ddh::L2Persist{};
+      return DDH_OK;
+    };
+    int prev = -2;
+    for (int i = 0; i < count; ++i) {
+      ddh_state* s = states[i];
+      if (!s->staged) continue;
+      if (lp.b.count > 0 && (s->kp.n_k != lp.n_k || lp.b.count == ddh::kMaxBatchL2 ||
+                             (ytab != nullptr && prev != i - 1) ||
+                             (lp.n[lp.groups - 1] != s->prm.n && lp.groups == ddh::kPersistGroups))) {
+        const int rc = flush();
+        if (rc != DDH_OK) return rc;
+      }
+      if (lp.b.count == 0) {
+        lp.b.ytab = ytab;
+        lp.b.ytab_base = i;
+        lp.n_k = s->kp.n_k;
+      }
+      if (lp.groups == 0 || lp.n[lp.groups - 1] != s->prm.n) {
+        lp.first[lp.groups] = lp.b.count;
+        lp.count[lp.groups] = 0;
+        lp.n[lp.groups] = s->prm.n;
+        lp.tw[lp.groups] = s->tw;
+        ++lp.groups;
+      }
+      lp.b.prm[lp.b.count] = s->kp;
+      lp.b.st[lp.b.count] = l2_view(s, ys != nullptr ? ys[i] : nullptr);
+      ++lp.b.count;
+      ++lp.count[lp.groups - 1];
+      prev = i;
+    }
+    const int rc = flush();
+    if (rc != DDH_OK) return rc;
+    if (ss != nullptr) {
+      DDH_CUDA(cudaEventRecord(ss->join[g], st));
+      DDH_CUDA(cudaStreamWaitEvent(main, ss->join[g], 0));
+    }
+    ++g;
+  }
   for (const Group& gr : order) {
+    if (persist && gr.staged) continue;
     const int n = gr.n;
     int members = 0;
     for (int i = 0; i < count; ++i) members += member(i, gr) ? 1 : 0;
@@ -578,6 +645,8 @@ int ddh_init(ddh_state** out, const ddh_params* p, void* cuda_stream) {
   if (e == cudaSuccess) e = cudaMalloc(&s->ystage, 2 * img);
   if (e == cudaSuccess) e = cudaMalloc(&s->scalar, 256);
   if (e == cudaSuccess && staged) e = cudaMalloc(&s->l2scratch, ddh::l2_scratch_bytes(p->n));
+  if (e == cudaSuccess && staged)  // the frame flag and the grid-barrier words start at zero
+    e = cudaMemsetAsync(ddh::l2_stream_view(s->l2scratch, p->n).flag, 0, 256, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->r, 0, img, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->phi, 0, img, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->status, 0, 256, s->stream);
@@ -1012,6 +1081,22 @@ int ddh_set_staged_chunk(int n, int chunk) {
   std::lock_guard<std::mutex> lock(g_mu);
   g_chunk[dev][n_slot(n)] = chunk;
   return DDH_OK;
+}
+
+int ddh_set_staged_persistent(int on) {
+  if (on != 0 && on != 1) return DDH_EINVAL;
+  int dev = 0;
+  DDH_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return DDH_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_persistent[dev] = on;
+  return DDH_OK;
+}
+
+int ddh_get_staged_persistent(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DDH_ECUDA;
+  return g_persistent[dev];
 }
 
 int ddh_get_staged_chunk(int n) {

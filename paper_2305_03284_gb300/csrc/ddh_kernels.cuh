@@ -88,7 +88,7 @@ struct StepBatch {
 // L2-staged path (grids beyond a cluster's shared memory, or any batch run for throughput):
 // per-stream views of the global scratch the stages exchange data through.  A batch is cut
 // into launch chunks of at most kMaxBatchL2 streams (the chunk size is a tuning knob).
-constexpr int kMaxBatchL2 = 32;
+constexpr int kMaxBatchL2 = 64;
 
 struct L2Stream {
   const float2* y;
@@ -102,6 +102,7 @@ struct L2Stream {
   float* beta;    // 4 images of pair weights: E, S, SE, SW
   float* part;    // row-block statistics, then the combined statistics
   int* flag;      // frame dropped (non-finite or zero variance)
+  unsigned* bar;  // grid-barrier words of a persistent launch led by this stream (zeroed at init)
 };
 
 struct L2Batch {
@@ -112,6 +113,24 @@ struct L2Batch {
   int ytab_base;
   int count;
 };
+
+// One persistent launch for a whole staged batch: every stage of every stream, the stages
+// separated by grid-wide barriers.  The streams of `b` come in up to kPersistGroups runs of
+// one grid size each (group g: streams [first[g], first[g] + count[g]) of size n[g], twiddle
+// table tw[g]); they share n_k.  `bar` points to three zeroed words (arrivals, generation,
+// abort) that no other launch uses at the same time.
+constexpr int kPersistGroups = 4;
+struct L2Persist {
+  L2Batch b;
+  int groups;
+  int first[kPersistGroups];
+  int count[kPersistGroups];
+  int n[kPersistGroups];
+  const float2* tw[kPersistGroups];
+  int n_k;
+  unsigned* bar;
+};
+cudaError_t launch_step_l2_persistent(const L2Persist& p, cudaStream_t st);
 
 size_t l2_scratch_bytes(int n);                    // per stream; 0 when n uses the cluster kernel
 L2Stream l2_stream_view(void* scratch, int n);     // y, r, phi, status left for the caller

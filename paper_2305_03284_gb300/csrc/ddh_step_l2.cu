@@ -32,51 +32,54 @@ constexpr int kRowThreads = 32 * kTr;
 __device__ __forceinline__ bool frame_dropped(const L2Stream& S) { return *S.flag != 0; }
 
 // ---- s1: per-row statistics and tip/tilt partial sums ---------------------------------------
+// One block of kT rows of stream `sid` (block `bx`): each warp takes whole rows (one row per
+// warp with 512 threads, two with 256); thread 0 combines the rows in row order.
 template <int N>
-__global__ void __launch_bounds__(kThreads) k_l2_stats(const __grid_constant__ L2Batch b) {
-  const L2Stream& S = b.st[blockIdx.y];
-  const KParams& P = b.prm[blockIdx.y];
-  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
+__device__ __forceinline__ void l2_stage_stats(const L2Batch& b, int sid, int bx) {
+  const L2Stream& S = b.st[sid];
+  const KParams& P = b.prm[sid];
+  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + sid] : S.y;
   __shared__ float red[16][8];
-  grid_dep_launch();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rho = kT * blockIdx.x + warp;
-  constexpr int PER = N / 32;
-  float2 v[PER];
-  float sre = 0.f, sim = 0.f;
+  for (int lr = warp; lr < kT; lr += static_cast<int>(blockDim.x >> 5)) {
+    const int rho = kT * bx + lr;
+    constexpr int PER = N / 32;
+    float2 v[PER];
+    float sre = 0.f, sim = 0.f;
 #pragma unroll
-  for (int j = 0; j < PER; ++j) {
-    v[j] = y[static_cast<size_t>(rho) * N + lane + 32 * j];
-    sre += v[j].x;
-    sim += v[j].y;
-  }
-  sre = warp_sum(sre);
-  sim = warp_sum(sim);
-  const float invN = 1.f / static_cast<float>(N);
-  const float2 m = make_float2(sre * invN, sim * invN);
-  float q = 0.f;
-#pragma unroll
-  for (int j = 0; j < PER; ++j) q += c_abs2(c_sub(v[j], m));
-  q = warp_sum(q);
-  // the frame's statistics above do not depend on the previous stage; phi and the
-  // statistics buffers below do
-  grid_dep_wait();
-  float txs = 0.f, txc = 0.f, tys = 0.f, tyc = 0.f;
-  if (P.tilt_mode) {
-    const float* pr = S.phi + static_cast<size_t>(rho) * N;
-    const int dy2 = ap_dist2(rho, N);
-    const int dy2n = rho + 1 < N ? ap_dist2(rho + 1, N) : (1 << 30);
-    for (int x = lane; x < N; x += 32) {
-      const int dx2 = ap_dist2(x, N);
-      if (dx2 + dy2 > P.ap_lim) continue;
-      if (x + 1 < N && ap_dist2(x + 1, N) + dy2 <= P.ap_lim) { txs += wrap_pi(pr[x + 1] - pr[x]); txc += 1.f; }
-      if (dx2 + dy2n <= P.ap_lim) { tys += wrap_pi(pr[x + N] - pr[x]); tyc += 1.f; }
+    for (int j = 0; j < PER; ++j) {
+      v[j] = y[static_cast<size_t>(rho) * N + lane + 32 * j];
+      sre += v[j].x;
+      sim += v[j].y;
     }
-    txs = warp_sum(txs); txc = warp_sum(txc); tys = warp_sum(tys); tyc = warp_sum(tyc);
-  }
-  if (lane == 0) {
-    red[warp][0] = m.x; red[warp][1] = m.y; red[warp][2] = q;
-    red[warp][3] = txs; red[warp][4] = txc; red[warp][5] = tys; red[warp][6] = tyc;
+    sre = warp_sum(sre);
+    sim = warp_sum(sim);
+    const float invN = 1.f / static_cast<float>(N);
+    const float2 m = make_float2(sre * invN, sim * invN);
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) q += c_abs2(c_sub(v[j], m));
+    q = warp_sum(q);
+    // the frame's statistics above do not depend on the previous stage; phi and the
+    // statistics buffers below do
+    grid_dep_wait();
+    float txs = 0.f, txc = 0.f, tys = 0.f, tyc = 0.f;
+    if (P.tilt_mode) {
+      const float* pr = S.phi + static_cast<size_t>(rho) * N;
+      const int dy2 = ap_dist2(rho, N);
+      const int dy2n = rho + 1 < N ? ap_dist2(rho + 1, N) : (1 << 30);
+      for (int x = lane; x < N; x += 32) {
+        const int dx2 = ap_dist2(x, N);
+        if (dx2 + dy2 > P.ap_lim) continue;
+        if (x + 1 < N && ap_dist2(x + 1, N) + dy2 <= P.ap_lim) { txs += wrap_pi(pr[x + 1] - pr[x]); txc += 1.f; }
+        if (dx2 + dy2n <= P.ap_lim) { tys += wrap_pi(pr[x + N] - pr[x]); tyc += 1.f; }
+      }
+      txs = warp_sum(txs); txc = warp_sum(txc); tys = warp_sum(tys); tyc = warp_sum(tyc);
+    }
+    if (lane == 0) {
+      red[lr][0] = m.x; red[lr][1] = m.y; red[lr][2] = q;
+      red[lr][3] = txs; red[lr][4] = txc; red[lr][5] = tys; red[lr][6] = tyc;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -93,10 +96,16 @@ __global__ void __launch_bounds__(kThreads) k_l2_stats(const __grid_constant__ L
       n_a = nn;
       t0 += red[w][3]; t1 += red[w][4]; t2 += red[w][5]; t3 += red[w][6];
     }
-    float* o = S.part + 8 * blockIdx.x;
+    float* o = S.part + 8 * bx;
     o[0] = m_a.x; o[1] = m_a.y; o[2] = q_a; o[3] = t0; o[4] = t1; o[5] = t2; o[6] = t3; o[7] = 0.f;
-    if (blockIdx.x == 0) *S.flag = 0;
+    if (bx == 0) *S.flag = 0;
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads) k_l2_stats(const __grid_constant__ L2Batch b) {
+  grid_dep_launch();
+  l2_stage_stats<N>(b, blockIdx.y, blockIdx.x);
 }
 
 // combine the row-block partials in rank order (identical in every block); called by one warp:
@@ -135,11 +144,10 @@ __device__ void l2_combine(const L2Stream& S, const KParams& P, float* g, float 
 
 // ---- s2: prologue and row IFFT of the pupil rows; transposed store into fb ------------------
 template <int N, int V>
-__global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_constant__ L2Batch b, int first) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const L2Stream& S = b.st[blockIdx.y];
-  const KParams& P = b.prm[blockIdx.y];
-  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
+__device__ __forceinline__ void l2_stage_rows_inv(const L2Batch& b, const float2* twg, int sid, int bx, int first, unsigned char* smem) {
+  const L2Stream& S = b.st[sid];
+  const KParams& P = b.prm[sid];
+  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + sid] : S.y;
   float2* tw = reinterpret_cast<float2*>(smem);
   // row tile with stride N + 4: the transposed accesses (8 rows x 4 columns per warp) hit
   // 16 bank pairs
@@ -147,13 +155,12 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
   float2* rows = tw + N;  // kTr rows x RW
   __shared__ float g[8];
   __shared__ float rec[N / kT][8];
-  for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = b.tw[i];
-  grid_dep_launch();
+  for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = twg[i];
   grid_dep_wait();
   if (first && threadIdx.x < 32) l2_combine<N>(S, P, g, rec, threadIdx.x);
   if (threadIdx.x == 0) {
     if (first) {
-      if (blockIdx.x == 0) {
+      if (bx == 0) {
         float* st = S.part + 8 * (N / kT);  // combined statistics for the later stages
         for (int k = 0; k < 6; ++k) st[k] = g[k];
         if (g[5] != 0.f) {
@@ -172,7 +179,7 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
   const float scale = g[2], tx = g[3], ty = g[4];
   const float cc = 0.5f * static_cast<float>(N - 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rho = kTr * blockIdx.x + warp;
+  const int rho = kTr * bx + warp;
   const int dy2 = ap_dist2(rho, N);
   float2* rb = rows + warp * RW;
   float* pr = S.phi + static_cast<size_t>(rho) * N;
@@ -217,18 +224,23 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
   // the aperture are zero and are not stored: the column pass fills them in itself.
   for (int i = threadIdx.x; i < kTr * N; i += kRowThreads) {
     const int x = i / kTr, r = i - x * kTr;
-    if (ap_dist2(kTr * blockIdx.x + r, N) <= P.ap_lim)
-      S.fb[static_cast<size_t>(x) * N + kTr * blockIdx.x + r] = rows[r * RW + swz(x)];
+    if (ap_dist2(kTr * bx + r, N) <= P.ap_lim)
+      S.fb[static_cast<size_t>(x) * N + kTr * bx + r] = rows[r * RW + swz(x)];
   }
+}
+
+template <int N, int V>
+__global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_constant__ L2Batch b, int first) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  grid_dep_launch();
+  l2_stage_rows_inv<N, V>(b, b.tw, blockIdx.y, blockIdx.x, first, smem);
 }
 
 // ---- s3: column IFFT, r-init + E-step, column FFT of mu; transposed store into fa ----------
 template <int N, int V>
-__global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const L2Stream& S = b.st[blockIdx.y];
-  const KParams& P = b.prm[blockIdx.y];
-  grid_dep_launch();
+__device__ __forceinline__ void l2_stage_cols(const L2Batch& b, const float2* twg, int sid, int bx, int first, unsigned char* smem) {
+  const L2Stream& S = b.st[sid];
+  const KParams& P = b.prm[sid];
   grid_dep_wait();
   if (frame_dropped(S)) return;
   float2* tw = reinterpret_cast<float2*>(smem);
@@ -238,8 +250,8 @@ __global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__
   float2* cols = tw + N;                                    // kTc columns x CW
   float* rt = reinterpret_cast<float*>(cols + kTc * CW);    // kTc x CW: r, then r-init
   float* stile = rt + kTc * CW;                             // kTc x CW: s
-  for (int i = threadIdx.x; i < N; i += kColThreads) tw[i] = b.tw[i];
-  const int x0 = kTc * blockIdx.x;
+  for (int i = threadIdx.x; i < N; i += kColThreads) tw[i] = twg[i];
+  const int x0 = kTc * bx;
   {
     // every load of a thread is issued before its first store (the shared-memory stores could
     // alias the loads' generic addresses otherwise, which would serialise them)
@@ -298,28 +310,33 @@ __global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__
   }
 }
 
+template <int N, int V>
+__global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  grid_dep_launch();
+  l2_stage_cols<N, V>(b, b.tw, blockIdx.y, blockIdx.x, first, smem);
+}
+
 // ---- s4: row FFT of mu and phase M-step ------------------------------------------------------
 template <int N, int V>
-__global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_constant__ L2Batch b) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const L2Stream& S = b.st[blockIdx.y];
-  const KParams& P = b.prm[blockIdx.y];
-  grid_dep_launch();
+__device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2* twg, int sid, int bx, unsigned char* smem) {
+  const L2Stream& S = b.st[sid];
+  const KParams& P = b.prm[sid];
   grid_dep_wait();
   if (frame_dropped(S)) return;
-  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + blockIdx.y] : S.y;
+  const float2* y = b.ytab != nullptr ? b.ytab[b.ytab_base + sid] : S.y;
   float2* tw = reinterpret_cast<float2*>(smem);
   // row tile with stride N + 4: the transposed accesses (8 rows x 4 columns per warp) hit
   // 16 bank pairs
   constexpr int RW = N + 4;
   float2* rows = tw + N;  // kTr rows x RW
-  for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = b.tw[i];
+  for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = twg[i];
   const float* st = S.part + 8 * (N / kT);
   const float2 ymean = make_float2(st[0], st[1]);
   const float scale = st[2];
   const int gs = P.g_shift, G = 1 << gs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rho = kTr * blockIdx.x + warp;
+  const int rho = kTr * bx + warp;
   const int dy2 = ap_dist2(rho, N);
   const bool row_ap = dy2 <= P.ap_lim;
   float2* rb = rows + warp * RW;
@@ -367,12 +384,18 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_consta
   }
 }
 
+template <int N, int V>
+__global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_constant__ L2Batch b) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  grid_dep_launch();
+  l2_stage_rows_fwd<N, V>(b, b.tw, blockIdx.y, blockIdx.x, smem);
+}
+
 // ---- s5: surrogate pair weights at the sweep's entry values ---------------------------------
 template <int N>
-__global__ void __launch_bounds__(256) k_l2_weights(const __grid_constant__ L2Batch b) {
-  const L2Stream& S = b.st[blockIdx.y];
-  const KParams& P = b.prm[blockIdx.y];
-  grid_dep_launch();
+__device__ __forceinline__ void l2_stage_weights(const L2Batch& b, int sid, int bx) {
+  const L2Stream& S = b.st[sid];
+  const KParams& P = b.prm[sid];
   grid_dep_wait();
   if (frame_dropped(S)) return;
   constexpr int M = N * N;
@@ -380,7 +403,7 @@ __global__ void __launch_bounds__(256) k_l2_weights(const __grid_constant__ L2Ba
   // kWPx pixels per thread (the grid covers the image once); all their loads are issued
   // before the first store, which could alias them otherwise
   constexpr int kWPx = 2;
-  const int i0 = blockIdx.x * blockDim.x * kWPx + threadIdx.x;
+  const int i0 = bx * blockDim.x * kWPx + threadIdx.x;
   float a[kWPx], vE[kWPx], vS[kWPx], vSE[kWPx], vSW[kWPx];
 #pragma unroll
   for (int u = 0; u < kWPx; ++u) {
@@ -403,17 +426,22 @@ __global__ void __launch_bounds__(256) k_l2_weights(const __grid_constant__ L2Ba
   }
 }
 
+template <int N>
+__global__ void __launch_bounds__(256) k_l2_weights(const __grid_constant__ L2Batch b) {
+  grid_dep_launch();
+  l2_stage_weights<N>(b, blockIdx.y, blockIdx.x);
+}
+
 // ---- s6: one ICD colour ---------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Batch b, int c) {
-  const L2Stream& S = b.st[blockIdx.y];
-  const KParams& P = b.prm[blockIdx.y];
-  grid_dep_launch();
+__device__ __forceinline__ void l2_stage_colour(const L2Batch& b, int sid, int bx, int c, int nbx) {
+  const L2Stream& S = b.st[sid];
+  const KParams& P = b.prm[sid];
   grid_dep_wait();
   if (frame_dropped(S)) return;
   constexpr int M = N * N;
   const int cx = c & 1, cy = c >> 1;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M / 4; k += gridDim.x * blockDim.x) {
+  for (int k = bx * blockDim.x + threadIdx.x; k < M / 4; k += nbx * blockDim.x) {
     const int rho = cy + 2 * (k / (N / 2)), x = cx + 2 * (k % (N / 2));
     const int i = rho * N + x;
     const bool up = rho > 0, dn = rho + 1 < N, lf = x > 0, rt = x + 1 < N;
@@ -442,6 +470,12 @@ __global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Bat
     Csum = fmaf(wSE, rSE, Csum);
     S.r[i] = fmaxf(icd_root_from(Wsum, Csum, S.s[i], S.r0[i]), P.r_floor);
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Batch b, int c) {
+  grid_dep_launch();
+  l2_stage_colour<N>(b, blockIdx.y, blockIdx.x, c, gridDim.x);
 }
 
 template <int N>
@@ -498,7 +532,185 @@ cudaError_t l2_configure() {
   return e;
 }
 
+// ---- one persistent launch per batched step -----------------------------------------------
+// The nine stages of every stream of the batch (any mix of the staged grid sizes) in one
+// cooperative launch: at each stage the grid's blocks take the stage's work items -- (stream,
+// block) pairs of the chained kernels, listed group by group -- in a block-strided loop, and a
+// grid-wide barrier separates the stages.  Every item runs the same stage function as the
+// chained kernels (256 threads), so the results are bit for bit those of the chained launches.
+constexpr int kPersistThreads = 256;
+constexpr uint64_t kBarrierLimitNs = 200000000ull;  // 200 ms; a stage takes tens of microseconds
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Items (blocks of the chained kernel) of stage `stage` for one stream of grid n: 0 statistics,
+// 1 prologue + row IFFT, 2 column pass, 3 row FFT + phase step, 4 pair weights, 5-8 colours.
+__device__ __forceinline__ int stage_items(int stage, int n) {
+  switch (stage) {
+    case 0: return n / kT;
+    case 1: case 3: return n / kTr;
+    case 2: return n / kTc;
+    case 4: return n * n / 512;
+    default: return n * n / 1024;
+  }
+}
+
+// Each stage of each grid size is its own (not inlined) function, so that the persistent
+// kernel's register budget is that of its largest stage rather than of all of them inlined
+// together.
+template <int N>
+__device__ __noinline__ void pi_stats(const L2Batch& b, int sid, int bx) { l2_stage_stats<N>(b, sid, bx); }
+template <int N>
+__device__ __noinline__ void pi_rows_inv(const L2Batch& b, const float2* tw, int sid, int bx, int first,
+                                         unsigned char* smem) {
+  l2_stage_rows_inv<N, 0>(b, tw, sid, bx, first, smem);
+}
+template <int N>
+__device__ __noinline__ void pi_cols(const L2Batch& b, const float2* tw, int sid, int bx, int first,
+                                     unsigned char* smem) {
+  l2_stage_cols<N, 0>(b, tw, sid, bx, first, smem);
+}
+template <int N>
+__device__ __noinline__ void pi_rows_fwd(const L2Batch& b, const float2* tw, int sid, int bx, unsigned char* smem) {
+  l2_stage_rows_fwd<N, 0>(b, tw, sid, bx, smem);
+}
+template <int N>
+__device__ __noinline__ void pi_weights(const L2Batch& b, int sid, int bx) { l2_stage_weights<N>(b, sid, bx); }
+template <int N>
+__device__ __noinline__ void pi_colour(const L2Batch& b, int sid, int bx, int c) {
+  l2_stage_colour<N>(b, sid, bx, c, N * N / 1024);
+}
+
+template <int N>
+__device__ __forceinline__ void persist_item(const L2Batch& b, const float2* tw, int stage, int first, int sid,
+                                             int bx, unsigned char* smem) {
+  switch (stage) {
+    case 0: pi_stats<N>(b, sid, bx); break;
+    case 1: pi_rows_inv<N>(b, tw, sid, bx, first, smem); break;
+    case 2: pi_cols<N>(b, tw, sid, bx, first, smem); break;
+    case 3: pi_rows_fwd<N>(b, tw, sid, bx, smem); break;
+    case 4: pi_weights<N>(b, sid, bx); break;
+    default: pi_colour<N>(b, sid, bx, stage - 5); break;
+  }
+}
+
+// Grid-wide barrier: thread 0 of each block publishes the block's writes (fence), arrives on
+// bar[0] and waits for the last arrival to advance the generation bar[1]; the wait polls with
+// a device-time limit, after which it raises the abort word bar[2].  Returns false (to every
+// thread of the block) when the barrier was abandoned, by this block or another.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* vabort = bar + 2;
+    int res = 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      while (*vgen == gen) {
+        if (*vabort != 0u) { res = 0; break; }
+        if (global_ns() - t0 > kBarrierLimitNs) {
+          atomicExch(bar + 2, 1u);
+          res = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = res;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(kPersistThreads, 4) k_l2_persistent(const __grid_constant__ L2Persist p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  grid_dep_wait();
+  for (int it = 0; it < p.n_k; ++it) {
+    const int first = it == 0 ? 1 : 0;
+    for (int stage = it == 0 ? 0 : 1; stage < 9; ++stage) {
+      int total = 0;
+      for (int g = 0; g < p.groups; ++g) total += p.count[g] * stage_items(stage, p.n[g]);
+      for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int g = 0, local = item;
+        for (; g < p.groups - 1; ++g) {
+          const int ng = p.count[g] * stage_items(stage, p.n[g]);
+          if (local < ng) break;
+          local -= ng;
+        }
+        const int per = stage_items(stage, p.n[g]);
+        const int sid = p.first[g] + local / per, bx = local % per;
+        switch (p.n[g]) {
+          case 512: persist_item<512>(p.b, p.tw[g], stage, first, sid, bx, smem); break;
+          case 256: persist_item<256>(p.b, p.tw[g], stage, first, sid, bx, smem); break;
+          default: persist_item<128>(p.b, p.tw[g], stage, first, sid, bx, smem); break;
+        }
+        __syncthreads();  // the item's shared scratch is free for the next item
+      }
+      if (it == p.n_k - 1 && stage == 8) break;  // no barrier after the last stage
+      if (!grid_barrier(p.bar, gridDim.x)) {
+        // abandoned: every stream of the launch reports the expired wait; its state is left
+        // part-way through the step (reload a checkpoint)
+        if (threadIdx.x == 0 && blockIdx.x == 0)
+          for (int i = 0; i < p.b.count; ++i)
+            if (p.b.st[i].status != nullptr) atomicOr(p.b.st[i].status, kStatusTimeout);
+        return;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_step_l2_persistent(const L2Persist& p, cudaStream_t st) {
+  // shared memory of the largest stage of the largest grid in the launch
+  int nmax = 0;
+  for (int g = 0; g < p.groups; ++g) nmax = p.n[g] > nmax ? p.n[g] : nmax;
+  const size_t smem = nmax == 512 ? cols_smem<512>() : nmax == 256 ? cols_smem<256>() : cols_smem<128>();
+  static thread_local int dev_cached = -1;
+  static thread_local int blocks_cached[3] = {0, 0, 0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int slot = nmax == 512 ? 0 : nmax == 256 ? 1 : 2;
+  if (dev != dev_cached) {
+    blocks_cached[0] = blocks_cached[1] = blocks_cached[2] = 0;
+    dev_cached = dev;
+  }
+  if (blocks_cached[slot] == 0) {
+    e = cudaFuncSetAttribute(k_l2_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(cols_smem<512>()));
+    int per_sm = 0, sms = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_l2_persistent, kPersistThreads, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    blocks_cached[slot] = per_sm * sms;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks_cached[slot]);
+  cfg.blockDim = dim3(kPersistThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_l2_persistent, p);
+}
 
 size_t l2_scratch_bytes(int n) {
   if (n != 128 && n != 256 && n != 512) return 0;
@@ -518,6 +730,7 @@ L2Stream l2_stream_view(void* scratch, int n) {
   s.beta = s.s + M;
   s.part = s.beta + 4 * M;
   s.flag = reinterpret_cast<int*>(s.part + 8 * (n / kT) + 16);
+  s.bar = reinterpret_cast<unsigned*>(s.flag + 4);  // inside the 256-byte tail
   return s;
 }
 

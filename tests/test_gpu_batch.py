@@ -117,7 +117,7 @@ def test_autotune_small(ddh, tmp_path):
     try:
         out = str(tmp_path / "t.json")
         table = autotune.tune(path=out, sizes=(128,), batch_sizes=(1, 4), big={128: 4}, chunks=(2, 4),
-                              schedule_streams={128: 2})
+                              schedule_streams={128: 2}, persistent_mix=False)
         row = table["128"]
         assert 0 <= row["schedule"] < ddh.fft_schedule_count(128)
         assert row["staged_chunk"] in (2, 4) and set(row["path_us_per_step"]) == {"1", "4"}
@@ -130,7 +130,50 @@ def test_autotune_small(ddh, tmp_path):
         start = row["staged_from_streams"]
         assert autotune.recommend_path(128, 1000, out) == (2 if start is not None else 1)
         assert autotune.recommend_path(512, 3, out) == 0
-        assert L.ddh_set_staged_chunk(64, 4) == -1 and L.ddh_set_staged_chunk(256, 33) == -1
+        assert L.ddh_set_staged_chunk(64, 4) == -1 and L.ddh_set_staged_chunk(256, 65) == -1
     finally:
         ddh.set_fft_schedule(128, old_s)
         L.ddh_set_staged_chunk(128, old_c)
+
+
+@pytest.mark.parametrize("n_k", [1, 2])
+def test_persistent_staged_launch_equals_chained_launches(ddh, n_k):
+    """A batch whose staged streams (128^2, 256^2 and 512^2 runs, with a cluster-kernel stream
+    between them) run as one persistent launch per step gives, bit for bit, what the chained
+    stage launches give -- by ddh_step_batch and through a captured graph."""
+    from synth import ddh_synth as sy
+    L = ddh.lib()
+    b = sy.config_batched(3)
+    cfgs = [b[0], b[1], b[2], sy.config_single_256(3), b[30], sy.config_single_256(3), b[56], b[57]]
+    paths = [2, 2, 2, 2, 1, 2, 0, 0]
+    data = []
+    for c, pa in zip(cfgs, paths):
+        ys, _ = sy.Stream(sy.with_frames(c, 3)).frames(3)
+        data.append((torch.from_numpy(ys).cuda(), ddh.default_params(c.n, c.aperture_diam, c.snr, exec_path=pa,
+                                                                     n_k=n_k)))
+    old = L.ddh_get_staged_persistent()
+    results = {}
+    try:
+        for mode in (0, 1):
+            assert L.ddh_set_staged_persistent(mode) == 0
+            direct = [ddh.Stream(p) for _, p in data]
+            graphed = [ddh.Stream(p) for _, p in data]
+            g = ddh.BatchGraph(graphed)
+            for f in range(3):
+                ys = [y[f] for y, _ in data]
+                ddh.step_batch(direct, ys)
+                g.run(ys)
+            torch.cuda.synchronize()
+            for s_ in direct + graphed:
+                s_.sync()
+            results[mode] = [(s_.phase().clone(), s_.reflectance().clone()) for s_ in direct + graphed]
+            g.close()
+    finally:
+        L.ddh_set_staged_persistent(old)
+    for (p0, r0), (p1, r1) in zip(results[0], results[1]):
+        assert torch.equal(p0, p1) and torch.equal(r0, r1)
+    # direct and graph agree too
+    k = len(data)
+    for i in range(k):
+        assert torch.equal(results[1][i][0], results[1][k + i][0])
+    assert L.ddh_set_staged_persistent(2) == -1
