@@ -562,9 +562,11 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=N
         for i, c in enumerate(cfgs):
             # the per-frame comparison runs the plain path (the library's default kernels)
             svc.admit(i, ddh.default_params(c.n, c.aperture_diam, c.snr, exec_path=0 if per_frame else paths[c.n]))
-        # warm-up: 20 frames per sensor queued at once (the GPU leaves its idle clocks and every
-        # kernel of the mix is loaded before the trace starts)
-        svc.drive([(0.0, i, rings[i][k % ring]) for k in range(20) for i in range(len(cfgs))])
+        # warm-up (untimed): 20 frames per sensor queued at once (the GPU leaves its idle clocks
+        # and every kernel of the mix is loaded), then the trace's first 20 ms replayed at its
+        # own pace, so that the measured replay starts from a service in its steady state
+        svc.drive([(0.0, i, rings[i][k % ring]) for k in range(20) for i in range(len(cfgs))], keep_running=True)
+        svc.drive([a for a in trace if a[0] < 0.02], keep_running=True)
         st0 = svc.stats()
         res = svc.drive(trace)
         st1 = svc.stats()
@@ -573,8 +575,19 @@ def service_measure(ddh, total_frames=10_000, ring=4, seed=5, cfgs=None, label=N
         last = max(r[4] for r in res)
         lat = sorted((r[4] - r[3]) * 1e6 for r in res)
         batches = st1["batches"] - st0["batches"]
+        # where the tail sits: p99 per 10 ms window of arrival time, and the longest stretch
+        # with no completion
+        win = {}
+        for r in res:
+            win.setdefault(int((r[3] - first) / 0.01), []).append((r[4] - r[3]) * 1e6)
+        done = sorted(r[4] for r in res)
+        gap = max((b - a for a, b in zip(done, done[1:])), default=0.0)
         return {"frames_per_s": len(res) / (last - first), "latency_us_p50": lat[len(lat) // 2],
                 "latency_us_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                "latency_us_max": lat[-1],
+                "latency_us_p99_per_10ms_window": [round(sorted(v)[min(len(v) - 1, int(0.99 * len(v)))])
+                                                   for _, v in sorted(win.items())],
+                "longest_completion_gap_us": gap * 1e6,
                 "mean_frames_per_launch_group": len(res) / max(1, batches), "launch_groups": batches}
     out["continuous_batching"] = one(False, arrivals)
     out["per_frame_launch"] = one(True, arrivals)

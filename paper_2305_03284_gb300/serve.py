@@ -44,6 +44,7 @@ class NativeService:
         _lib.check(_lib.lib().ddh_service_create(ctypes.byref(self._h), ctypes.c_void_p(self.stream.cuda_stream),
                                                  int(mem_budget_bytes), int(max_in_flight),
                                                  1 if per_frame_launch else 0))
+        self._running = False
         self._buf = (_lib.DdhCompletion * 4096)()
         self._n = ctypes.c_int()
         self._sizes = {}
@@ -110,20 +111,25 @@ class NativeService:
 
     def start(self) -> None:
         self._L.check(self._L.lib().ddh_service_start(self._h))
+        self._running = True
 
     def stop(self) -> None:
+        self._running = False
         self._L.check(self._L.lib().ddh_service_stop(self._h))
 
-    def drive(self, arrivals, timeout_s: float = 120.0) -> list:
+    def drive(self, arrivals, timeout_s: float = 120.0, keep_running: bool = False) -> list:
         """Replay ``arrivals`` = sorted ``(t_seconds, sensor, frame)`` on the library thread;
-        returns completions (tag = index into ``arrivals``).  The replaying Python loop runs
+        returns completions (tag = index into ``arrivals``).  The library thread is started if
+        it is not running; ``keep_running`` leaves it running afterwards (a later replay then
+        does not pay for starting it).  The replaying Python loop runs
         with the garbage collector paused: a collection pass over a large heap stops this
         thread for tens of milliseconds, which would delay submissions past their scheduled
         arrival times and be counted as service latency."""
         import gc
         gc_was_on = gc.isenabled()
         gc.disable()
-        self.start()
+        if not self._running:
+            self.start()
         done = []
         try:
             t0 = self.now()
@@ -140,7 +146,8 @@ class NativeService:
                 if self.now() - t0 > timeout_s:
                     raise TimeoutError("service did not finish the trace")
         finally:
-            self.stop()
+            if not keep_running:
+                self.stop()
             if gc_was_on:
                 gc.enable()
         return done
