@@ -231,6 +231,35 @@ def test_parity_256_every_frame_long_run(ddh):
     print(f"300 frames at 256^2, worst one-step error: phi {worst[0]:.2e}, r {worst[1]:.2e}, Strehl {worst[2]:.2e}")
 
 
+def test_parity_256_full_1000_frame_stream_every_tenth_frame(ddh):
+    """The whole 1000-frame 256^2 stream of the benchmark workload, free-running on the GPU;
+    at every tenth frame the oracle takes one step from the GPU's own state and phi, r and
+    that frame's Strehl ratio are compared."""
+    cfg = sy.config_single_256(frames=1000)
+    st = sy.Stream(cfg)
+    p = ddh.default_params(cfg.n, cfg.aperture_diam, cfg.snr)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    s = ddh.Stream(p)
+    worst = [0.0, 0.0, 0.0]
+    for i in range(1000):
+        y, ph = st.frame(i)
+        check = i % 10 == 9
+        if check:
+            r0 = np32(s.reflectance()).astype(np.float64)
+            p0 = np32(s.phase()).astype(np.float64)
+        s.step(cu(y))
+        if check:
+            nxt, _ = o.step(o.State(r=r0, phi=p0, n=i), y, prm)
+            g_s = s.strehl(cu(ph.astype(np.float32)))
+            o_s = o.strehl(nxt.phi, ph.astype(np.float32).astype(np.float64), a)
+            e = (rel_l2_phase(np32(s.phase()), nxt.phi, a), rel_l2(np32(s.reflectance()), nxt.r), abs(g_s - o_s) / o_s)
+            worst = [max(w, v) for w, v in zip(worst, e)]
+            assert e[0] < TOL and e[1] < TOL and e[2] < TOL, (i, e)
+    s.sync()
+    print(f"1000 frames at 256^2, every tenth frame: phi {worst[0]:.2e}, r {worst[1]:.2e}, Strehl {worst[2]:.2e}")
+
+
 @pytest.mark.parametrize("over", [{"n_k": 2}, {"n_k": 3}, {"n_k": 4}, {"n_k": 8}, {"tilt_mode": 0},
                                   {"aperture_diam": 31.3},
                                   {"prior_sigma": 0.05, "prior_p": 1.5}, {"phase_block": 4},
