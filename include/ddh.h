@@ -195,7 +195,10 @@ int ddh_step_batch(ddh_state *const *states, const void *const *y_c64_dev, int c
  * graph whose grid-size groups run on concurrent branches; the graph reads each stream's frame
  * through a device table of frame pointers owned by the batch.  ddh_batch_run() uploads the
  * table from `y_c64_dev` (count device pointers, 16-byte aligned, valid until the step has
- * run) and launches the graph on that stream: one graph launch per time step.  The graph
+ * run) on a library-owned copy stream, while the previous step may still run, and launches the
+ * graph on that stream after the upload: one graph launch per time step.  Four instances of
+ * the graph, each with its own table, take the steps in turn (a call waits on the host until
+ * the step four calls earlier has finished).  The graph
  * holds each state's parameters as they were at creation: rebuild it after ddh_load.  The
  * batch does not own the states; free it before them. */
 typedef struct ddh_batch ddh_batch;

@@ -869,32 +869,42 @@ int ddh_step_batch(ddh_state* const* states, const void* const* ys, int count) {
   return DDH_OK;
 }
 
+// A captured batch: kSlots instances of the same graph, instance j reading its frame pointers
+// from device table j.  Run k uses instance k % kSlots: the table is uploaded on a side copy
+// stream (while the previous run's graph still executes) and the graph launch waits only for
+// that copy, so no upload sits on the batch's stream between two steps.
+constexpr int kBatchSlots = 4;
 struct ddh_batch {
   int count;
   int device;
   cudaStream_t stream;
   cudaStream_t capture;
+  cudaStream_t copy;
   std::vector<ddh_state*> states;
-  const float2** ytab;      // device table of frame pointers read by the graph's kernels
-  const void** staging[4];  // pinned host copies of the table (a ring, one per run in flight)
-  cudaEvent_t slot_done[4];
+  const float2** ytab[kBatchSlots];     // device tables of frame pointers, one per instance
+  const void** staging[kBatchSlots];    // pinned host copies of the tables
+  cudaEvent_t copied[kBatchSlots];      // table j uploaded (copy stream)
+  cudaEvent_t slot_done[kBatchSlots];   // instance j's last run finished (batch stream)
   int run;
-  cudaGraph_t graph;
-  cudaGraphExec_t exec;
+  cudaGraph_t graph[kBatchSlots];
+  cudaGraphExec_t exec[kBatchSlots];
 };
 
 int ddh_batch_free(ddh_batch* b) {
   if (b == nullptr) return DDH_OK;
   DdhDeviceGuard dg(b->device);
   cudaStreamSynchronize(b->stream);
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  cudaFree(const_cast<float2**>(b->ytab));
-  for (int i = 0; i < 4; ++i) {
-    if (b->staging[i]) cudaFreeHost(b->staging[i]);
-    if (b->slot_done[i]) cudaEventDestroy(b->slot_done[i]);
+  if (b->copy) cudaStreamSynchronize(b->copy);
+  for (int j = 0; j < kBatchSlots; ++j) {
+    if (b->exec[j]) cudaGraphExecDestroy(b->exec[j]);
+    if (b->graph[j]) cudaGraphDestroy(b->graph[j]);
+    cudaFree(const_cast<float2**>(b->ytab[j]));
+    if (b->staging[j]) cudaFreeHost(b->staging[j]);
+    if (b->copied[j]) cudaEventDestroy(b->copied[j]);
+    if (b->slot_done[j]) cudaEventDestroy(b->slot_done[j]);
   }
   if (b->capture) cudaStreamDestroy(b->capture);
+  if (b->copy) cudaStreamDestroy(b->copy);
   delete b;
   return DDH_OK;
 }
@@ -911,31 +921,35 @@ int ddh_batch_create(ddh_batch** out, ddh_state* const* states, int count) {
   b->device = states[0]->device;
   b->stream = states[0]->stream;
   b->states.assign(states, states + count);
-  cudaError_t e = cudaMalloc(&b->ytab, sizeof(float2*) * count);
-  for (int i = 0; e == cudaSuccess && i < 4; ++i) {
-    e = cudaMallocHost(&b->staging[i], sizeof(void*) * count);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->slot_done[i], cudaEventDisableTiming);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->copy, cudaStreamNonBlocking);
+  for (int j = 0; e == cudaSuccess && j < kBatchSlots; ++j) {
+    e = cudaMalloc(&b->ytab[j], sizeof(float2*) * count);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->staging[j], sizeof(void*) * count);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied[j], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->slot_done[j], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     const int code = cuda_fail(e);
     ddh_batch_free(b);
     return code;
   }
-  // capture one batched step (grid-size groups on concurrent branches) into a graph
-  e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    rc = enqueue_batch(states, nullptr, b->ytab, count, b->capture, b->device);
+  // capture one batched step (groups on concurrent branches) per table slot
+  for (int j = 0; j < kBatchSlots && rc == DDH_OK; ++j) {
+    e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e);
+      break;
+    }
+    rc = enqueue_batch(states, nullptr, b->ytab[j], count, b->capture, b->device);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->capture, &g);
-    b->graph = g;
+    b->graph[j] = g;
     if (rc == DDH_OK && e2 != cudaSuccess) rc = cuda_fail(e2);
     if (rc == DDH_OK) {
-      e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      e = cudaGraphInstantiate(&b->exec[j], b->graph[j], 0);
       if (e != cudaSuccess) rc = cuda_fail(e);
     }
-  } else {
-    rc = cuda_fail(e);
   }
   if (rc != DDH_OK) {
     ddh_batch_free(b);
@@ -951,13 +965,16 @@ int ddh_batch_run(ddh_batch* b, const void* const* ys) {
   for (int i = 0; i < b->count; ++i)
     if (ys[i] == nullptr || reinterpret_cast<uintptr_t>(ys[i]) % 16 != 0) return DDH_EINVAL;
   DDH_ON_DEVICE(b->device);
-  const int slot = b->run & 3;
-  DDH_CUDA(cudaEventSynchronize(b->slot_done[slot]));  // that slot's previous upload has run
-  std::memcpy(b->staging[slot], ys, sizeof(void*) * b->count);
-  DDH_CUDA(cudaMemcpyAsync(const_cast<float2**>(b->ytab), b->staging[slot], sizeof(void*) * b->count,
-                           cudaMemcpyHostToDevice, b->stream));
-  DDH_CUDA(cudaEventRecord(b->slot_done[slot], b->stream));
-  DDH_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  const int j = b->run % kBatchSlots;
+  // instance j's previous run has finished: its table and staging copy are free
+  DDH_CUDA(cudaEventSynchronize(b->slot_done[j]));
+  std::memcpy(b->staging[j], ys, sizeof(void*) * b->count);
+  DDH_CUDA(cudaMemcpyAsync(const_cast<float2**>(b->ytab[j]), b->staging[j], sizeof(void*) * b->count,
+                           cudaMemcpyHostToDevice, b->copy));
+  DDH_CUDA(cudaEventRecord(b->copied[j], b->copy));
+  DDH_CUDA(cudaStreamWaitEvent(b->stream, b->copied[j], 0));
+  DDH_CUDA(cudaGraphLaunch(b->exec[j], b->stream));
+  DDH_CUDA(cudaEventRecord(b->slot_done[j], b->stream));
   b->run += 1;
   for (ddh_state* s : b->states) s->frame += 1;
   return DDH_OK;
