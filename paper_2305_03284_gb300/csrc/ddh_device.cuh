@@ -356,7 +356,7 @@ __device__ __forceinline__ float icd_root_from(float W, float C, float s, float 
     for (int it = 0; it < 6; ++it) {
       const float f = fmaf(fmaf(fmaf(W, r, -C), r, 1.f), r, -s);
       const float fp = fmaf(fmaf(3.f * W, r, -2.f * C), r, 1.f);  // >= 1 - C^2/(3W) >= 0
-      step = __fdividef(f, fp);
+      step = f * hw_rcp(fp);
       r -= step;
     }
     if (r > 0.f && fabsf(step) <= 9.5367431640625e-7f * r) return r;
