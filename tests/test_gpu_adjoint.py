@@ -157,6 +157,39 @@ def test_config4_sixteen_streams_256(mods):
             assert np.all(eg < TOL_UNROLLED) and er < TOL_UNROLLED and ep < TOL_UNROLLED, (eg, er, ep)
 
 
+def _window_grads(ddh, adjoint, cfg, ys_dev):
+    p = ddh.default_params(cfg.n, cfg.aperture_diam, cfg.snr)
+    r0 = torch.full((cfg.n, cfg.n), 1e-3, device="cuda", requires_grad=True)
+    phi0 = torch.zeros((cfg.n, cfg.n), device="cuda", requires_grad=True)
+    sig = torch.tensor(float(p.prior_sigma), dtype=torch.float64, requires_grad=True)
+    pp = torch.tensor(float(p.prior_p), dtype=torch.float64, requires_grad=True)
+    s2 = torch.tensor(float(p.noise_var), dtype=torch.float64, requires_grad=True)
+    rK, phiK = adjoint.unrolled(r0, phi0, sig, pp, s2, ys_dev, p)
+    (rK.sum() + phiK.square().sum()).backward()
+    return [sig.grad, pp.grad, s2.grad, r0.grad, phi0.grad]
+
+
+def test_windows_on_concurrent_streams_equal_sequential_windows(mods):
+    """Unrolled windows issued on four CUDA streams at once (the library keeps one state per
+    stream) give bit for bit the gradients of the same windows run one after another."""
+    ddh, adjoint = mods
+    cfgs = sy.config_adjoint(streams=8, frames=8)
+    ys = [torch.from_numpy(sy.Stream(c).frames(8)[0]).cuda() for c in cfgs]
+    seq = [[t.detach().clone() for t in _window_grads(ddh, adjoint, c, y)] for c, y in zip(cfgs, ys)]
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    conc = []
+    for i, (c, y) in enumerate(zip(cfgs, ys)):
+        st = streams[i % 4]
+        st.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(st):
+            conc.append(_window_grads(ddh, adjoint, c, y))
+    torch.cuda.synchronize()
+    for a, b in zip(seq, conc):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y.to(x.device))
+
+
 def test_unrolled_calls_equal_per_frame_calls(mods):
     """ddh_unrolled_forward / ddh_unrolled_backward (the K-frame loops inside the library)
     give bit for bit what the per-frame calls give: ddh_step from each checkpoint, then
