@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import ddh_oracle as o
 from synth import ddh_synth as sy
 
 pytestmark = pytest.mark.gpu
@@ -75,3 +76,37 @@ def test_every_simulation_reaches_strehl_0_8_within_150_frames(gpu_traces):
     print("best 10-frame mean Strehl per simulation:", " ".join(f"{b:.3f}" for b in best))
     assert min(best) >= 0.8, best
     assert float(np.median(gpu_traces[:, 0])) < 0.2  # it starts from the uncorrected phase
+
+
+def test_state_after_100_free_running_frames_matches_the_oracle(ddh):
+    """The spec parity bar at the paper's 256^2 size: after 100 free-running frames of
+    simulation 0 (tracking parameter set, one EM iteration per frame) the GPU's phi (wrapped,
+    over the pupil) and r agree with the FP64 oracle's, run on the same float32 parameter values,
+    to a relative L2 error below 2e-5, and so does the 100-frame Strehl trace."""
+    p = ddh.tracking_params(256, 128.0, 10.0)
+    prm = o.Params(n=p.n, aperture_diam=float(p.aperture_diam), lam=float(p.lam), alpha=float(p.alpha),
+                   n_k=p.n_k, noise_var=float(p.noise_var), prior_p=float(p.prior_p), prior_q=float(p.prior_q),
+                   prior_T=float(p.prior_T), prior_sigma=float(p.prior_sigma), r_floor=float(p.r_floor),
+                   tilt_mode=p.tilt_mode, phase_block=p.phase_block, phase_prior=float(p.phase_prior),
+                   phase_sweeps=p.phase_sweeps, noise_update=p.noise_update)
+    frames = 100
+    ys, ph = sy.Stream(sy.config_paper_256(0, frames)).frames(frames)
+    a = o.aperture(256, 128.0)
+    s = ddh.Stream(p)
+    yd = torch.from_numpy(ys).cuda()
+    gS = []
+    for k in range(frames):
+        s.step(yd[k])
+        gS.append(s.strehl(torch.from_numpy(ph[k].astype(np.float32)).cuda()))
+    gphi = s.phase().cpu().numpy().astype(np.float64)
+    gr = s.reflectance().cpu().numpy().astype(np.float64)
+    st = o.init_state(256)
+    oS = []
+    for k in range(frames):
+        st, _ = o.step(st, ys[k], prm)
+        oS.append(o.strehl(st.phi, ph[k].astype(np.float32).astype(np.float64), a))
+    ephi = float(np.linalg.norm(o.wrap(gphi - st.phi)[a]) / np.linalg.norm(st.phi[a]))
+    er = float(np.linalg.norm(gr - st.r) / np.linalg.norm(st.r))
+    eS = float(np.linalg.norm(np.array(gS) - np.array(oS)) / np.linalg.norm(oS))
+    print(f"256^2 tracking set, 100 free-running frames: phi {ephi:.2e}, r {er:.2e}, Strehl trace {eS:.2e}")
+    assert ephi < TOL and er < TOL and eS < TOL, (ephi, er, eS)
