@@ -148,6 +148,38 @@ def test_free_running_parity_64_100_frames_tiled_phase(ddh):
     assert np.all(gphi[:, ~a] == 0.0)
 
 
+@pytest.mark.parametrize("stream", ["paper", "bench"])
+def test_free_running_parity_256_100_frames_tiled_phase_both_paths(ddh, stream):
+    """North-star parity at the realistic size: 100 free-running 256^2 frames with the phase
+    held constant on 2x2 tiles, on the cluster kernel and on the L2-staged kernels, against one
+    FP64 oracle trajectory: the paper's Sec. 5.A stream (bar chart, D/r0 10, SNR 10 dB; sigma_r
+    0.03, alpha 0.0125) and the benchmark's stream (D/r0 15, 1 px/frame, SNR 5; defaults)."""
+    from paper_2305_03284_gb300 import _lib
+    frames = 100
+    if stream == "paper":
+        cfg = sy.config_paper_256(0, frames)
+        mk = lambda path: ddh.tracking_params(256, 128.0, 10.0, phase_prior=0.0, exec_path=path)
+    else:
+        cfg = sy.with_frames(sy.config_single_256(), frames)
+        mk = lambda path: ddh.default_params(256, 128.0, 5.0, phase_block=2, exec_path=path)
+    ys, ph = sy.Stream(cfg).frames(frames)
+    ph = ph.astype(np.float32).astype(np.float64)
+    a = o.aperture(256, 128.0)
+    ophi, orr, oS = _run_oracle(oracle_params(mk(_lib.DDH_PATH_CLUSTER)), ys, ph)
+    for path in (_lib.DDH_PATH_CLUSTER, _lib.DDH_PATH_STAGED):
+        s = ddh.Stream(mk(path))
+        yd = cu(ys)
+        gS = []
+        for k in range(frames):
+            s.step(yd[k])
+            gS.append(s.strehl(cu(ph[k].astype(np.float32))))
+        e = (rel_l2_phase(np32(s.phase()), ophi[-1], a), rel_l2(np32(s.reflectance()), orr[-1]), rel_l2(gS, oS))
+        s.close()
+        print(f"256^2 {stream} stream, path {path}, 100 frames, tiled phase: phi {e[0]:.2e}, r {e[1]:.2e}, "
+              f"Strehl trace {e[2]:.2e}")
+        assert e[0] < TOL and e[1] < TOL and e[2] < TOL, (path, e)
+
+
 def test_free_running_parity_64_per_pixel_phase_short(ddh):
     """Per-pixel phase: the iteration amplifies any perturbation (the FP64 oracle against
     itself grows 1e-7 to O(1) within ~30 frames), so free-running agreement is checked over
