@@ -175,9 +175,10 @@ int ddh_set_params(ddh_state *s, const ddh_params *p);
  * stream for a state admitted by ddh_service_admit); NULL if s is NULL. */
 void *ddh_state_stream(const ddh_state *s);
 
-/* Peak Strehl ratio (N <= 256) of the current phase estimate against `phi_true_dev` (N*N float32,
- * device): max |F^H(a exp(j(phi_true - phi)))|^2 / max |F^H a|^2 (Sec. 5.B).  Synchronous:
- * the value lands in *out.  Evaluation only, never part of a step. */
+/* Peak Strehl ratio of the current phase estimate against `phi_true_dev` (N*N float32, device):
+ * max |F^H(a exp(j(phi_true - phi)))|^2 / max |F^H a|^2 (Sec. 5.B); any supported N (512 x 512:
+ * a row and a column launch through the stream's scratch image, which steps rewrite anyway).
+ * Synchronous: the value lands in *out.  Evaluation only, never part of a step. */
 int ddh_strehl(ddh_state *s, const float *phi_true_dev, float *out);
 
 /* Advance `count` states by one frame each: the states are grouped by grid size and path

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libddh.so")
 SOURCES = ["ddh_step.cu", "ddh_step_l2.cu", "ddh_post.cu", "ddh_selftest.cu", "ddh_api.cu", "ddh_service.cu",
-           "ddh_adjoint.cu"]
+           "ddh_adjoint.cu", "ddh_eval.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

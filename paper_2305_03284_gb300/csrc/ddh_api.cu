@@ -16,6 +16,7 @@
 
 #include "../../include/ddh.h"
 #include "ddh_internal.h"
+#include "ddh_eval.cuh"
 #include "ddh_kernels.cuh"
 
 namespace ddh {
@@ -829,7 +830,28 @@ int ddh_noise_estimate(ddh_state* s, float* out) {
 void* ddh_state_stream(const ddh_state* s) { return s ? static_cast<void*>(s->stream) : nullptr; }
 
 int ddh_strehl(ddh_state* s, const float* phi_true_dev, float* out) {
-  if (s == nullptr || phi_true_dev == nullptr || out == nullptr || !cluster_n(s->prm.n)) return DDH_EINVAL;
+  if (s == nullptr || phi_true_dev == nullptr || out == nullptr) return DDH_EINVAL;
+  if (!cluster_n(s->prm.n)) {
+    if (s->prm.n != 512 || s->l2scratch == nullptr) return DDH_EINVAL;
+    // 512 x 512: a row and a column pass through the stream's first scratch image (scratch
+    // between steps), the maximum gathered as float bits in the stream's scalar
+    DDH_ON_DEVICE(s->device);
+    ddh::StrehlL2Args a{};
+    a.phi_est = s->phi;
+    a.phi_true = phi_true_dev;
+    a.work = ddh::l2_stream_view(s->l2scratch, s->prm.n).fa;
+    a.max_bits = reinterpret_cast<unsigned*>(s->scalar);
+    a.tw = s->tw;
+    a.ap_lim = s->kp.ap_lim;
+    DDH_CUDA(cudaMemsetAsync(s->scalar, 0, sizeof(float), s->stream));
+    DDH_CUDA(ddh::launch_strehl_l2(s->prm.n, a, s->stream));
+    float m = 0.f;
+    DDH_CUDA(cudaMemcpyAsync(&m, s->scalar, sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    const int rc = check_status(s);
+    if (rc != DDH_OK) return rc;
+    *out = m * static_cast<float>(1.0 / (static_cast<double>(s->ap_count) * s->ap_count));
+    return DDH_OK;
+  }
   DDH_ON_DEVICE(s->device);
   ddh::StrehlArgs a{};
   a.phi_est = s->phi;

@@ -343,6 +343,29 @@ def test_strehl_matches_oracle(ddh):
     assert abs(s.strehl(cu(ph[0].astype(np.float32))) - 1.0) < 1e-5
 
 
+@pytest.mark.parametrize("n", [256, 512])
+def test_strehl_matches_oracle_large_grids(ddh, n):
+    """The Strehl evaluation at 256^2 (cluster kernel) and 512^2 (row and column launches through
+    the staged stream's scratch) against the oracle's, for a perturbed estimate and for the true
+    phase (Strehl 1)."""
+    cfg = sy.config_single_256() if n == 256 else sy.config_batched(frames=1)[56]
+    assert cfg.n == n
+    st, ys, ph, p = make(ddh, cfg, 1)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    s = ddh.Stream(p)
+    rng = np.random.default_rng(5)
+    est = np.where(a, ph[0] + 0.3 * rng.standard_normal(ph[0].shape), 0.0).astype(np.float32)
+    zeros = cu(np.zeros((n, n), np.float32))
+    s.set_state(zeros, cu(est), 0)
+    got = s.strehl(cu(ph[0].astype(np.float32)))
+    ref = o.strehl(est.astype(np.float64), ph[0].astype(np.float32).astype(np.float64), a)
+    print(f"{n}^2 Strehl: library {got:.6f}, oracle {ref:.6f}")
+    assert abs(got - ref) < 1e-5 * ref
+    s.set_state(zeros, cu(ph[0].astype(np.float32) * a), 0)
+    assert abs(s.strehl(cu(ph[0].astype(np.float32))) - 1.0) < 1e-5
+    s.close()
+
+
 # -------------------------------------------------------------------------- API behaviour
 def test_batch_equals_individual_steps(ddh):
     cfgs = [sy.config_single_64(), sy.config_batched(4)[0], sy.config_single_256(4), sy.config_batched(4)[1]]
@@ -548,6 +571,22 @@ def test_parity_512_l2_staged(ddh, over):
     assert rel_l2_phase(gphi[-1], ophi[-1], a) < TOL
     assert rel_l2(gr[-1], orr[-1]) < TOL
     assert np.all(gphi[-1][~a] == 0.0)
+
+
+def test_parity_512_free_running_30_frames_tiled_phase(ddh):
+    """A 512^2 stream of the 64-stream workload (L2-staged kernels, the only path at this size)
+    free-running for 30 frames with 2x2 phase tiles: phi, r and the Strehl trace against the
+    FP64 oracle."""
+    cfg = sy.config_batched(frames=30)[56]
+    assert cfg.n == 512
+    st, ys, ph, p = make(ddh, cfg, 30, phase_block=2)
+    ph = ph.astype(np.float32).astype(np.float64)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    gphi, gr, gS = _run_free(ddh, p, ys, ph)
+    ophi, orr, oS = _run_oracle(oracle_params(p), ys, ph)
+    e = (rel_l2_phase(gphi[-1], ophi[-1], a), rel_l2(gr[-1], orr[-1]), rel_l2(gS, oS))
+    print(f"512^2, 30 free-running frames, tiled phase: phi {e[0]:.2e}, r {e[1]:.2e}, Strehl trace {e[2]:.2e}")
+    assert e[0] < TOL and e[1] < TOL and e[2] < TOL, e
 
 
 # ------------------------------------------- 128^2 and 256^2 on the L2-staged path (exec_path)
