@@ -59,15 +59,16 @@ typedef struct ddh_params {
                            8-neighbour tiles; the tile-phase M-step then minimises
                            -(2/sigma^2) sum_t |v_t| cos(phi_t - angle v_t) + prior by
                            `phase_sweeps` majorised 4-colour ICD sweeps from the tile angles.
-                           0 (default): flat prior.  > 0 needs phase_block 2 or 4, n_k = 1,
-                           N <= 256 and the cluster kernel (exec_path); in batches and the
+                           0 (default): flat prior.  > 0 needs phase_block 2 or 4, n_k = 1 and
+                           a pupil of at most 128 x 128 tiles (any grid and exec_path, e.g.
+                           512^2 with a 256 px pupil in 2 x 2 tiles); in batches and the
                            service the streams that use it share one post-step launch */
   int phase_sweeps;     /* ICD sweeps of that M-step, 1..16 (0 counts as the default, 2) */
   int noise_update;     /* 1: sigma^2 (noise_var above is then its starting value) is
                            re-estimated once per frame, after the frame's last EM iteration, by
                            its EM M-step (1/|P|) sum_pupil |y~ - e^{j phi} F mu|^2 + mean(C);
-                           floored at 1e-6.  N <= 256 on the cluster kernel (also in batches
-                           and the service), no adjoint.  0 (default): sigma^2 fixed */
+                           floored at 1e-6.  Any grid and exec_path, also in batches and the
+                           service; no adjoint.  0 (default): sigma^2 fixed */
   int exec_path;        /* which kernels run this stream's steps (same method, same readings;
                            results agree within FP32 rounding, not bit for bit):
                            DDH_PATH_DEFAULT (0): the cluster kernel for N <= 256, the L2-staged

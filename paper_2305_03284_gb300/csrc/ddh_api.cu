@@ -165,6 +165,23 @@ int64_t aperture_count(int n, int64_t lim) {
   return c;
 }
 
+// The pupil's box in G x G tiles, from the integer pupil test: a column x holds pupil pixels iff
+// (2x - (n-1))^2 + min_y (2y - (n-1))^2 <= ap_lim (the box is square, the pupil centred).
+void tile_box(int n, int64_t ap_lim, int gs, int* t_lo, int* nt) {
+  int64_t miny = INT64_MAX;
+  for (int y = 0; y < n; ++y) miny = std::min<int64_t>(miny, int64_t(2 * y - (n - 1)) * (2 * y - (n - 1)));
+  int lo = n, hi = -1;
+  for (int x = 0; x < n; ++x) {
+    const int64_t dx = 2 * x - (n - 1);
+    if (dx * dx + miny <= ap_lim) {
+      lo = std::min(lo, x);
+      hi = std::max(hi, x);
+    }
+  }
+  *t_lo = hi >= lo ? lo >> gs : 0;
+  *nt = hi >= lo ? (hi >> gs) - *t_lo + 1 : 0;
+}
+
 int validate(const ddh_params* p) {
   if (p == nullptr || !supported_n(p->n)) return DDH_EINVAL;
   if (!(p->aperture_diam > 0.f && p->aperture_diam <= static_cast<float>(p->n))) return DDH_EINVAL;
@@ -181,11 +198,15 @@ int validate(const ddh_params* p) {
   if (!(p->phase_prior >= 0.f && std::isfinite(p->phase_prior))) return DDH_EINVAL;
   if (p->phase_sweeps < 0 || p->phase_sweeps > 16) return DDH_EINVAL;
   if (p->noise_update != 0 && p->noise_update != 1) return DDH_EINVAL;
-  if (p->phase_prior > 0.f && (p->phase_block == 1 || p->n_k != 1 || p->n > 256)) return DDH_EINVAL;
-  if (p->noise_update && p->n > 256) return DDH_EINVAL;
+  if (p->phase_prior > 0.f && (p->phase_block == 1 || p->n_k != 1)) return DDH_EINVAL;
   if (p->exec_path < DDH_PATH_DEFAULT || p->exec_path > DDH_PATH_STAGED) return DDH_EINVAL;
   if (p->exec_path == DDH_PATH_CLUSTER && !cluster_n(p->n)) return DDH_EINVAL;
-  if (staged_path(*p) && (!staged_n(p->n) || p->phase_prior > 0.f || p->noise_update)) return DDH_EINVAL;
+  if (staged_path(*p) && !staged_n(p->n)) return DDH_EINVAL;
+  if (p->phase_prior > 0.f) {  // the prior's tile box must fit the post kernel
+    int t_lo = 0, nt = 0;
+    tile_box(p->n, aperture_limit(p->aperture_diam), p->phase_block == 4 ? 2 : 1, &t_lo, &nt);
+    if (nt > ddh::kPostMaxTiles) return DDH_EINVAL;
+  }
   return DDH_OK;
 }
 
@@ -213,7 +234,7 @@ ddh::PostArgs post_args(const ddh_state* s) {
   a.n = n;
   a.gs = gs;
   a.ap_lim = s->kp.ap_lim;
-  a.ctas = n / ddh::kRowsPerCta;
+  a.ctas = s->staged ? n / 8 : n / ddh::kRowsPerCta;  // blocks that write partial sums
   a.prior = s->prm.phase_prior > 0.f ? 1 : 0;
   a.sweeps = s->prm.phase_sweeps > 0 ? s->prm.phase_sweeps : 2;
   a.noise_update = s->prm.noise_update;
@@ -221,19 +242,7 @@ ddh::PostArgs post_args(const ddh_state* s) {
   a.inv_ap_count = s->ap_count > 0 ? static_cast<float>(1.0 / static_cast<double>(s->ap_count)) : 0.f;
   a.inv_m = static_cast<float>(1.0 / (static_cast<double>(n) * n));
   a.nv_floor = 1e-6f;
-  // a column x holds pupil pixels iff (2x - (n-1))^2 + min_y (2y - (n-1))^2 <= ap_lim
-  int64_t miny = INT64_MAX;
-  for (int y = 0; y < n; ++y) miny = std::min<int64_t>(miny, int64_t(2 * y - (n - 1)) * (2 * y - (n - 1)));
-  int lo = n, hi = -1;
-  for (int x = 0; x < n; ++x) {
-    const int64_t dx = 2 * x - (n - 1);
-    if (dx * dx + miny <= a.ap_lim) {
-      lo = std::min(lo, x);
-      hi = std::max(hi, x);
-    }
-  }
-  a.t_lo = hi >= lo ? lo >> gs : 0;
-  a.nt = hi >= lo ? (hi >> gs) - a.t_lo + 1 : 0;
+  tile_box(n, a.ap_lim, gs, &a.t_lo, &a.nt);
   return a;
 }
 
@@ -296,6 +305,10 @@ ddh::L2Stream l2_view(ddh_state* s, const void* y) {
   v.r = s->r;
   v.phi = s->phi;
   v.status = s->status;
+  if (s->aux != nullptr && aux_needed(s->prm)) {  // side outputs for the post kernel
+    v.aux = s->aux;
+    v.aux_tiles = s->prm.phase_prior > 0.f ? 1 : 0;
+  }
   return v;
 }
 
@@ -315,6 +328,7 @@ int enqueue(ddh_state* s, const void* y, float* trace, bool y_host = false, floa
     lb.tw = s->tw;
     lb.count = 1;
     DDH_CUDA(ddh::launch_step_l2(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], lb, s->kp.n_k, s->stream));
+    if (lb.st[0].aux != nullptr) DDH_CUDA(ddh::launch_post(post_args(s), s->stream));
     s->frame += 1;
     return DDH_OK;
   }
@@ -347,10 +361,15 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
     int n;
     bool staged;
   };
+  ddh_state* lb_states[ddh::kMaxBatchL2];  // the states of the staged launch being formed
   const Group order[kGroups] = {{512, true}, {256, true}, {128, true}, {32, false},
                                 {64, false}, {128, false}, {256, false}};
   auto member = [&](int i, const Group& gr) { return states[i]->prm.n == gr.n && states[i]->staged == gr.staged; };
-  const bool persist = g_persistent[dev] != 0;
+  // streams with the post-step M-steps keep the chained launches (their post kernel follows
+  // each launch chunk)
+  bool aux_staged = false;
+  for (int i = 0; i < count; ++i) aux_staged |= states[i]->staged && states[i]->aux != nullptr && aux_needed(states[i]->prm);
+  const bool persist = g_persistent[dev] != 0 && !aux_staged;
   int groups = 0;
   bool any_staged = false;
   for (const Group& gr : order)
@@ -437,27 +456,47 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
     const int sched = g_schedule[dev][n_slot(n)];
     if (gr.staged) {
       ddh::L2Batch lb{};
+      ddh::PostBatch pb{};  // the chunk's streams with the tile-phase prior or the sigma^2 M-step
       lb.ytab = ytab;
       lb.count = 0;
+      auto flush = [&]() -> int {  // the chunk's step, then the post kernels of its aux streams
+        DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
+        pb.count = 0;
+        for (int j = 0; j < lb.count; ++j) {
+          if (lb.st[j].aux == nullptr) continue;
+          pb.a[pb.count++] = post_args(lb_states[j]);
+          if (pb.count == ddh::kMaxBatch) {
+            DDH_CUDA(ddh::launch_post_batch(pb, st));
+            pb.count = 0;
+          }
+        }
+        if (pb.count > 0) DDH_CUDA(ddh::launch_post_batch(pb, st));
+        lb.count = 0;
+        return DDH_OK;
+      };
       for (int i = 0; i < count; ++i) {
         ddh_state* s = states[i];
         if (!member(i, gr)) continue;
         if (lb.count > 0 && s->kp.n_k != lb.prm[0].n_k) {  // one EM-iteration count per launch
-          DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
-          lb.count = 0;
+          const int rc = flush();
+          if (rc != DDH_OK) return rc;
         }
         if (lb.count == 0) lb.ytab_base = i;
         lb.prm[lb.count] = s->kp;
         lb.st[lb.count] = l2_view(s, ys != nullptr ? ys[i] : nullptr);
+        lb_states[lb.count] = s;
         lb.tw = s->tw;
         ++lb.count;
         const bool next_same = i + 1 < count && member(i + 1, gr);
         if (lb.count == staged_chunk(dev, n) || (ytab != nullptr && !next_same)) {
-          DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
-          lb.count = 0;
+          const int rc = flush();
+          if (rc != DDH_OK) return rc;
         }
       }
-      if (lb.count > 0) DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
+      if (lb.count > 0) {
+        const int rc = flush();
+        if (rc != DDH_OK) return rc;
+      }
     } else {
       ddh::StepBatch b{};
       ddh::PostBatch pb{};  // the chunk's streams with the tile-phase prior or the sigma^2 M-step

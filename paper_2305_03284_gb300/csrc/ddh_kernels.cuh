@@ -51,12 +51,16 @@ struct FrameArgs {
 //   aux[0]                     sigma^2 in use: read by the step kernel after its dependency
 //                              wait, replaced by the post kernel when sigma^2 is re-estimated
 //   aux[1]                     1 when the step accepted the frame, 0 when it dropped it
-//   aux[kAuxPart + 2k, + 1]    CTA k's sums: pupil residual at the tile angles, sum of C
+//   aux[kAuxPart + 2k, + 1]    block k's sums (a cluster kernel's CTA k, or the k-th 8-row and
+//                              8-column block of the L2-staged kernels; at most kAuxParts):
+//                              pupil residual at the tile angles, sum of C
 //   aux[kAuxTiles ...]         float4 per tile of the N/G x N/G grid (row-major), written for
 //                              the tiles that hold a pupil pixel: (Re v_t, Im v_t, E_t, 0),
 //                              v_t = sum a y~ conj(z), E_t = sum a (|y~|^2 + |z|^2)
 constexpr int kAuxPart = 16;
-constexpr int kAuxTiles = 64;
+constexpr int kAuxParts = 64;
+constexpr int kAuxTiles = kAuxPart + 2 * kAuxParts;
+constexpr int kPostMaxTiles = 128;  // the tile-phase prior's box: at most 128 x 128 tiles
 inline size_t aux_floats(int n) { return kAuxTiles + size_t(4) * (n / 2) * (n / 2); }
 
 struct PostArgs {
@@ -102,6 +106,8 @@ struct L2Stream {
   float* beta;    // 4 images of pair weights: E, S, SE, SW
   float* part;    // row-block statistics, then the combined statistics
   int* flag;      // frame dropped (non-finite or zero variance)
+  float* aux;     // side buffer of the post-step M-steps (layout above), or null
+  int aux_tiles;  // with aux: 1 = tile sums for the phase prior, 0 = residual partial sums
   unsigned* bar;  // grid-barrier words of a persistent launch led by this stream (zeroed at init)
 };
 

@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kPostCluster = 8;   // CTAs; the tile box's rows are split into 8 contiguous blocks
 constexpr int kPostThreads = 256;
-constexpr int kPostCols = 128;    // the box is at most 128 x 128 tiles (N <= 256, G >= 2)
+constexpr int kPostCols = kPostMaxTiles;  // the prior's tile box is at most 128 x 128 tiles
 constexpr int kPostRows = kPostCols / kPostCluster;
 
 __global__ void __cluster_dims__(kPostCluster, 1, 1) __launch_bounds__(kPostThreads)
@@ -155,7 +155,7 @@ __global__ void __cluster_dims__(kPostCluster, 1, 1) __launch_bounds__(kPostThre
   }
   if (a.noise_update && q == 0) {
     // the step kernel's partial sums are fetched in parallel, then added in CTA order
-    __shared__ float pa[2 * 16];
+    __shared__ float pa[2 * kAuxParts];
     if (tid < 2 * a.ctas) pa[tid] = aux[kAuxPart + tid];
     __syncthreads();
     if (tid == 0) {
@@ -176,7 +176,7 @@ __global__ void __cluster_dims__(kPostCluster, 1, 1) __launch_bounds__(kPostThre
 cudaError_t launch_post_batch(const PostBatch& b, cudaStream_t st) {
   if (b.count < 1 || b.count > kMaxBatch) return cudaErrorInvalidValue;
   for (int i = 0; i < b.count; ++i)
-    if (b.a[i].nt > kPostCols) return cudaErrorInvalidValue;
+    if ((b.a[i].prior && b.a[i].nt > kPostCols) || b.a[i].ctas > kAuxParts) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kPostCluster, b.count, 1);
   cfg.blockDim = dim3(kPostThreads, 1, 1);

@@ -98,7 +98,10 @@ __device__ __forceinline__ void l2_stage_stats(const L2Batch& b, int sid, int bx
     }
     float* o = S.part + 8 * bx;
     o[0] = m_a.x; o[1] = m_a.y; o[2] = q_a; o[3] = t0; o[4] = t1; o[5] = t2; o[6] = t3; o[7] = 0.f;
-    if (bx == 0) *S.flag = 0;
+    if (bx == 0) {
+      *S.flag = 0;
+      if (S.aux != nullptr) S.aux[1] = 0.f;  // set again by the phase step of an accepted frame
+    }
   }
 }
 
@@ -238,11 +241,16 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
 
 // ---- s3: column IFFT, r-init + E-step, column FFT of mu; transposed store into fa ----------
 template <int N, int V>
-__device__ __forceinline__ void l2_stage_cols(const L2Batch& b, const float2* twg, int sid, int bx, int first, unsigned char* smem) {
+__device__ __forceinline__ void l2_stage_cols(const L2Batch& b, const float2* twg, int sid, int bx, int first, int last,
+                                              unsigned char* smem) {
   const L2Stream& S = b.st[sid];
   const KParams& P = b.prm[sid];
   grid_dep_wait();
   if (frame_dropped(S)) return;
+  // sigma^2 of this frame: the stream's running estimate when it is re-estimated (written by the
+  // previous frame's post kernel), else the parameter
+  const float nv = S.aux != nullptr ? S.aux[0] : P.noise_var;
+  const bool aux_out = S.aux != nullptr && last;  // side outputs of the frame's last iteration
   float2* tw = reinterpret_cast<float2*>(smem);
   // column tiles with stride N + 4: the transposed accesses (8 columns x 4 rows per warp) hit
   // 32 distinct banks (16 bank pairs for the complex tile)
@@ -286,19 +294,31 @@ __device__ __forceinline__ void l2_stage_cols(const L2Batch& b, const float2* tw
   float* sc = stile + warp * CW;
   fft_row<N, +1, V>(cb, tw, lane);
   const float invN = 1.f / static_cast<float>(N);
+  float csum = 0.f;  // sum of the posterior variances C = sigma^2 w (side output)
   for (int rho = lane; rho < N; rho += 32) {
     const float2 bb = c_scale(cb[swz(rho)], invN);
     const float rp = rc[rho];
     const float ri = first ? fmaxf(fmaf(P.lam1, rp, P.lam_alpha * c_abs2(bb)), P.r_floor) : rp;
-    const float w = ri / (ri + P.noise_var);
+    const float w = ri / (ri + nv);
     const float2 mu = c_scale(bb, w);
     cb[swz(rho)] = mu;
     rc[rho] = ri;
-    sc[rho] = fmaf(P.noise_var, w, c_abs2(mu));
+    sc[rho] = fmaf(nv, w, c_abs2(mu));
+    if (aux_out) csum += nv * w;
+  }
+  __shared__ float cred[kTc];
+  if (aux_out) {
+    csum = warp_sum(csum);
+    if (lane == 0) cred[warp] = csum;
   }
   __syncwarp();
   fft_row<N, -1, V>(cb, tw, lane);
   __syncthreads();
+  if (aux_out && threadIdx.x == 0) {  // this block's sum, its columns in order
+    float sc0 = 0.f;
+    for (int w2 = 0; w2 < kTc; ++w2) sc0 += cred[w2];
+    S.aux[kAuxPart + 2 * bx + 1] = sc0;
+  }
   for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {
     const int rho = i / kTc, c = i - rho * kTc;
     const size_t gi = static_cast<size_t>(rho) * N + x0 + c;
@@ -311,15 +331,16 @@ __device__ __forceinline__ void l2_stage_cols(const L2Batch& b, const float2* tw
 }
 
 template <int N, int V>
-__global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first) {
+__global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first, int last) {
   extern __shared__ __align__(128) unsigned char smem[];
   grid_dep_launch();
-  l2_stage_cols<N, V>(b, b.tw, blockIdx.y, blockIdx.x, first, smem);
+  l2_stage_cols<N, V>(b, b.tw, blockIdx.y, blockIdx.x, first, last, smem);
 }
 
 // ---- s4: row FFT of mu and phase M-step ------------------------------------------------------
 template <int N, int V>
-__device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2* twg, int sid, int bx, unsigned char* smem) {
+__device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2* twg, int sid, int bx, int last,
+                                                  unsigned char* smem) {
   const L2Stream& S = b.st[sid];
   const KParams& P = b.prm[sid];
   grid_dep_wait();
@@ -330,6 +351,8 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
   // 16 bank pairs
   constexpr int RW = N + 4;
   float2* rows = tw + N;  // kTr rows x RW
+  float* ev = reinterpret_cast<float*>(rows + kTr * RW);  // kTr rows x N: a (|y~|^2 + |z|^2)
+  const bool aux_out = S.aux != nullptr && last;          // side outputs of the frame's last iteration
   for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = twg[i];
   const float* st = S.part + 8 * (N / kT);
   const float2 ymean = make_float2(st[0], st[1]);
@@ -361,16 +384,20 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
   for (int j = 0; j < PER; ++j) {
     const int x = lane + 32 * j;
     float2 v = make_float2(0.f, 0.f);
+    float e = 0.f;
     if (row_ap && ap_dist2(x, N) + dy2 <= P.ap_lim) {
       const float2 z = c_scale(rb[swz(x)], invN);
       const float2 yt = c_scale(c_sub(yv[j], ymean), scale);
       v = make_float2(fmaf(yt.x, z.x, yt.y * z.y), fmaf(yt.y, z.x, -yt.x * z.y));
+      if (aux_out) e = c_abs2(yt) + c_abs2(z);
     }
-    for (int o = 1; o < G; o <<= 1) {
+    for (int o = 1; o < G; o <<= 1) {  // sum over the G consecutive x of the tile
       v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
       v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      if (aux_out) e += __shfl_xor_sync(0xffffffffu, e, o);
     }
     rb[swz(x)] = v;
+    if (aux_out) ev[warp * N + x] = e;
   }
   __syncthreads();
   const int l0 = warp & ~(G - 1);
@@ -382,13 +409,48 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
       if (v.x != 0.f || v.y != 0.f) pr[x] = atan2f(v.y, v.x);  // else phi' is kept
     }
   }
+  if (aux_out) {
+    // Side outputs for the post kernel, per G x G tile of this block's rows: the tile sums v_t
+    // and E_t.  With the phase prior they go to the tile grid; otherwise the tile phase is
+    // angle(v_t) and the pupil residual |y~ - e^{j phi} z|^2 over the tile is E_t - 2 |v_t|,
+    // summed here.  Then this block's residual, its warps in order.
+    const int NT = N >> gs;
+    float res = 0.f;
+    for (int t = threadIdx.x; t < (kTr >> gs) * NT; t += kRowThreads) {
+      const int tl = t / NT, tx = t - tl * NT;
+      const int lt = tl << gs, xt = tx << gs;
+      float2 v = rows[lt * RW + swz(xt)];
+      float e = ev[lt * N + xt];
+      for (int j = 1; j < G; ++j) {
+        v = c_add(v, rows[(lt + j) * RW + swz(xt)]);
+        e += ev[(lt + j) * N + xt];
+      }
+      if (S.aux_tiles) {
+        const int T = (kTr * bx + lt) >> gs;
+        if (tile_in_pupil(T, tx, gs, N, P.ap_lim))
+          reinterpret_cast<float4*>(S.aux + kAuxTiles)[T * NT + tx] = make_float4(v.x, v.y, e, 0.f);
+      } else {
+        res += e - 2.f * sqrtf(fmaf(v.x, v.x, v.y * v.y));
+      }
+    }
+    __shared__ float rred[kTr];
+    res = warp_sum(res);
+    if (lane == 0) rred[warp] = res;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float sr = 0.f;
+      for (int w2 = 0; w2 < kTr; ++w2) sr += rred[w2];
+      S.aux[kAuxPart + 2 * bx] = sr;
+      if (bx == 0) S.aux[1] = 1.f;  // the frame was accepted
+    }
+  }
 }
 
 template <int N, int V>
-__global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_constant__ L2Batch b) {
+__global__ void __launch_bounds__(kRowThreads, N == 512 ? 4 : 6) k_l2_rows_fwd(const __grid_constant__ L2Batch b, int last) {
   extern __shared__ __align__(128) unsigned char smem[];
   grid_dep_launch();
-  l2_stage_rows_fwd<N, V>(b, b.tw, blockIdx.y, blockIdx.x, smem);
+  l2_stage_rows_fwd<N, V>(b, b.tw, blockIdx.y, blockIdx.x, last, smem);
 }
 
 // ---- s5: surrogate pair weights at the sweep's entry values ---------------------------------
@@ -479,7 +541,7 @@ __global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Bat
 }
 
 template <int N>
-constexpr size_t rows_smem() { return sizeof(float2) * (N + kTr * (N + 4)); }
+constexpr size_t rows_smem() { return sizeof(float2) * (N + kTr * (N + 4)) + sizeof(float) * kTr * N; }
 template <int N>
 constexpr size_t cols_smem() { return sizeof(float2) * (N + kTc * (N + 4)) + 2 * sizeof(float) * kTc * (N + 4); }
 
@@ -511,8 +573,9 @@ cudaError_t l2_step(const L2Batch& b, int n_k, cudaStream_t st) {
   for (int it = 0; it < n_k && e == cudaSuccess; ++it) {
     const int first = it == 0 ? 1 : 0;
     e = launch_pdl(k_l2_rows_inv<N, V>, rgrid, rblk, rows_smem<N>(), st, b, first);
-    if (e == cudaSuccess) e = launch_pdl(k_l2_cols<N, V>, cgrid2, cblk, cols_smem<N>(), st, b, first);
-    if (e == cudaSuccess) e = launch_pdl(k_l2_rows_fwd<N, V>, rgrid, rblk, rows_smem<N>(), st, b);
+    const int last = it == n_k - 1 ? 1 : 0;
+    if (e == cudaSuccess) e = launch_pdl(k_l2_cols<N, V>, cgrid2, cblk, cols_smem<N>(), st, b, first, last);
+    if (e == cudaSuccess) e = launch_pdl(k_l2_rows_fwd<N, V>, rgrid, rblk, rows_smem<N>(), st, b, last);
     if (e == cudaSuccess) e = launch_pdl(k_l2_weights<N>, wgrid, dim3(256), 0, st, b);
     for (int c = 0; c < 4 && e == cudaSuccess; ++c) e = launch_pdl(k_l2_colour<N>, cgrid, dim3(256), 0, st, b, c);
   }
@@ -570,13 +633,14 @@ __device__ __noinline__ void pi_rows_inv(const L2Batch& b, const float2* tw, int
   l2_stage_rows_inv<N, 0>(b, tw, sid, bx, first, smem);
 }
 template <int N>
-__device__ __noinline__ void pi_cols(const L2Batch& b, const float2* tw, int sid, int bx, int first,
+__device__ __noinline__ void pi_cols(const L2Batch& b, const float2* tw, int sid, int bx, int first, int last,
                                      unsigned char* smem) {
-  l2_stage_cols<N, 0>(b, tw, sid, bx, first, smem);
+  l2_stage_cols<N, 0>(b, tw, sid, bx, first, last, smem);
 }
 template <int N>
-__device__ __noinline__ void pi_rows_fwd(const L2Batch& b, const float2* tw, int sid, int bx, unsigned char* smem) {
-  l2_stage_rows_fwd<N, 0>(b, tw, sid, bx, smem);
+__device__ __noinline__ void pi_rows_fwd(const L2Batch& b, const float2* tw, int sid, int bx, int last,
+                                         unsigned char* smem) {
+  l2_stage_rows_fwd<N, 0>(b, tw, sid, bx, last, smem);
 }
 template <int N>
 __device__ __noinline__ void pi_weights(const L2Batch& b, int sid, int bx) { l2_stage_weights<N>(b, sid, bx); }
@@ -586,13 +650,13 @@ __device__ __noinline__ void pi_colour(const L2Batch& b, int sid, int bx, int c)
 }
 
 template <int N>
-__device__ __forceinline__ void persist_item(const L2Batch& b, const float2* tw, int stage, int first, int sid,
-                                             int bx, unsigned char* smem) {
+__device__ __forceinline__ void persist_item(const L2Batch& b, const float2* tw, int stage, int first, int last,
+                                             int sid, int bx, unsigned char* smem) {
   switch (stage) {
     case 0: pi_stats<N>(b, sid, bx); break;
     case 1: pi_rows_inv<N>(b, tw, sid, bx, first, smem); break;
-    case 2: pi_cols<N>(b, tw, sid, bx, first, smem); break;
-    case 3: pi_rows_fwd<N>(b, tw, sid, bx, smem); break;
+    case 2: pi_cols<N>(b, tw, sid, bx, first, last, smem); break;
+    case 3: pi_rows_fwd<N>(b, tw, sid, bx, last, smem); break;
     case 4: pi_weights<N>(b, sid, bx); break;
     default: pi_colour<N>(b, sid, bx, stage - 5); break;
   }
@@ -638,7 +702,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_l2_persistent(const __gr
   extern __shared__ __align__(128) unsigned char smem[];
   grid_dep_wait();
   for (int it = 0; it < p.n_k; ++it) {
-    const int first = it == 0 ? 1 : 0;
+    const int first = it == 0 ? 1 : 0, last = it == p.n_k - 1 ? 1 : 0;
     for (int stage = it == 0 ? 0 : 1; stage < 9; ++stage) {
       int total = 0;
       for (int g = 0; g < p.groups; ++g) total += p.count[g] * stage_items(stage, p.n[g]);
@@ -652,9 +716,9 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_l2_persistent(const __gr
         const int per = stage_items(stage, p.n[g]);
         const int sid = p.first[g] + local / per, bx = local % per;
         switch (p.n[g]) {
-          case 512: persist_item<512>(p.b, p.tw[g], stage, first, sid, bx, smem); break;
-          case 256: persist_item<256>(p.b, p.tw[g], stage, first, sid, bx, smem); break;
-          default: persist_item<128>(p.b, p.tw[g], stage, first, sid, bx, smem); break;
+          case 512: persist_item<512>(p.b, p.tw[g], stage, first, last, sid, bx, smem); break;
+          case 256: persist_item<256>(p.b, p.tw[g], stage, first, last, sid, bx, smem); break;
+          default: persist_item<128>(p.b, p.tw[g], stage, first, last, sid, bx, smem); break;
         }
         __syncthreads();  // the item's shared scratch is free for the next item
       }

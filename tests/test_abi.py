@@ -57,10 +57,11 @@ def test_default_params_match_oracle(lib, n, d, snr):
 @pytest.mark.parametrize("over", [{"phase_prior": 1.0}, {"phase_prior": 1.0, "phase_block": 2, "n_k": 2},
                                   {"phase_prior": -1.0}, {"phase_prior": float("nan"), "phase_block": 2},
                                   {"phase_sweeps": 17}, {"phase_sweeps": -1}, {"noise_update": 2},
-                                  {"n": 512, "aperture_diam": 256.0, "noise_update": 1},
-                                  {"n": 512, "aperture_diam": 256.0, "phase_prior": 1.0, "phase_block": 2}])
+                                  {"n": 512, "aperture_diam": 512.0, "phase_prior": 1.0, "phase_block": 2},
+                                  {"n": 64, "exec_path": 2, "noise_update": 1}])
 def test_init_rejects_unsupported_prior_and_noise_options(lib, over):
-    """Parameter validation runs before any CUDA call, so it is checked without a GPU."""
+    """Parameter validation runs before any CUDA call, so it is checked without a GPU (a 512 px
+    pupil in 2x2 tiles is a 256-tile box, beyond the prior's 128; 64^2 has no staged kernels)."""
     from paper_2305_03284_gb300._lib import DdhParams, DDH_EINVAL
     p = DdhParams()
     n = over.get("n", 64)

@@ -137,8 +137,8 @@ def test_checkpoint_carries_the_sigma2_estimate(ddh):
 
 
 def test_refused_where_unsupported(ddh):
-    """The adjoint refuses the post-step M-steps; so do a prior without tiles, with n_k > 1, on
-    the 512^2 path or on the staged kernels."""
+    """The adjoint refuses the post-step M-steps; so do a prior without tiles, with n_k > 1, or
+    whose tile box exceeds the post kernel's 128 x 128 (a 512 px pupil in 2x2 tiles)."""
     cfg = sy.config_single_64()
     st, ys, ph, p = make(ddh, cfg, 1, noise_update=1)
     for over in ({"phase_prior": 1.0}, {"phase_prior": 1.0, "phase_block": 2, "n_k": 2},
@@ -146,9 +146,7 @@ def test_refused_where_unsupported(ddh):
         with pytest.raises(ddh.DdhError):
             ddh.Stream(ddh.default_params(64, 32.0, 10.0, **over))
     with pytest.raises(ddh.DdhError):
-        ddh.Stream(ddh.default_params(512, 256.0, 10.0, noise_update=1))
-    with pytest.raises(ddh.DdhError):
-        ddh.Stream(ddh.default_params(256, 128.0, 10.0, phase_block=2, phase_prior=5.0, exec_path=2))
+        ddh.Stream(ddh.default_params(512, 512.0, 10.0, phase_block=2, phase_prior=5.0))
     s = ddh.Stream(p)
     L = ddh.lib()
     z = torch.zeros((64, 64), device="cuda")
@@ -200,3 +198,69 @@ def test_batches_and_service_equal_solo_steps_with_the_post_step_m_steps(ddh):
         assert torch.equal(s1.phase(), svc.phase(k)), k
         assert torch.equal(s1.reflectance(), svc.reflectance(k)), k
     svc.close()
+
+
+@pytest.mark.parametrize("n,frames,over", [
+    (256, 30, {"phase_block": 2, "phase_prior": 10.0, "noise_update": 1}),
+    (512, 10, {"phase_block": 2, "phase_prior": 20.0, "noise_update": 1}),
+    (256, 4, {"noise_update": 1}),
+])
+def test_staged_kernels_with_the_post_step_m_steps(ddh, n, frames, over):
+    """The L2-staged kernels' side outputs (tile sums, residual and posterior-variance partials
+    per 8-row / 8-column block) feed the same post-step kernel: free-running against the oracle
+    (phase, reflectance, Strehl trace and the sigma^2 estimate); per-pixel phase only over a few
+    frames, where the iteration does not contract."""
+    from paper_2305_03284_gb300 import _lib
+    cfg = sy.config_single_256() if n == 256 else sy.config_batched(frames=frames)[56]
+    assert cfg.n == n
+    st, ys, ph, p = make(ddh, cfg, frames, exec_path=_lib.DDH_PATH_STAGED, **over)
+    ph = ph.astype(np.float32).astype(np.float64)
+    prm = oracle_params(p)
+    a = o.aperture(cfg.n, cfg.aperture_diam)
+    s = ddh.Stream(p)
+    ost = o.init_state(cfg.n)
+    gS, oS, gnv, onv = [], [], [], []
+    for i in range(frames):
+        s.step(cu(ys[i]))
+        gS.append(s.strehl(cu(ph[i].astype(np.float32))))
+        gnv.append(s.noise_estimate())
+        ost, _ = o.step(ost, ys[i], prm)
+        oS.append(o.strehl(ost.phi, ph[i], a))
+        onv.append(ost.noise_var)
+    e = (rel_l2_phase(np32(s.phase()), ost.phi, a), rel_l2(np32(s.reflectance()), ost.r),
+         rel_l2(np.array(gS), np.array(oS)), rel_l2(np.array(gnv), np.array(onv)))
+    print(f"staged {n}^2 {over}, {frames} frames: phi {e[0]:.2e} r {e[1]:.2e} Strehl {e[2]:.2e} sigma^2 {e[3]:.2e}")
+    assert max(e) < TOL, e
+    s.close()
+
+
+def test_staged_batches_and_graphs_equal_solo_steps_with_the_post_step_m_steps(ddh):
+    """Staged streams with the prior and/or the sigma^2 M-step beside plain staged and cluster
+    streams, in one batch and in a captured graph: phi, r and sigma^2 equal the solo runs bit
+    for bit."""
+    from paper_2305_03284_gb300 import _lib
+    S = _lib.DDH_PATH_STAGED
+    cfgs = [sy.config_single_256(6), sy.config_single_256(6), sy.config_batched(6)[56], sy.config_single_256(6)]
+    overs = [{"phase_block": 2, "phase_prior": 10.0, "noise_update": 1, "exec_path": S},
+             {"exec_path": S},
+             {"phase_block": 2, "phase_prior": 20.0, "exec_path": S},
+             {"phase_block": 2, "phase_prior": 10.0, "noise_update": 1}]
+    data = [make(ddh, c, 6, **o_) for c, o_ in zip(cfgs, overs)]
+    solo = [ddh.Stream(d[3]) for d in data]
+    for f in range(6):
+        for s_, d in zip(solo, data):
+            s_.step(cu(d[1][f]))
+    batch = [ddh.Stream(d[3]) for d in data]
+    graph = [ddh.Stream(d[3]) for d in data]
+    g = ddh.BatchGraph(graph)
+    for f in range(6):
+        ys = [cu(d[1][f]) for d in data]
+        ddh.step_batch(batch, ys)
+        g.run(ys)
+    torch.cuda.synchronize()
+    for k, s1 in enumerate(solo):
+        for s2 in (batch[k], graph[k]):
+            assert torch.equal(s1.phase(), s2.phase()), k
+            assert torch.equal(s1.reflectance(), s2.reflectance()), k
+            assert s1.noise_estimate() == s2.noise_estimate(), k
+    g.close()
