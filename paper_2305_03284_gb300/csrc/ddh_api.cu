@@ -305,11 +305,16 @@ ddh::L2Stream l2_view(ddh_state* s, const void* y) {
   v.r = s->r;
   v.phi = s->phi;
   v.status = s->status;
-  if (s->aux != nullptr && aux_needed(s->prm)) {  // side outputs for the post kernel
-    v.aux = s->aux;
-    v.aux_tiles = s->prm.phase_prior > 0.f ? 1 : 0;
-  }
   return v;
+}
+
+// A staged stream's entry `i` of a launch: its view, parameters and post-kernel side buffer.
+void l2_put(ddh::L2Batch& lb, int i, ddh_state* s, const void* y) {
+  lb.prm[i] = s->kp;
+  lb.st[i] = l2_view(s, y);
+  const bool aux = s->aux != nullptr && aux_needed(s->prm);
+  lb.aux[i] = aux ? s->aux : nullptr;
+  lb.aux_tiles[i] = aux && s->prm.phase_prior > 0.f ? 1 : 0;
 }
 
 // One step of `s` on frame `y`.  `y_host`: y is pinned host memory mapped into the device's
@@ -323,12 +328,11 @@ int enqueue(ddh_state* s, const void* y, float* trace, bool y_host = false, floa
   if (s->staged) {
     if (trace != nullptr || y_host || phi_copy != nullptr || r_copy != nullptr) return DDH_EINVAL;  // cluster path
     ddh::L2Batch lb{};
-    lb.prm[0] = s->kp;
-    lb.st[0] = l2_view(s, y);
+    l2_put(lb, 0, s, y);
     lb.tw = s->tw;
     lb.count = 1;
     DDH_CUDA(ddh::launch_step_l2(s->prm.n, g_schedule[s->device][n_slot(s->prm.n)], lb, s->kp.n_k, s->stream));
-    if (lb.st[0].aux != nullptr) DDH_CUDA(ddh::launch_post(post_args(s), s->stream));
+    if (lb.aux[0] != nullptr) DDH_CUDA(ddh::launch_post(post_args(s), s->stream));
     s->frame += 1;
     return DDH_OK;
   }
@@ -428,8 +432,7 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
         lp.tw[lp.groups] = s->tw;
         ++lp.groups;
       }
-      lp.b.prm[lp.b.count] = s->kp;
-      lp.b.st[lp.b.count] = l2_view(s, ys != nullptr ? ys[i] : nullptr);
+      l2_put(lp.b, lp.b.count, s, ys != nullptr ? ys[i] : nullptr);
       ++lp.b.count;
       ++lp.count[lp.groups - 1];
       prev = i;
@@ -463,7 +466,7 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
         DDH_CUDA(ddh::launch_step_l2(n, sched, lb, lb.prm[0].n_k, st));
         pb.count = 0;
         for (int j = 0; j < lb.count; ++j) {
-          if (lb.st[j].aux == nullptr) continue;
+          if (lb.aux[j] == nullptr) continue;
           pb.a[pb.count++] = post_args(lb_states[j]);
           if (pb.count == ddh::kMaxBatch) {
             DDH_CUDA(ddh::launch_post_batch(pb, st));
@@ -482,8 +485,7 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
           if (rc != DDH_OK) return rc;
         }
         if (lb.count == 0) lb.ytab_base = i;
-        lb.prm[lb.count] = s->kp;
-        lb.st[lb.count] = l2_view(s, ys != nullptr ? ys[i] : nullptr);
+        l2_put(lb, lb.count, s, ys != nullptr ? ys[i] : nullptr);
         lb_states[lb.count] = s;
         lb.tw = s->tw;
         ++lb.count;

@@ -106,8 +106,6 @@ struct L2Stream {
   float* beta;    // 4 images of pair weights: E, S, SE, SW
   float* part;    // row-block statistics, then the combined statistics
   int* flag;      // frame dropped (non-finite or zero variance)
-  float* aux;     // side buffer of the post-step M-steps (layout above), or null
-  int aux_tiles;  // with aux: 1 = tile sums for the phase prior, 0 = residual partial sums
   unsigned* bar;  // grid-barrier words of a persistent launch led by this stream (zeroed at init)
 };
 
@@ -118,6 +116,8 @@ struct L2Batch {
   const float2* const* ytab;
   int ytab_base;
   int count;
+  float* aux[kMaxBatchL2];     // per stream: side buffer of the post-step M-steps (layout above), or null
+  int aux_tiles[kMaxBatchL2];  // with aux: 1 = tile sums for the phase prior, 0 = residual partial sums
 };
 
 // One persistent launch for a whole staged batch: every stage of every stream, the stages

@@ -100,7 +100,7 @@ __device__ __forceinline__ void l2_stage_stats(const L2Batch& b, int sid, int bx
     o[0] = m_a.x; o[1] = m_a.y; o[2] = q_a; o[3] = t0; o[4] = t1; o[5] = t2; o[6] = t3; o[7] = 0.f;
     if (bx == 0) {
       *S.flag = 0;
-      if (S.aux != nullptr) S.aux[1] = 0.f;  // set again by the phase step of an accepted frame
+      if (b.aux[sid] != nullptr) b.aux[sid][1] = 0.f;  // set again by the phase step of an accepted frame
     }
   }
 }
@@ -240,7 +240,9 @@ __global__ void __launch_bounds__(kRowThreads) k_l2_rows_inv(const __grid_consta
 }
 
 // ---- s3: column IFFT, r-init + E-step, column FFT of mu; transposed store into fa ----------
-template <int N, int V>
+// AUX: the stream has the post-step M-steps' side buffer (the instantiation without it is the
+// plain stage; a kernel picks one per stream, uniformly over each block)
+template <int N, int V, bool AUX>
 __device__ __forceinline__ void l2_stage_cols(const L2Batch& b, const float2* twg, int sid, int bx, int first, int last,
                                               unsigned char* smem) {
   const L2Stream& S = b.st[sid];
@@ -249,8 +251,9 @@ __device__ __forceinline__ void l2_stage_cols(const L2Batch& b, const float2* tw
   if (frame_dropped(S)) return;
   // sigma^2 of this frame: the stream's running estimate when it is re-estimated (written by the
   // previous frame's post kernel), else the parameter
-  const float nv = S.aux != nullptr ? S.aux[0] : P.noise_var;
-  const bool aux_out = S.aux != nullptr && last;  // side outputs of the frame's last iteration
+  float* aux = AUX ? b.aux[sid] : nullptr;
+  const float nv = AUX ? aux[0] : P.noise_var;
+  const bool aux_out = AUX && last;  // side outputs of the frame's last iteration
   float2* tw = reinterpret_cast<float2*>(smem);
   // column tiles with stride N + 4: the transposed accesses (8 columns x 4 rows per warp) hit
   // 32 distinct banks (16 bank pairs for the complex tile)
@@ -304,20 +307,24 @@ __device__ __forceinline__ void l2_stage_cols(const L2Batch& b, const float2* tw
     cb[swz(rho)] = mu;
     rc[rho] = ri;
     sc[rho] = fmaf(nv, w, c_abs2(mu));
-    if (aux_out) csum += nv * w;
+    if constexpr (AUX) csum += nv * w;
   }
   __shared__ float cred[kTc];
-  if (aux_out) {
-    csum = warp_sum(csum);
-    if (lane == 0) cred[warp] = csum;
+  if constexpr (AUX) {
+    if (aux_out) {
+      csum = warp_sum(csum);
+      if (lane == 0) cred[warp] = csum;
+    }
   }
   __syncwarp();
   fft_row<N, -1, V>(cb, tw, lane);
   __syncthreads();
-  if (aux_out && threadIdx.x == 0) {  // this block's sum, its columns in order
-    float sc0 = 0.f;
-    for (int w2 = 0; w2 < kTc; ++w2) sc0 += cred[w2];
-    S.aux[kAuxPart + 2 * bx + 1] = sc0;
+  if constexpr (AUX) {
+    if (aux_out && threadIdx.x == 0) {  // this block's sum, its columns in order
+      float sc0 = 0.f;
+      for (int w2 = 0; w2 < kTc; ++w2) sc0 += cred[w2];
+      aux[kAuxPart + 2 * bx + 1] = sc0;
+    }
   }
   for (int i = threadIdx.x; i < kTc * N; i += kColThreads) {
     const int rho = i / kTc, c = i - rho * kTc;
@@ -334,11 +341,14 @@ template <int N, int V>
 __global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first, int last) {
   extern __shared__ __align__(128) unsigned char smem[];
   grid_dep_launch();
-  l2_stage_cols<N, V>(b, b.tw, blockIdx.y, blockIdx.x, first, last, smem);
+  if (b.aux[blockIdx.y] != nullptr)
+    l2_stage_cols<N, V, true>(b, b.tw, blockIdx.y, blockIdx.x, first, last, smem);
+  else
+    l2_stage_cols<N, V, false>(b, b.tw, blockIdx.y, blockIdx.x, first, last, smem);
 }
 
 // ---- s4: row FFT of mu and phase M-step ------------------------------------------------------
-template <int N, int V>
+template <int N, int V, bool AUX>
 __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2* twg, int sid, int bx, int last,
                                                   unsigned char* smem) {
   const L2Stream& S = b.st[sid];
@@ -352,7 +362,8 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
   constexpr int RW = N + 4;
   float2* rows = tw + N;  // kTr rows x RW
   float* ev = reinterpret_cast<float*>(rows + kTr * RW);  // kTr rows x N: a (|y~|^2 + |z|^2)
-  const bool aux_out = S.aux != nullptr && last;          // side outputs of the frame's last iteration
+  float* aux = AUX ? b.aux[sid] : nullptr;
+  const bool aux_out = AUX && last;                       // side outputs of the frame's last iteration
   for (int i = threadIdx.x; i < N; i += kRowThreads) tw[i] = twg[i];
   const float* st = S.part + 8 * (N / kT);
   const float2 ymean = make_float2(st[0], st[1]);
@@ -389,15 +400,15 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
       const float2 z = c_scale(rb[swz(x)], invN);
       const float2 yt = c_scale(c_sub(yv[j], ymean), scale);
       v = make_float2(fmaf(yt.x, z.x, yt.y * z.y), fmaf(yt.y, z.x, -yt.x * z.y));
-      if (aux_out) e = c_abs2(yt) + c_abs2(z);
+      if constexpr (AUX) e = aux_out ? c_abs2(yt) + c_abs2(z) : 0.f;
     }
     for (int o = 1; o < G; o <<= 1) {  // sum over the G consecutive x of the tile
       v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
       v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-      if (aux_out) e += __shfl_xor_sync(0xffffffffu, e, o);
+      if constexpr (AUX) e += __shfl_xor_sync(0xffffffffu, e, o);
     }
     rb[swz(x)] = v;
-    if (aux_out) ev[warp * N + x] = e;
+    if constexpr (AUX) ev[warp * N + x] = e;
   }
   __syncthreads();
   const int l0 = warp & ~(G - 1);
@@ -409,7 +420,7 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
       if (v.x != 0.f || v.y != 0.f) pr[x] = atan2f(v.y, v.x);  // else phi' is kept
     }
   }
-  if (aux_out) {
+  if (AUX && aux_out) {
     // Side outputs for the post kernel, per G x G tile of this block's rows: the tile sums v_t
     // and E_t.  With the phase prior they go to the tile grid; otherwise the tile phase is
     // angle(v_t) and the pupil residual |y~ - e^{j phi} z|^2 over the tile is E_t - 2 |v_t|,
@@ -425,10 +436,10 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
         v = c_add(v, rows[(lt + j) * RW + swz(xt)]);
         e += ev[(lt + j) * N + xt];
       }
-      if (S.aux_tiles) {
+      if (b.aux_tiles[sid]) {
         const int T = (kTr * bx + lt) >> gs;
         if (tile_in_pupil(T, tx, gs, N, P.ap_lim))
-          reinterpret_cast<float4*>(S.aux + kAuxTiles)[T * NT + tx] = make_float4(v.x, v.y, e, 0.f);
+          reinterpret_cast<float4*>(aux + kAuxTiles)[T * NT + tx] = make_float4(v.x, v.y, e, 0.f);
       } else {
         res += e - 2.f * sqrtf(fmaf(v.x, v.x, v.y * v.y));
       }
@@ -440,8 +451,8 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
     if (threadIdx.x == 0) {
       float sr = 0.f;
       for (int w2 = 0; w2 < kTr; ++w2) sr += rred[w2];
-      S.aux[kAuxPart + 2 * bx] = sr;
-      if (bx == 0) S.aux[1] = 1.f;  // the frame was accepted
+      aux[kAuxPart + 2 * bx] = sr;
+      if (bx == 0) aux[1] = 1.f;  // the frame was accepted
     }
   }
 }
@@ -450,7 +461,10 @@ template <int N, int V>
 __global__ void __launch_bounds__(kRowThreads, N == 512 ? 4 : 6) k_l2_rows_fwd(const __grid_constant__ L2Batch b, int last) {
   extern __shared__ __align__(128) unsigned char smem[];
   grid_dep_launch();
-  l2_stage_rows_fwd<N, V>(b, b.tw, blockIdx.y, blockIdx.x, last, smem);
+  if (b.aux[blockIdx.y] != nullptr)
+    l2_stage_rows_fwd<N, V, true>(b, b.tw, blockIdx.y, blockIdx.x, last, smem);
+  else
+    l2_stage_rows_fwd<N, V, false>(b, b.tw, blockIdx.y, blockIdx.x, last, smem);
 }
 
 // ---- s5: surrogate pair weights at the sweep's entry values ---------------------------------
@@ -635,12 +649,12 @@ __device__ __noinline__ void pi_rows_inv(const L2Batch& b, const float2* tw, int
 template <int N>
 __device__ __noinline__ void pi_cols(const L2Batch& b, const float2* tw, int sid, int bx, int first, int last,
                                      unsigned char* smem) {
-  l2_stage_cols<N, 0>(b, tw, sid, bx, first, last, smem);
+  l2_stage_cols<N, 0, false>(b, tw, sid, bx, first, last, smem);  // no side buffers here
 }
 template <int N>
 __device__ __noinline__ void pi_rows_fwd(const L2Batch& b, const float2* tw, int sid, int bx, int last,
                                          unsigned char* smem) {
-  l2_stage_rows_fwd<N, 0>(b, tw, sid, bx, last, smem);
+  l2_stage_rows_fwd<N, 0, false>(b, tw, sid, bx, last, smem);
 }
 template <int N>
 __device__ __noinline__ void pi_weights(const L2Batch& b, int sid, int bx) { l2_stage_weights<N>(b, sid, bx); }
