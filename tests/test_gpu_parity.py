@@ -132,7 +132,7 @@ def _run_oracle(prm, ys, ph):
 
 
 def test_free_running_parity_64_100_frames_tiled_phase(ddh):
-    """North-star parity: 64x64 stream (32 px pupil, D/r0 10, 0.5 px/frame, SNR 10), 100
+    """Parity bar (phi, r, Strehl within 2e-5 after 100 frames): 64x64 stream (32 px pupil, D/r0 10, 0.5 px/frame, SNR 10), 100
     free-running frames of one EM iteration each, phase held constant on 2x2 tiles.  With
     tiles the iteration contracts (the oracle's own 1e-7 perturbations decay), so GPU and
     oracle trajectories can agree after 100 frames."""
@@ -150,7 +150,7 @@ def test_free_running_parity_64_100_frames_tiled_phase(ddh):
 
 @pytest.mark.parametrize("stream", ["paper", "bench"])
 def test_free_running_parity_256_100_frames_tiled_phase_both_paths(ddh, stream):
-    """North-star parity at the realistic size: 100 free-running 256^2 frames with the phase
+    """The same parity bar at the realistic size: 100 free-running 256^2 frames with the phase
     held constant on 2x2 tiles, on the cluster kernel and on the L2-staged kernels, against one
     FP64 oracle trajectory: the paper's Sec. 5.A stream (bar chart, D/r0 10, SNR 10 dB; sigma_r
     0.03, alpha 0.0125) and the benchmark's stream (D/r0 15, 1 px/frame, SNR 5; defaults)."""
