@@ -132,8 +132,9 @@ def _run_oracle(prm, ys, ph):
 
 
 def test_free_running_parity_64_100_frames_tiled_phase(ddh):
-    """Parity bar (phi, r, Strehl within 2e-5 after 100 frames): 64x64 stream (32 px pupil, D/r0 10, 0.5 px/frame, SNR 10), 100
-    free-running frames of one EM iteration each, phase held constant on 2x2 tiles.  With
+    """Parity bar (phi, r, Strehl within 2e-5 after 100 frames): 64x64 stream (32 px pupil,
+    D/r0 10, 0.5 px/frame, SNR 10), 100 free-running frames of one EM iteration each, phase
+    held constant on 2x2 tiles.  With
     tiles the iteration contracts (the oracle's own 1e-7 perturbations decay), so GPU and
     oracle trajectories can agree after 100 frames."""
     cfg = sy.config_single_64()
