@@ -804,7 +804,10 @@ def run_ours(args):
             for name, over in (("tiles_2x2", {"phase_block": 2}),
                                ("tiles_2x2_prior_20_noise_update", {"phase_block": 2, "phase_prior": 20.0,
                                                                     "noise_update": 1}),
-                               ("per_pixel_noise_update", {"noise_update": 1})):
+                               ("per_pixel_noise_update", {"noise_update": 1}),
+                               ("staged_tiles_2x2", {"phase_block": 2, "exec_path": 2}),
+                               ("staged_tiles_2x2_prior_20_noise_update", {"phase_block": 2, "phase_prior": 20.0,
+                                                                           "noise_update": 1, "exec_path": 2})):
                 sp = ddh.Stream(ddh.default_params(n, cfg.aperture_diam, cfg.snr, **over), stream=stream)
                 for i in range(5):
                     lib.ddh_step(sp._h, ptrs[i % len(ptrs)])
@@ -818,8 +821,9 @@ def run_ours(args):
                 sp.sync()
                 us = c0.elapsed_time(c1) * 1e3 / 200
                 prior[name] = {"us_per_frame": us, "frames_per_s": 1e6 / us}
-            prior["definition"] = ("256^2 stream, 200 frames back to back (CUDA events); the prior and "
-                                   "sigma^2 variants add the post-step kernel per frame")
+            prior["definition"] = ("256^2 stream, 200 frames back to back (CUDA events), on the cluster kernel "
+                                   "or (staged_*) one stream on the L2-staged kernels; the prior and sigma^2 "
+                                   "variants add the post-step kernel per frame")
         # ---- end to end through the pipelined host-buffer call ---------------------------
         # pinned host frames in, every frame's phase back to pinned host memory; four output
         # buffers in rotation, each reused only after its previous frame has arrived

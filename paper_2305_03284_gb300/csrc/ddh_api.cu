@@ -480,7 +480,10 @@ int enqueue_batch(ddh_state* const* states, const void* const* ys, const float2*
       for (int i = 0; i < count; ++i) {
         ddh_state* s = states[i];
         if (!member(i, gr)) continue;
-        if (lb.count > 0 && s->kp.n_k != lb.prm[0].n_k) {  // one EM-iteration count per launch
+        const bool aux = s->aux != nullptr && aux_needed(s->prm);
+        // one EM-iteration count per launch, and either all or none of its streams with the
+        // post-step side buffer
+        if (lb.count > 0 && (s->kp.n_k != lb.prm[0].n_k || aux != (lb.aux[0] != nullptr))) {
           const int rc = flush();
           if (rc != DDH_OK) return rc;
         }

@@ -341,10 +341,16 @@ template <int N, int V>
 __global__ void __launch_bounds__(kColThreads) k_l2_cols(const __grid_constant__ L2Batch b, int first, int last) {
   extern __shared__ __align__(128) unsigned char smem[];
   grid_dep_launch();
-  if (b.aux[blockIdx.y] != nullptr)
-    l2_stage_cols<N, V, true>(b, b.tw, blockIdx.y, blockIdx.x, first, last, smem);
-  else
-    l2_stage_cols<N, V, false>(b, b.tw, blockIdx.y, blockIdx.x, first, last, smem);
+  l2_stage_cols<N, V, false>(b, b.tw, blockIdx.y, blockIdx.x, first, last, smem);
+}
+
+// the same stage for a launch whose streams all have the post-step side buffer (a separate
+// kernel, so that the plain one keeps its own register allocation)
+template <int N, int V>
+__global__ void __launch_bounds__(kColThreads) k_l2_cols_aux(const __grid_constant__ L2Batch b, int first, int last) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  grid_dep_launch();
+  l2_stage_cols<N, V, true>(b, b.tw, blockIdx.y, blockIdx.x, first, last, smem);
 }
 
 // ---- s4: row FFT of mu and phase M-step ------------------------------------------------------
@@ -458,13 +464,19 @@ __device__ __forceinline__ void l2_stage_rows_fwd(const L2Batch& b, const float2
 }
 
 template <int N, int V>
-__global__ void __launch_bounds__(kRowThreads, N == 512 ? 4 : 6) k_l2_rows_fwd(const __grid_constant__ L2Batch b, int last) {
+__global__ void __launch_bounds__(kRowThreads) k_l2_rows_fwd(const __grid_constant__ L2Batch b, int last) {
   extern __shared__ __align__(128) unsigned char smem[];
   grid_dep_launch();
-  if (b.aux[blockIdx.y] != nullptr)
-    l2_stage_rows_fwd<N, V, true>(b, b.tw, blockIdx.y, blockIdx.x, last, smem);
-  else
-    l2_stage_rows_fwd<N, V, false>(b, b.tw, blockIdx.y, blockIdx.x, last, smem);
+  l2_stage_rows_fwd<N, V, false>(b, b.tw, blockIdx.y, blockIdx.x, last, smem);
+}
+
+// with the post-step side outputs (four blocks per SM at 512^2 keep it at 64 registers)
+template <int N, int V>
+__global__ void __launch_bounds__(kRowThreads, N == 512 ? 4 : 6) k_l2_rows_fwd_aux(const __grid_constant__ L2Batch b,
+                                                                                  int last) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  grid_dep_launch();
+  l2_stage_rows_fwd<N, V, true>(b, b.tw, blockIdx.y, blockIdx.x, last, smem);
 }
 
 // ---- s5: surrogate pair weights at the sweep's entry values ---------------------------------
@@ -555,7 +567,9 @@ __global__ void __launch_bounds__(256) k_l2_colour(const __grid_constant__ L2Bat
 }
 
 template <int N>
-constexpr size_t rows_smem() { return sizeof(float2) * (N + kTr * (N + 4)) + sizeof(float) * kTr * N; }
+constexpr size_t rows_smem() { return sizeof(float2) * (N + kTr * (N + 4)); }
+template <int N>
+constexpr size_t rows_smem_aux() { return rows_smem<N>() + sizeof(float) * kTr * N; }  // + the E rows
 template <int N>
 constexpr size_t cols_smem() { return sizeof(float2) * (N + kTc * (N + 4)) + 2 * sizeof(float) * kTc * (N + 4); }
 
@@ -576,8 +590,10 @@ cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t sm
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// every stream of `b` has the post-step side buffer, or none (the caller forms such launches)
 template <int N, int V>
 cudaError_t l2_step(const L2Batch& b, int n_k, cudaStream_t st) {
+  const bool aux = b.aux[0] != nullptr;
   const dim3 grid(N / kT, b.count), blk(kThreads);
   const dim3 rgrid(N / kTr, b.count), rblk(kRowThreads);
   const dim3 cgrid2(N / kTc, b.count), cblk(kColThreads);
@@ -588,8 +604,11 @@ cudaError_t l2_step(const L2Batch& b, int n_k, cudaStream_t st) {
     const int first = it == 0 ? 1 : 0;
     e = launch_pdl(k_l2_rows_inv<N, V>, rgrid, rblk, rows_smem<N>(), st, b, first);
     const int last = it == n_k - 1 ? 1 : 0;
-    if (e == cudaSuccess) e = launch_pdl(k_l2_cols<N, V>, cgrid2, cblk, cols_smem<N>(), st, b, first, last);
-    if (e == cudaSuccess) e = launch_pdl(k_l2_rows_fwd<N, V>, rgrid, rblk, rows_smem<N>(), st, b, last);
+    if (e == cudaSuccess)
+      e = launch_pdl(aux ? k_l2_cols_aux<N, V> : k_l2_cols<N, V>, cgrid2, cblk, cols_smem<N>(), st, b, first, last);
+    if (e == cudaSuccess)
+      e = launch_pdl(aux ? k_l2_rows_fwd_aux<N, V> : k_l2_rows_fwd<N, V>, rgrid, rblk,
+                     aux ? rows_smem_aux<N>() : rows_smem<N>(), st, b, last);
     if (e == cudaSuccess) e = launch_pdl(k_l2_weights<N>, wgrid, dim3(256), 0, st, b);
     for (int c = 0; c < 4 && e == cudaSuccess; ++c) e = launch_pdl(k_l2_colour<N>, cgrid, dim3(256), 0, st, b, c);
   }
@@ -606,6 +625,12 @@ cudaError_t l2_configure() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_l2_rows_fwd<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(rows_smem<N>()));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_l2_cols_aux<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(cols_smem<N>()));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_l2_rows_fwd_aux<N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(rows_smem_aux<N>()));
   return e;
 }
 
