@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-stream", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-frames", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-warm", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -241,7 +242,7 @@ def oracle_frames_per_second(seconds, max_frames=None, warm=1, stream_id=0):
 
 def cpu_worker(args):
     fps, frames, el = oracle_frames_per_second(args.cpu_seconds, max_frames=args.cpu_frames or None,
-                                               stream_id=args.cpu_stream)
+                                               warm=args.cpu_warm, stream_id=args.cpu_stream)
     print(json.dumps({"value": fps, "frames": frames, "seconds": el}))
 
 
@@ -249,15 +250,17 @@ def host_cores():
     return max(1, min(os.cpu_count() or 1, 64))
 
 
-def parallel_oracle(cores, seconds, frames_per_worker=0):
+def parallel_oracle(cores, seconds, frames_per_worker=0, warm=1):
     """The oracle on `cores` host cores: one single-threaded process per core, each running its
-    own 256^2 stream (independent streams, as the GPU's replicas), started together.  Returns
-    (aggregate frames/s, total frames, longest worker time) or an error string."""
+    own 256^2 stream (independent streams, as the GPU's replicas), started together;
+    `frames_per_worker` is one count for all or a list with one per process, 0 = timed by
+    `seconds`.  Returns (aggregate frames/s, total frames, longest worker time) or an error string."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    counts = frames_per_worker if isinstance(frames_per_worker, list) else [frames_per_worker] * cores
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--cpu-seconds", str(seconds),
-           "--cpu-frames", str(int(frames_per_worker))]
-    procs = [subprocess.Popen(cmd + ["--cpu-stream", str(i)], env=env, stdout=subprocess.PIPE,
-                              stderr=subprocess.PIPE, text=True) for i in range(cores)]
+           "--cpu-warm", str(int(warm))]
+    procs = [subprocess.Popen(cmd + ["--cpu-stream", str(i), "--cpu-frames", str(int(counts[i]))], env=env,
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True) for i in range(cores)]
     res, err = [], None
     for p in procs:
         out, e = p.communicate(timeout=900)
@@ -288,23 +291,27 @@ def run_reference(args):
     rank, _, world = dist_info()
     if rank != 0:
         return
-    cores = host_cores()
-    # each step is one oracle frame; the steps are spread over the host cores (one stream per
-    # core) and capped so that the run stays within a few minutes
+    # each step is one oracle frame: the K steps are spread over up to one process per host core
+    # (one stream each), each process capped at about two minutes of frames so that the run
+    # stays within a few minutes, after W untimed warm-up frames of its own
+    k_steps, warm = max(1, args.steps), max(0, args.warmup)
+    cores = min(host_cores(), k_steps)
     fps_probe, _, _ = oracle_frames_per_second(0.0, max_frames=1, warm=1)
-    per_worker = max(1, min(-(-args.steps // cores), int(120.0 * fps_probe)))
-    out, err = parallel_oracle(cores, 1e9, frames_per_worker=per_worker)
+    cap = max(1, int(120.0 * fps_probe))
+    counts = [min(cap, k_steps // cores + (1 if i < k_steps % cores else 0)) for i in range(cores)]
+    out, err = parallel_oracle(cores, 1e9, frames_per_worker=counts, warm=warm)
     if out is None:
         print(json.dumps({"impl": "reference", "unavailable": f"oracle workers failed: {err}"}))
         return
     fps, frames, el = out
     line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": world,
-            "steps": frames, "warmup": 1, "ms_per_step": 1e3 / fps, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / fps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": 256, "streams": cores},
             "cpu_baseline": {"value": fps, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{frames} frames of {args.steps} requested (bounded): {cores} single-threaded "
-                                       f"processes, one 256x256 stream each, {per_worker} frames per process"},
+                             "sample": f"{frames} of the {args.steps} requested frames timed (each process capped "
+                                       f"at {cap} frames): {cores} single-threaded processes, one 256x256 stream "
+                                       f"each, {warm} untimed warm-up frames per process"},
             "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
