@@ -287,6 +287,14 @@ def cpu_baseline(seconds):
 
 
 # ------------------------------------------------------------------------------ arms
+def reference_counts(k_steps, cores, cap):
+    """Oracle frames per process for the reference arm: the K steps spread over up to `cores`
+    processes as evenly as possible, each process capped at `cap` frames."""
+    k_steps = max(1, k_steps)
+    workers = max(1, min(cores, k_steps))
+    return [min(cap, k_steps // workers + (1 if i < k_steps % workers else 0)) for i in range(workers)]
+
+
 def run_reference(args):
     rank, _, world = dist_info()
     if rank != 0:
@@ -294,11 +302,11 @@ def run_reference(args):
     # each step is one oracle frame: the K steps are spread over up to one process per host core
     # (one stream each), each process capped at about two minutes of frames so that the run
     # stays within a few minutes, after W untimed warm-up frames of its own
-    k_steps, warm = max(1, args.steps), max(0, args.warmup)
-    cores = min(host_cores(), k_steps)
+    warm = max(0, args.warmup)
     fps_probe, _, _ = oracle_frames_per_second(0.0, max_frames=1, warm=1)
     cap = max(1, int(120.0 * fps_probe))
-    counts = [min(cap, k_steps // cores + (1 if i < k_steps % cores else 0)) for i in range(cores)]
+    counts = reference_counts(args.steps, host_cores(), cap)
+    cores = len(counts)
     out, err = parallel_oracle(cores, 1e9, frames_per_worker=counts, warm=warm)
     if out is None:
         print(json.dumps({"impl": "reference", "unavailable": f"oracle workers failed: {err}"}))
