@@ -79,8 +79,9 @@ typedef struct ddh_params {
                            256 or 512; uses every SM when many streams step together, so the
                            higher throughput for large batches).  Fixed for the state's
                            lifetime: a stream steps the same way alone and in any batch.  The
-                           staged path has no trace output, host-buffer in-place steps,
-                           tile-phase prior, sigma^2 M-step or adjoint (DDH_EINVAL) */
+                           staged path has no trace output, host-buffer in-place steps or
+                           adjoint (DDH_EINVAL); the tile-phase prior and the sigma^2 M-step run
+                           on both paths */
 } ddh_params;
 #define DDH_PATH_DEFAULT 0
 #define DDH_PATH_CLUSTER 1
